@@ -1,0 +1,389 @@
+"""Plain FP64 CPU oracle of the real-space RPA correlation-energy method
+(B. Zhang, S. Shah, J. E. Pask, E. Chow, P. Suryanarayana, arXiv 2504.01816).
+
+TEST INFRASTRUCTURE ONLY.  This package exists to check the CUDA library.  Only
+the test-suite, the smoke check (``__graft_entry__.smoke``) and the timed CPU
+baseline of ``bench.py`` may import it.  It shares no code with the CUDA library:
+it has its own finite-difference weights, Hamiltonian, Coulomb operator, COCG
+(``cocg_oracle.c``), projections, eigensolver calls and frequency quadrature.
+
+Every function follows the paper's steps in the paper's order, in FP64, with no
+blocking, fusion or reordering beyond what the definition states.  Library
+routines (numpy matmul, eigh, cholesky, Gauss-Legendre nodes) serve as single
+steps.
+
+Discrete conventions (the paper says only "high-order centred finite differences"
+and "trapezoidal rule", Section "Implementation"; these are the readings):
+
+* grid functions are vectors of length N_d = nx*ny*nz, point (i,j,k) at
+  i + nx*(j + ny*k); a block of K of them is an array (K, N_d);
+* orbitals u_n are l2-orthonormal (u = psi h^{3/2});
+* L_h is the 12th-order centred Laplacian with zero values outside the box;
+  H = -1/2 L_h + diag(V_loc);
+* nu = 4 pi (-L_h)^{-1} (Poisson equation, Eq. 5); nu^p is applied through the
+  eigendecompositions of the three 1D second-difference matrices (Kronecker
+  product formalism, Section "Implementation");
+* chi0 dV = drho = (4/h^3) Re sum_n u_n (.) x_n with
+  (H - eps_n + i omega) x_n = -P_c(u_n (.) dV),  P_c = I - U U^T   (Eqs. 7-9);
+* the correlation energy is E_c = (1/2pi) int_0^inf sum_i [log(1-lambda_i) +
+  lambda_i] d omega over the lowest N_r eigenvalues of nu^1/2 chi0 nu^1/2
+  (Eq. 10), by subspace iteration with Rayleigh-Ritz on the projected matrix
+  (Algorithm 1 with subspace diagonalisation in place of spectral quadrature).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import build as _build
+
+RADIUS = 6  # 12th-order centred differences
+
+OK, NOT_CONVERGED, BREAKDOWN, NOT_SPD = 0, 4, 5, 6
+
+_lib_handle = None
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        lib = ctypes.CDLL(_build.build())
+        d, i = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        lib.oracle_apply_h.argtypes = [ctypes.c_int] * 4 + [d, d, ctypes.c_double, ctypes.c_double, d, d]
+        lib.oracle_apply_h.restype = None
+        lib.oracle_cocg_batch.argtypes = ([ctypes.c_int] * 4 + [d, d, ctypes.c_int, d, d, d, d,
+                                          ctypes.c_double, ctypes.c_int, i, i])
+        lib.oracle_cocg_batch.restype = None
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib_handle = lib
+    return _lib_handle
+
+
+def num_threads() -> int:
+    return _lib().oracle_num_threads()
+
+
+def set_threads(n: int) -> None:
+    _lib().oracle_set_threads(int(n))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+# ------------------------------------------------------------------------------------
+# Finite differences and the Hamiltonian (Section "Implementation", Eq. 4 local part)
+# ------------------------------------------------------------------------------------
+def fd_weights(radius: int = RADIUS) -> np.ndarray:
+    """Centred second-derivative weights of order 2*radius on a unit grid.
+
+    f'' ~ w0 f(0) + sum_k wk (f(k) + f(-k)),
+    wk = 2 (-1)^(k+1) (p!)^2 / (k^2 (p-k)! (p+k)!),  w0 = -2 sum_k 1/k^2.
+    """
+    p = radius
+    w = np.zeros(p + 1)
+    for k in range(1, p + 1):
+        w[k] = 2.0 * (-1) ** (k + 1) * math.factorial(p) ** 2 / (
+            k * k * math.factorial(p - k) * math.factorial(p + k))
+    w[0] = -2.0 * sum(1.0 / (k * k) for k in range(1, p + 1))
+    return w
+
+
+@dataclass
+class Grid:
+    nx: int
+    ny: int
+    nz: int
+    h: float
+
+    @property
+    def n_d(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def apply_h(grid: Grid, vloc: np.ndarray, vec: np.ndarray, sigma: complex = 0.0) -> np.ndarray:
+    """(H + sigma) vec for one complex grid function (matrix-free, Dirichlet)."""
+    w = fd_weights() / grid.h ** 2
+    v = np.ascontiguousarray(vec, dtype=np.complex128)
+    out = np.empty_like(v)
+    _lib().oracle_apply_h(grid.nx, grid.ny, grid.nz, RADIUS, _dp(w), _dp(np.ascontiguousarray(vloc)),
+                          float(np.real(sigma)), float(np.imag(sigma)),
+                          _dp(v.view(np.float64)), _dp(out.view(np.float64)))
+    return out
+
+
+def cocg(grid: Grid, vloc: np.ndarray, sigma: np.ndarray, b: np.ndarray, tol: float, maxit: int):
+    """Solve (H + sigma_s) x_s = b_s for every row s of b by COCG (Section
+    "Implementation"; complex-symmetric Sternheimer operator of Eq. 9).
+
+    Returns (x, iterations, status); status 0 converged, 4 not converged, 5 breakdown.
+    """
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    nsys = b.shape[0]
+    sigma = np.asarray(sigma, dtype=np.complex128).reshape(nsys)
+    x = np.zeros_like(b)
+    it = np.zeros(nsys, dtype=np.int32)
+    st = np.zeros(nsys, dtype=np.int32)
+    w = fd_weights() / grid.h ** 2
+    sre = np.ascontiguousarray(sigma.real)
+    sim = np.ascontiguousarray(sigma.imag)
+    _lib().oracle_cocg_batch(grid.nx, grid.ny, grid.nz, RADIUS, _dp(w), _dp(np.ascontiguousarray(vloc)), nsys,
+                             _dp(sre), _dp(sim), _dp(b.view(np.float64)), _dp(x.view(np.float64)),
+                             float(tol), int(maxit), _ip(it), _ip(st))
+    return x, it, st
+
+
+# ------------------------------------------------------------------------------------
+# Coulomb operator by the Kronecker-product formalism (Section "Implementation")
+# ------------------------------------------------------------------------------------
+def second_difference_1d(n: int, h: float) -> np.ndarray:
+    """Dense 1D second-derivative matrix with zero boundary values (Toeplitz)."""
+    w = fd_weights()
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - RADIUS), min(n, i + RADIUS + 1)):
+            D[i, j] = w[abs(i - j)] / h ** 2
+    return D
+
+
+class Coulomb:
+    """nu^p = (4 pi)^p (-L_h)^(-p) through -L_h = (Q_z x Q_y x Q_x) diag(mu_x+mu_y+mu_z) (...)^T,
+    with K_a = -D_a = Q_a diag(mu_a) Q_a^T the 1D eigendecompositions."""
+
+    def __init__(self, grid: Grid):
+        self.grid = grid
+        self.mu, self.Q = [], []
+        for n in (grid.nx, grid.ny, grid.nz):
+            mu, Q = np.linalg.eigh(-second_difference_1d(n, grid.h))
+            self.mu.append(mu)
+            self.Q.append(Q)
+        mx, my, mz = self.mu
+        self.lam = mz[:, None, None] + my[None, :, None] + mx[None, None, :]
+
+    def apply(self, X: np.ndarray, power: float) -> np.ndarray:
+        """nu^power applied to every row of X (K, N_d)."""
+        g = self.grid
+        Qx, Qy, Qz = self.Q
+        Y = np.asarray(X, dtype=np.float64).reshape(-1, g.nz, g.ny, g.nx)
+        # to the eigenbasis: multiply by Q_a^T along each axis
+        Y = np.einsum("ia,kzyi->kzya", Qx, Y)
+        Y = np.einsum("ja,kzjx->kzax", Qy, Y)
+        Y = np.einsum("la,klyx->kayx", Qz, Y)
+        Y = Y * ((4.0 * math.pi) ** power * self.lam ** (-power))[None]
+        # back: multiply by Q_a along each axis
+        Y = np.einsum("ia,kzya->kzyi", Qx, Y)
+        Y = np.einsum("ja,kzax->kzjx", Qy, Y)
+        Y = np.einsum("la,kayx->klyx", Qz, Y)
+        return Y.reshape(np.shape(X))
+
+
+# ------------------------------------------------------------------------------------
+# chi0 by density functional perturbation theory (Eqs. 7-9, Algorithm 1 inner loop)
+# ------------------------------------------------------------------------------------
+@dataclass
+class SolveStats:
+    iterations: List[np.ndarray] = field(default_factory=list)
+    status: List[np.ndarray] = field(default_factory=list)
+
+    def total_iterations(self) -> int:
+        return int(sum(int(a.sum()) for a in self.iterations))
+
+    def n_solves(self) -> int:
+        return int(sum(a.size for a in self.iterations))
+
+    def worst_status(self) -> int:
+        return int(max((int(a.max()) for a in self.status if a.size), default=0))
+
+
+class Oracle:
+    """One model system (grid, V_loc, occupied u_n and eps_n) and the method on it."""
+
+    def __init__(self, nx, ny, nz, h, vloc, psi, eps, n_atoms=1):
+        self.grid = Grid(int(nx), int(ny), int(nz), float(h))
+        self.vloc = np.ascontiguousarray(vloc, dtype=np.float64)
+        self.psi = np.ascontiguousarray(psi, dtype=np.float64)   # (N_s, N_d)
+        self.eps = np.asarray(eps, dtype=np.float64)
+        self.n_atoms = int(n_atoms)
+        self.coulomb = Coulomb(self.grid)
+
+    @classmethod
+    def from_system(cls, s):
+        return cls(s.nx, s.ny, s.nz, s.h, s.vloc, s.psi, s.eps, s.n_atoms)
+
+    @property
+    def n_s(self):
+        return self.psi.shape[0]
+
+    def sternheimer_rhs(self, n: int, dv: np.ndarray) -> np.ndarray:
+        """b = -P_c(u_n (.) dV) for every row of dv: the Sternheimer right-hand side (Eq. 9)
+        with the occupied components removed (P_c = I - U U^T)."""
+        u = self.psi
+        pair = u[n][None, :] * dv
+        return -(pair - (pair @ u.T) @ u)
+
+    def chi0(self, dv: np.ndarray, omega: float, tol: float, maxit: int = 100000, sign: int = +1,
+             stats: Optional[SolveStats] = None, max_chunk_bytes: float = 2.5e8,
+             galerkin: bool = False, return_x: bool = False):
+        """drho = chi0(i omega) dV for every row of dv (Eqs. 7-9).
+
+        For each occupied n and each dV: solve (H - eps_n + sign*i*omega) x = b by COCG, then
+        drho = (4/h^3) Re sum_n u_n (.) x_n.  galerkin=True takes the paper's Galerkin
+        initial guess instead of projecting the right-hand side (Section "Implementation").
+        """
+        g = self.grid
+        dv = np.atleast_2d(np.asarray(dv, dtype=np.float64))
+        k = dv.shape[0]
+        drho = np.zeros((k, g.n_d))
+        xs = [] if return_x else None
+        per_row = 16.0 * 2 * g.n_d
+        chunk = max(1, int(max_chunk_bytes // per_row))
+        for n in range(self.n_s):
+            sigma = -self.eps[n] + sign * 1j * omega
+            for j0 in range(0, k, chunk):
+                blk = dv[j0:j0 + chunk]
+                if galerkin:
+                    x = self._galerkin_solve(n, blk, sigma, tol, maxit, stats)
+                else:
+                    b = self.sternheimer_rhs(n, blk).astype(np.complex128)
+                    x, it, st = cocg(g, self.vloc, np.full(len(blk), sigma), b, tol, maxit)
+                    if stats is not None:
+                        stats.iterations.append(it)
+                        stats.status.append(st)
+                drho[j0:j0 + chunk] += (4.0 / g.h ** 3) * np.real(self.psi[n][None, :] * x)
+                if return_x:
+                    xs.append((n, j0, x))
+        return (drho, xs) if return_x else drho
+
+    def _galerkin_solve(self, n, blk, sigma, tol, maxit, stats):
+        """Unprojected b = -u_n (.) dV; initial guess x0 = U y with (U^T A U) y = U^T b, which
+        removes the occupied components from the initial residual; COCG then solves for the
+        correction."""
+        g = self.grid
+        u = self.psi
+        b = -(u[n][None, :] * blk).astype(np.complex128)
+        UtAU = np.empty((self.n_s, self.n_s), dtype=np.complex128)
+        AU = np.array([apply_h(g, self.vloc, u[m].astype(np.complex128), sigma) for m in range(self.n_s)])
+        UtAU[:, :] = u @ AU.T
+        y = np.linalg.solve(UtAU, (b @ u.T).T).T          # (len(blk), N_s)
+        x0 = y @ u
+        r0 = b - np.array([apply_h(g, self.vloc, xi, sigma) for xi in x0])
+        d, it, st = cocg(g, self.vloc, np.full(len(blk), sigma), r0, tol, maxit)
+        if stats is not None:
+            stats.iterations.append(it)
+            stats.status.append(st)
+        return x0 + d
+
+    def chi_tilde(self, V: np.ndarray, omega: float, tol: float, maxit: int = 100000,
+                  stats: Optional[SolveStats] = None) -> np.ndarray:
+        """R = nu^1/2 chi0(i omega) nu^1/2 V for every row of V (Algorithm 1: V_j = N V_j,
+        Sternheimer loop over n, R_j = N R_j)."""
+        vt = self.coulomb.apply(V, 0.5)
+        drho = self.chi0(vt, omega, tol, maxit, stats=stats)
+        return self.coulomb.apply(drho, 0.5)
+
+    def nu_chi0(self, V: np.ndarray, omega: float, tol: float, maxit: int = 100000,
+                stats: Optional[SolveStats] = None) -> np.ndarray:
+        """nu chi0(i omega) V (same eigenvalues as nu^1/2 chi0 nu^1/2, Formulation)."""
+        return self.coulomb.apply(self.chi0(V, omega, tol, maxit, stats=stats), 1.0)
+
+
+# ------------------------------------------------------------------------------------
+# Subspace iteration, Rayleigh-Ritz and the frequency integral (Algorithm 1, Eq. 10)
+# ------------------------------------------------------------------------------------
+def frequency_quadrature(n_omega: int, omega0: float = 1.0):
+    """Gauss-Legendre nodes x_k, weights w_k on (-1,1) mapped to [0, inf):
+    omega = omega0 (1+x)/(1-x), weight = 2 omega0 w / (1-x)^2.  Ascending omega."""
+    x, w = np.polynomial.legendre.leggauss(n_omega)
+    return omega0 * (1.0 + x) / (1.0 - x), 2.0 * omega0 * w / (1.0 - x) ** 2
+
+
+def g_rpa(lam: np.ndarray) -> np.ndarray:
+    """g(x) = log(1 - x) + x."""
+    lam = np.asarray(lam, dtype=np.float64)
+    return np.log1p(-lam) + lam
+
+
+class NotSPD(RuntimeError):
+    pass
+
+
+def orthonormalize_cholesky(R: np.ndarray) -> np.ndarray:
+    """V = R L^{-T} with L L^T = R^T R (rows of R are the vectors): Algorithm 1 overlap,
+    Cholesky and orthonormalisation."""
+    M = R @ R.T
+    try:
+        L = np.linalg.cholesky(M)
+    except np.linalg.LinAlgError as e:
+        raise NotSPD(str(e))
+    return sla.solve_triangular(L, R, lower=True)
+
+
+@dataclass
+class EcResult:
+    e_c: float                        # Hartree
+    e_c_per_atom: float
+    e_c_per_omega: np.ndarray         # weighted contribution (w_m / 2 pi) sum_i g(lambda_i), ascending omega
+    lambdas: np.ndarray               # (N_omega, N_r) Ritz values of the last iteration, ascending omega
+    omegas: np.ndarray
+    weights: np.ndarray
+    subspace_iterations: np.ndarray   # per frequency
+    sternheimer_solves: int = 0
+    cocg_iterations: int = 0
+    V_final: Optional[np.ndarray] = None
+
+
+def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, omega0: float = 1.0,
+           max_subspace_iters: int = 100, fixed_iters: Optional[int] = None, maxit: int = 100000,
+           verbose: bool = False) -> EcResult:
+    """E_c by Algorithm 1 with Rayleigh-Ritz: frequencies from highest to lowest, the subspace
+    carried over from each frequency to the next; at each frequency iterate
+    R = chi~0 V, C = V^T R, lambda = eig(C), E_cm = (w_m/2pi) sum g(lambda), M = R^T R = L L^T,
+    V = R L^{-T} while |E_cm - E_cm_old| > eps_c * N_atoms / N_omega (eps_c in Ha/atom), at least
+    two iterations (E_cm starts at 0).  fixed_iters runs exactly that many iterations instead."""
+    omegas, weights = frequency_quadrature(n_omega, omega0)
+    V = orthonormalize_cholesky(np.asarray(V0, dtype=np.float64))
+    n_r = V.shape[0]
+    lambdas = np.zeros((n_omega, n_r))
+    e_m = np.zeros(n_omega)
+    iters = np.zeros(n_omega, dtype=np.int64)
+    stats = SolveStats()
+    thr = eps_c * o.n_atoms / n_omega
+    for m in range(n_omega - 1, -1, -1):
+        ecm = 0.0
+        it = 0
+        while True:
+            ecm_old = ecm
+            R = o.chi_tilde(V, omegas[m], tol, maxit, stats=stats)
+            C = V @ R.T
+            C = 0.5 * (C + C.T)
+            lam = np.linalg.eigvalsh(C)
+            ecm = weights[m] / (2.0 * math.pi) * float(np.sum(g_rpa(lam)))
+            V = orthonormalize_cholesky(R)
+            it += 1
+            if verbose:
+                print(f"  omega={omegas[m]:.5f} it={it} E_cm={ecm:.12f}")
+            if fixed_iters is not None:
+                if it >= fixed_iters:
+                    break
+            elif abs(ecm - ecm_old) <= thr or it >= max_subspace_iters:
+                break
+        lambdas[m] = lam
+        e_m[m] = ecm
+        iters[m] = it
+    e_c = float(np.sum(e_m))
+    return EcResult(e_c, e_c / o.n_atoms, e_m, lambdas, omegas, weights, iters,
+                    stats.n_solves(), stats.total_iterations(), V)

@@ -1,0 +1,53 @@
+"""Dense brute-force references used to pin the oracle (tiny grids only).
+
+Everything here is assembled from the model problem's sparse matrices (``synth``)
+and dense LAPACK routines: a route independent of the oracle's matrix-free
+stencil, Kronecker Coulomb operator and COCG.
+"""
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+import synth
+
+
+def dense_h(system):
+    return synth.hamiltonian_matrix(system).toarray()
+
+
+def dense_minus_laplacian(nx, ny, nz, h):
+    return -synth.laplacian_matrix(nx, ny, nz, h).toarray()
+
+
+def full_spectrum(system):
+    """All eigenpairs of the model Hamiltonian; rows of the vector array are u_k."""
+    vals, vecs = np.linalg.eigh(dense_h(system))
+    return vals, vecs.T.copy()
+
+
+def chi0_sum_over_states(system, omega):
+    """chi0(i omega) as an N_d x N_d matrix on grid values, from the sum over occupied i and
+    unoccupied a (Eq. 2 with f in {0,1}, both orderings of each pair combined):
+        chi0 = (4/h^3) sum_{i,a} (u_i u_a)(u_i u_a)^T (e_i - e_a) / ((e_i - e_a)^2 + omega^2)."""
+    vals, U = full_spectrum(system)
+    n_s = system.n_s
+    occ, un = U[:n_s], U[n_s:]
+    X = np.zeros((system.n_d, system.n_d))
+    for i in range(n_s):
+        d = vals[i] - vals[n_s:]
+        f = d / (d * d + omega * omega)
+        P = occ[i][None, :] * un                        # (N_un, N_d)
+        X += (P.T * f) @ P
+    return (4.0 / system.h ** 3) * X
+
+
+def nu_power_dense(nx, ny, nz, h, power):
+    """(4 pi)^p (-L_h)^{-p} by a dense symmetric eigendecomposition."""
+    mu, Q = np.linalg.eigh(dense_minus_laplacian(nx, ny, nz, h))
+    return (Q * ((4.0 * math.pi) ** power * mu ** (-power))) @ Q.T
+
+
+def chi_tilde_dense(system, omega):
+    nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5)
+    return nh @ chi0_sum_over_states(system, omega) @ nh
