@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the real-space RPA hot path (arXiv 2504.01816) on GB300.
+
+Workload (default): 40^3 Dirichlet grid, h = 0.4 bohr, 16 Gaussian wells, 16 occupied
+orbitals, 64 trial vectors, 8 Gauss-Legendre frequencies, mixed precision (complex FP32
+COCG inside FP64 refinement, COCG tol 1e-8).
+
+One step = one pass of the whole hot path over all frequencies: for each frequency from
+the highest to the lowest, one subspace iteration (nu^1/2 on V, 16 x 64 projected
+Sternheimer solves, drho, nu^1/2, projection C = V^T R, Rayleigh-Ritz, E_c,m, overlap,
+Cholesky, orthonormalisation), the subspace carried to the next frequency, then E_c.
+That is 8192 Sternheimer solves per step.  The metric is Sternheimer solves per second
+(whole job); ms_per_step is the time of one such pass.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RPA E_c time-to-solution & Sternheimer solves/s, mixed vs FP64 at 1e-5 Ha"
+UNIT = "Sternheimer solves/s"
+L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mixed40")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tts", action="store_true", help="also time E_c to convergence (eps_c 1e-5 Ha/atom)")
+    ap.add_argument("--fp64-compare", action="store_true", help="also time one step of the plain FP64 form")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"rpa_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def cpu_baseline(w, n_solves_target=128, budget_s=25.0):
+    """The FP64 oracle as it stands, on this host's cores: a bounded sample of the same
+    workload (for each frequency, the 16 Sternheimer solves of one trial vector)."""
+    import numpy as np
+    import oracle
+    import synth
+    s = w.system
+    o = oracle.Oracle.from_system(s)
+    V = synth.trial_vectors(w.seed, w.n_r, s.n_d)
+    omegas, _ = oracle.frequency_quadrature(w.n_omega)
+    stats = oracle.SolveStats()
+    t0 = time.perf_counter()
+    cols = 0
+    for m in range(w.n_omega - 1, -1, -1):
+        vt = o.coulomb.apply(V[m % w.n_r:m % w.n_r + 1], 0.5)
+        o.chi0(vt, omegas[m], w.tol, stats=stats)
+        cols += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    n = stats.n_solves()
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} Sternheimer solves (1 trial vector x {s.n_s} orbitals at each of {cols} "
+                      f"frequencies) of the {w.system.nx}^3 workload, FP64, tol {w.tol:g}, "
+                      f"{stats.total_iterations()} COCG iterations, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    import oracle
+    w = synth.workload(args.workload, tol=args.tol)
+    s = w.system
+    o = oracle.Oracle.from_system(s)
+    V = synth.trial_vectors(w.seed, w.n_r, s.n_d)
+    omegas, _ = oracle.frequency_quadrature(w.n_omega)
+
+    def step(k):
+        st = oracle.SolveStats()
+        m = w.n_omega - 1 - (k % w.n_omega)
+        vt = o.coulomb.apply(V[k % w.n_r:k % w.n_r + 1], 0.5)
+        o.chi0(vt, omegas[m], w.tol, stats=st)
+        return st.n_solves()
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    n = 0
+    for k in range(args.steps):
+        n += step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    val = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {s.nx}^3 grid h={s.h}, N_s={s.n_s}, N_r={w.n_r}, "
+                                   f"N_omega={w.n_omega}; one step = the {s.n_s} Sternheimer solves of one "
+                                   f"trial vector at one frequency (frequencies cycled)",
+                       "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{n} solves over {args.steps} steps"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_01816_gb300 as rpa
+    import synth
+
+    w = synth.workload(args.workload, tol=args.tol)
+    s = w.system
+    V0h = synth.trial_vectors(w.seed, w.n_r, s.n_d)
+    dev = torch.device("cuda", local)
+    V0 = torch.as_tensor(V0h, device=dev)
+    opts = rpa.default_options()
+    opts.prec = rpa.RPA_MIXED if args.prec == "mixed" else rpa.RPA_FP64
+    opts.tol = args.tol
+    opts.n_omega = w.n_omega
+    opts.fixed_subspace_iters = 1
+    opts.n_atoms = s.n_atoms
+    opts.profile = 1
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = rpa.Context.from_system(s, opts)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ctx.ec(V0)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    times, solves, kstats = [], 0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # evict L2 between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.ec(V0)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        solves += res.stats["sternheimer_solves"]
+        kstats.append(res.stats)
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms, solves], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms, solves = float(tmax[0]), int(t[1])
+    value = solves / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host V0 -> device, E_c, results back to the host
+    V0_pin = torch.from_numpy(V0h).pin_memory()
+    V0_dev = torch.empty_like(V0)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        V0_dev.copy_(V0_pin, non_blocking=True)
+        r = ctx.ec(V0_dev)                     # returns lambdas and energies on the host
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = {"value": r.stats["sternheimer_solves"] / statistics.median(e2e_times), "unit": UNIT,
+           "h2d_bytes_per_step": int(V0h.nbytes), "d2h_bytes_per_step": int(8 * (w.n_omega * w.n_r + 2 + w.n_omega))}
+
+    line = None
+    if rank == 0:
+        peaks = measured_peaks() or {}
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        # dominant kernel: the one with the largest summed device time in the timed steps
+        agg = {}
+        for st in kstats:
+            for k in st.get("kernels", []):
+                a = agg.setdefault(k["name"], {"ms": 0.0, "launches": 0, "bytes": 0.0})
+                a["ms"] += k["ms"]
+                a["launches"] += k["launches"]
+                a["bytes"] += k["bytes"]
+        roofline = None
+        if agg:
+            name, a = max(agg.items(), key=lambda kv: kv[1]["ms"])
+            per_launch_s = a["ms"] / 1e3 / max(a["launches"], 1)
+            bytes_per_launch = a["bytes"] / max(a["launches"], 1)
+            achieved = bytes_per_launch / per_launch_s / 1e9
+            roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved / hbm, "traffic": None,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
+                        "share_of_step": a["ms"] / total_ms, "avg_launch_us": 1e6 * per_launch_s}
+        mean_iters = sum(st["cocg_iterations"] for st in kstats) / max(sum(st["sternheimer_solves"] for st in kstats), 1)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64+f64 (mixed)" if args.prec == "mixed" else "c128 (f64)", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {s.nx}^3 Dirichlet grid h={s.h} bohr, "
+                                       f"{s.n_atoms} Gaussian wells, N_s={s.n_s}, N_r={w.n_r}, N_omega={w.n_omega}, "
+                                       f"{args.prec}, COCG tol {args.tol:g}; step = 1 subspace iteration at every "
+                                       f"frequency ({s.n_s * w.n_r * w.n_omega} Sternheimer solves)",
+                           "l2": "flushed (512 MB write) between timed steps",
+                           "mean_cocg_iterations_per_solve": mean_iters,
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": int(sum(st.get("launches", 0) for st in kstats)),
+                "clocks": clk, "e2e": e2e, "roofline": roofline,
+                "e_c_per_atom_last_step": res.e_c_per_atom}
+    if args.fp64_compare and rank == 0:
+        o64 = rpa.default_options()
+        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "profile"):
+            setattr(o64, k, getattr(opts, k))
+        o64.prec = rpa.RPA_FP64
+        ctx.set_options(o64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = ctx.ec(V0)
+        e1.record(stream)
+        e1.synchronize()
+        line["fp64_form"] = {"value": r64.stats["sternheimer_solves"] / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                             "ms_per_step": e0.elapsed_time(e1),
+                             "max_abs_dlambda_vs_mixed": float(np.max(np.abs(r64.lambdas - res.lambdas))),
+                             "de_c_per_atom_vs_mixed": float(r64.e_c_per_atom - res.e_c_per_atom)}
+        ctx.set_options(opts)
+    if args.tts and rank == 0:
+        ot = rpa.default_options()
+        for k in ("prec", "tol", "n_omega", "n_atoms", "profile"):
+            setattr(ot, k, getattr(opts, k))
+        ot.eps_c = 1e-5
+        ot.fixed_subspace_iters = 0
+        ctx.set_options(ot)
+        t0 = time.perf_counter()
+        rt = ctx.ec(V0)
+        line["time_to_solution"] = {"seconds": time.perf_counter() - t0, "e_c_per_atom": rt.e_c_per_atom,
+                                    "eps_c_ha_per_atom": 1e-5,
+                                    "subspace_iterations": rt.stats["subspace_iterations"],
+                                    "sternheimer_solves": rt.stats["sternheimer_solves"]}
+        ctx.set_options(opts)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

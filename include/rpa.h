@@ -1,0 +1,169 @@
+/*
+ * rpa.h -- C interface of librpa, a single-GPU (GB300, sm_103a) implementation of the
+ * hot path of the real-space RPA correlation-energy method of B. Zhang, S. Shah,
+ * J. E. Pask, E. Chow and P. Suryanarayana, "Random Phase Approximation Correlation
+ * Energy using Real-Space Density Functional Perturbation Theory" (arXiv 2504.01816).
+ *
+ * Discrete model (the paper's Formulation and Implementation sections):
+ *   grid        nx*ny*nz points, spacing h, zero (Dirichlet) values outside the box;
+ *               point (i,j,k) at index i + nx*(j + ny*k).  N_d = nx*ny*nz.
+ *   H           -1/2 L_h + diag(V_loc); L_h the 12th-order centred FD Laplacian
+ *               (Section "Implementation": high-order centred finite differences,
+ *               matrix-free application).
+ *   orbitals    u_n, n < N_s, l2-orthonormal eigenvectors of H (u = psi h^{3/2}) with
+ *               eigenvalues eps_n (the ground state the paper reads from files).
+ *   nu^p        (4 pi)^p (-L_h)^{-p}, applied by the Kronecker-product formalism
+ *               (per-axis eigendecompositions of the 1D second-difference matrices;
+ *               Section "Implementation"; Poisson equation, Eq. 5).
+ *   chi0(iw) dV = (4/h^3) Re sum_n u_n (.) x_n,  (H - eps_n + i w) x_n = -P_c(u_n (.) dV),
+ *               P_c = I - U U^T  (Eqs. 7-9; the Galerkin initial guess of Section
+ *               "Implementation" removes exactly the occupied components that P_c removes).
+ *   E_c         (1/2pi) int_0^inf sum_{i<N_r} [log(1-lambda_i) + lambda_i] dw over the
+ *               lowest N_r eigenvalues lambda_i of nu^1/2 chi0 nu^1/2 (Eq. 10), by
+ *               subspace iteration with Rayleigh-Ritz (Algorithm 1) and Gauss-Legendre
+ *               frequencies mapped to [0, inf) by w = w0 (1+x)/(1-x).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_dev are device pointers on the current CUDA device; *_host are host
+ *     pointers.  The caller owns every buffer it passes; the library never frees, keeps or
+ *     aliases them beyond the call (rpa_setup copies what it needs).
+ *   - A block of K grid functions is an N_d x K column-major matrix of doubles: column c
+ *     starts at c*N_d.  Complex vectors are interleaved (re, im) doubles.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work
+ *     is enqueued on it; calls that return host results synchronise it.
+ *   - Every call returns an rpa_status; nothing throws across this interface.  On any
+ *     status other than RPA_OK, rpa_last_error() gives a message (thread-local).
+ *     RPA_ERR_NOT_CONVERGED still fills every output.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef RPA_H
+#define RPA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpa_ctx rpa_ctx;
+
+typedef enum {
+    RPA_OK = 0,
+    RPA_ERR_INVALID = 1,        /* bad argument (size, pointer, option) */
+    RPA_ERR_CUDA = 2,           /* a CUDA runtime error */
+    RPA_ERR_OOM = 3,            /* device allocation failed */
+    RPA_ERR_NOT_CONVERGED = 4,  /* a COCG solve hit maxit; outputs are still written */
+    RPA_ERR_BREAKDOWN = 5,      /* COCG breakdown: p^T A p or r^T r vanished */
+    RPA_ERR_NOT_SPD = 6         /* the overlap matrix R^T R is not positive definite */
+} rpa_status;
+
+typedef enum {
+    RPA_FP64 = 0,   /* plain form: complex FP64 COCG */
+    RPA_MIXED = 1   /* complex FP32 COCG inside FP64 iterative refinement */
+} rpa_precision;
+
+typedef struct {
+    int prec;                  /* rpa_precision */
+    double tol;                /* COCG: stop when ||b - A x||_2 <= tol ||b||_2 (Hermitian norm) */
+    int maxit;                 /* COCG: iteration limit per system (FP64) or per inner solve (mixed) */
+    int max_refine;            /* mixed: limit on FP64 refinement cycles per system */
+    double inner_tol;          /* mixed: relative residual reduction asked of each FP32 inner solve */
+    double eps_c;              /* subspace iteration: stop when |dE_c,m| <= eps_c * n_atoms / n_omega (Ha/atom) */
+    int n_omega;               /* Gauss-Legendre frequency count (<= 64) */
+    double omega0;             /* frequency map scale w0 (Ha) */
+    int max_subspace_iters;    /* subspace iteration limit per frequency */
+    int fixed_subspace_iters;  /* > 0: run exactly this many iterations per frequency */
+    int n_atoms;               /* divides eps_c and the reported per-atom energy */
+    int batch_systems;         /* Sternheimer systems in flight at once (0 = automatic) */
+    int profile;               /* != 0: time every launch of the COCG kernels with CUDA events and
+                                  count the grid points they process (filled into rpa_stats.prof_*) */
+} rpa_options;
+
+#define RPA_PROF_SLOTS 8
+
+typedef struct {
+    long long sternheimer_solves;   /* systems solved */
+    long long cocg_iterations;      /* COCG iterations summed over systems (inner ones for mixed) */
+    long long refinement_steps;     /* FP64 residual evaluations summed over systems (mixed) */
+    long long stencil_points;       /* grid points x stencil applications in COCG (work measure) */
+    int subspace_iterations[64];    /* per frequency, ascending omega */
+    double omegas[64];              /* frequency nodes, ascending */
+    double weights[64];             /* frequency weights */
+    double ms_coulomb;              /* device time per phase (CUDA events), milliseconds */
+    double ms_projection;           /* P_c coefficients and right-hand sides */
+    double ms_cocg;                 /* Sternheimer solves including refinement */
+    double ms_density;              /* drho accumulation */
+    double ms_subspace;             /* Gram/projection, Cholesky, Rayleigh-Ritz, rotation */
+    double ms_total;
+    int worst_status;               /* largest per-system COCG status seen */
+    /* with rpa_options.profile: one entry per COCG kernel (name, launches, summed device time,
+     * grid points processed, algorithmic bytes moved = points x the kernel's bytes per point) */
+    int prof_count;
+    char prof_name[RPA_PROF_SLOTS][32];
+    long long prof_launches[RPA_PROF_SLOTS];
+    double prof_ms[RPA_PROF_SLOTS];
+    double prof_points[RPA_PROF_SLOTS];
+    double prof_bytes[RPA_PROF_SLOTS];
+    long long launches;             /* kernels launched by the call (all of the library's kernels) */
+} rpa_stats;
+
+/* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
+ * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
+ * profile 0. */
+void rpa_default_options(rpa_options *opt);
+
+/* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).
+ * nx,ny,nz >= 1, h > 0, fd_order must be 12.  vloc_dev: N_d doubles.  psi_dev: N_d x n_s
+ * column-major, l2-orthonormal columns.  eps_host: n_s doubles.  opt may be NULL
+ * (defaults).  The library copies all inputs; the caller may free them on return.
+ * The per-axis eigendecompositions of the Kronecker Coulomb operator are computed here. */
+rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_order,
+                     const double *vloc_dev, const double *psi_dev, const double *eps_host,
+                     int n_s, const rpa_options *opt, void *stream);
+
+/* Replace the context's options (tolerances, precision, frequency count ...). */
+rpa_status rpa_set_options(rpa_ctx *ctx, const rpa_options *opt);
+
+/* out = nu^power in for ncols columns (N_d x ncols, column-major), with
+ * nu = 4 pi (-L_h)^{-1} (Poisson, Eq. 5) by the Kronecker-product formalism.  Any real
+ * power is accepted (0.5 and 1 are the ones the method uses).  in and out may alias. */
+rpa_status rpa_coulomb_apply(rpa_ctx *ctx, double power, const double *in_dev, double *out_dev,
+                             int ncols, void *stream);
+
+/* Solve nsys Sternheimer systems (H - eps_n + i omega) x_s = b_s (Eq. 9) by COCG, with n =
+ * orbital_idx_host[s].  rhs_dev: N_d x nsys real right-hand sides.  project != 0 replaces
+ * b_s by P_c b_s first (removes the occupied components, as the Galerkin initial guess
+ * does).  x_dev: N_d x nsys complex (interleaved), written.  iters_dev/status_dev: nsys
+ * ints on the device (iterations, per-system rpa_status), may be NULL.  Returns the worst
+ * per-system status. */
+rpa_status rpa_sternheimer_solve(rpa_ctx *ctx, double omega, const int *orbital_idx_host, int nsys,
+                                 const double *rhs_dev, int project, double *x_dev,
+                                 int *iters_dev, int *status_dev, void *stream);
+
+/* R = nu^1/2 chi0(i omega) nu^1/2 V (symmetric = 1) or R = nu chi0(i omega) V (symmetric = 0)
+ * for n_r columns (N_d x n_r, column-major).  One application of Algorithm 1's loop over
+ * trial vectors: Coulomb half-apply, N_s x n_r Sternheimer solves, drho accumulation,
+ * Coulomb half-apply.  V and R must not alias. */
+rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, double *R_dev, int n_r,
+                            int symmetric, void *stream);
+
+/* E_c by Algorithm 1 with Rayleigh-Ritz.  V0_dev: N_d x n_r starting vectors (need not be
+ * orthonormal; they are orthonormalised through the Cholesky factor of V0^T V0).  Frequencies run from
+ * the highest to the lowest, the subspace carried over.  Outputs (host, each may be NULL):
+ * lambdas_host n_omega x n_r (row m = ascending Ritz values of the last iteration at the
+ * m-th frequency, ascending omega); ec_host[0] = E_c (Ha), ec_host[1] = E_c / n_atoms;
+ * ec_per_omega_host n_omega weighted contributions (w_m/2pi) sum_i g(lambda_i); stats. */
+rpa_status rpa_ec(rpa_ctx *ctx, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host,
+                  double *ec_per_omega_host, rpa_stats *stats, void *stream);
+
+/* Release the context and its device workspaces.  NULL is ignored. */
+void rpa_destroy(rpa_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *rpa_last_error(void);
+
+/* Library version string. */
+const char *rpa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPA_H */

@@ -1,0 +1,461 @@
+// C entry points of librpa (declared in include/rpa.h) and the subspace-iteration driver of
+// Algorithm 1 (arXiv 2504.01816) with Rayleigh-Ritz energies.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace rpa {
+
+static thread_local std::string g_last_error;
+
+void fail(rpa_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    throw Error{st, buf};
+}
+
+void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    const rpa_status st = (e == cudaErrorMemoryAllocation) ? RPA_ERR_OOM : RPA_ERR_CUDA;
+    fail(st, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+void *DevBuf::ensure(size_t need) {
+    if (need <= bytes && ptr) return ptr;
+    release();
+    size_t want = std::max(need, (size_t)256);
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        (void)cudaGetLastError();
+        fail(RPA_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    bytes = want;
+    return ptr;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+Ctx::~Ctx() {
+    cudaFree(vloc64);
+    cudaFree(vloc32);
+    cudaFree(psi64);
+    cudaFree(eps_dev);
+    for (double *q : Q) cudaFree(q);
+    cudaFree(lam);
+    for (DevBuf *b : {&cocg_state, &cocg_partials, &sys_state, &rhs, &pc_coef, &coul_tmp, &blockA, &blockB,
+                      &blockC, &blockD, &small, &slot_idx, &dense_scratch})
+        b->release();
+    if (h_state) cudaFreeHost(h_state);
+    if (h_count) cudaFreeHost(h_count);
+    cudaFree(d_count);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cudaFree(d_prof_points);
+}
+
+int prof_slot(Ctx &c, const char *name) {
+    for (int i = 0; i < c.stats.prof_count; ++i)
+        if (std::strncmp(c.stats.prof_name[i], name, 31) == 0) return i;
+    if (c.stats.prof_count >= RPA_PROF_SLOTS) return RPA_PROF_SLOTS - 1;
+    const int i = c.stats.prof_count++;
+    std::strncpy(c.stats.prof_name[i], name, 31);
+    c.stats.prof_name[i][31] = 0;
+    return i;
+}
+
+namespace {
+
+__global__ void k_to_float(const double *in, float *out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+void validate_options(const rpa_options &o) {
+    if (o.prec != RPA_FP64 && o.prec != RPA_MIXED) fail(RPA_ERR_INVALID, "prec must be RPA_FP64 or RPA_MIXED");
+    if (!(o.tol > 0.0) || !(o.tol < 1.0)) fail(RPA_ERR_INVALID, "tol must be in (0, 1)");
+    if (o.maxit < 1) fail(RPA_ERR_INVALID, "maxit must be >= 1");
+    if (o.max_refine < 1) fail(RPA_ERR_INVALID, "max_refine must be >= 1");
+    if (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0)) fail(RPA_ERR_INVALID, "inner_tol must be in (0, 1)");
+    if (!(o.eps_c >= 0.0)) fail(RPA_ERR_INVALID, "eps_c must be >= 0");
+    if (o.n_omega < 1 || o.n_omega > kMaxOmega) fail(RPA_ERR_INVALID, "n_omega must be in [1, %d]", kMaxOmega);
+    if (!(o.omega0 > 0.0)) fail(RPA_ERR_INVALID, "omega0 must be > 0");
+    if (o.max_subspace_iters < 1) fail(RPA_ERR_INVALID, "max_subspace_iters must be >= 1");
+    if (o.fixed_subspace_iters < 0) fail(RPA_ERR_INVALID, "fixed_subspace_iters must be >= 0");
+    if (o.n_atoms < 1) fail(RPA_ERR_INVALID, "n_atoms must be >= 1");
+    if (o.batch_systems < 0) fail(RPA_ERR_INVALID, "batch_systems must be >= 0");
+}
+
+// Gauss-Legendre nodes and weights on (-1, 1) by Newton iteration on P_n, then the map
+// omega = w0 (1+x)/(1-x), weight = 2 w0 w / (1-x)^2.  Ascending omega.
+void frequency_rule(int n, double w0, double *om, double *wt) {
+    std::vector<double> x(n), w(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // recompute the derivative at the converged root
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    // roots come out descending in x; emit ascending
+    for (int i = 0; i < n; ++i) {
+        const double xi = x[n - 1 - i], wi = w[n - 1 - i];
+        om[i] = w0 * (1.0 + xi) / (1.0 - xi);
+        wt[i] = 2.0 * w0 * wi / ((1.0 - xi) * (1.0 - xi));
+    }
+}
+
+template <typename F>
+rpa_status guarded(F &&f) {
+    try {
+        f();
+        g_last_error.clear();
+        return RPA_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return RPA_ERR_OOM;
+    } catch (...) {
+        g_last_error = "unexpected internal error";
+        return RPA_ERR_INVALID;
+    }
+}
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+float ms_between(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+// R = nu^1/2 chi0 nu^1/2 V (symmetric) or nu chi0 V.  tmp1, tmp2: ncols x nd scratch.
+int apply_nuchi0_impl(Ctx &c, double omega, const double *V, double *R, int ncols, int symmetric, double *tmp1,
+                      double *tmp2, cudaStream_t s) {
+    cudaEvent_t e[4];
+    for (auto &x : e) RPA_CUDA(cudaEventCreate(&x));
+    RPA_CUDA(cudaEventRecord(e[0], s));
+    const double *dv = V;
+    if (symmetric) {
+        coulomb_apply(c, 0.5, V, tmp1, ncols, s);
+        dv = tmp1;
+    }
+    RPA_CUDA(cudaEventRecord(e[1], s));
+    const int worst = chi0_apply(c, omega, dv, tmp2, ncols, s);
+    RPA_CUDA(cudaEventRecord(e[2], s));
+    coulomb_apply(c, symmetric ? 0.5 : 1.0, tmp2, R, ncols, s);
+    RPA_CUDA(cudaEventRecord(e[3], s));
+    RPA_CUDA(cudaEventSynchronize(e[3]));
+    c.stats.ms_coulomb += ms_between(e[0], e[1]) + ms_between(e[2], e[3]);
+    c.stats.ms_cocg += ms_between(e[1], e[2]);
+    for (auto &x : e) cudaEventDestroy(x);
+    return worst;
+}
+
+}  // namespace
+}  // namespace rpa
+
+using namespace rpa;
+
+extern "C" {
+
+void rpa_default_options(rpa_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->prec = RPA_FP64;
+    o->tol = 1e-8;
+    o->maxit = 20000;
+    o->max_refine = 20;
+    o->inner_tol = 1e-4;
+    o->eps_c = 1e-5;
+    o->n_omega = 8;
+    o->omega0 = 1.0;
+    o->max_subspace_iters = 100;
+    o->fixed_subspace_iters = 0;
+    o->n_atoms = 1;
+    o->batch_systems = 0;
+    o->profile = 0;
+}
+
+const char *rpa_last_error(void) { return g_last_error.c_str(); }
+
+const char *rpa_version(void) { return "librpa 0.1 (sm_103a)"; }
+
+rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_order, const double *vloc_dev,
+                     const double *psi_dev, const double *eps_host, int n_s, const rpa_options *opt, void *stream) {
+    return guarded([&] {
+        if (!out) fail(RPA_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        if (nx < 1 || ny < 1 || nz < 1) fail(RPA_ERR_INVALID, "grid dimensions must be >= 1");
+        if (!(h > 0.0)) fail(RPA_ERR_INVALID, "h must be > 0");
+        if (fd_order != 2 * kRadius) fail(RPA_ERR_INVALID, "fd_order must be %d", 2 * kRadius);
+        if (n_s < 1) fail(RPA_ERR_INVALID, "n_s must be >= 1");
+        if (!vloc_dev || !psi_dev || !eps_host) fail(RPA_ERR_INVALID, "NULL input pointer");
+        const long long nd = (long long)nx * ny * nz;
+        if (n_s >= nd) fail(RPA_ERR_INVALID, "n_s must be smaller than the number of grid points");
+        if (nd >= (1LL << 31)) fail(RPA_ERR_INVALID, "grids of 2^31 points or more are not supported");
+        rpa_options o;
+        rpa_default_options(&o);
+        if (opt) o = *opt;
+        validate_options(o);
+        cudaStream_t s = as_stream(stream);
+        auto *ctx = new rpa_ctx();
+        Ctx &c = ctx->impl;
+        try {
+            RPA_CUDA(cudaGetDevice(&c.device));
+            c.nx = nx; c.ny = ny; c.nz = nz; c.nd = nd; c.h = h; c.ns = n_s; c.opt = o;
+            // centred weights of order 12: w_k = 2(-1)^{k+1}(p!)^2/(k^2 (p-k)!(p+k)!), w_0 = -2 sum 1/k^2
+            double fact[2 * kRadius + 1];
+            fact[0] = 1.0;
+            for (int i = 1; i <= 2 * kRadius; ++i) fact[i] = fact[i - 1] * i;
+            double w0 = 0.0;
+            for (int k = 1; k <= kRadius; ++k) {
+                const double wk = 2.0 * ((k & 1) ? 1.0 : -1.0) * fact[kRadius] * fact[kRadius] /
+                                  ((double)k * k * fact[kRadius - k] * fact[kRadius + k]);
+                c.coef.a[k] = -wk / (2.0 * h * h);
+                w0 -= 2.0 / ((double)k * k);
+            }
+            c.coef.a[0] = -w0 / (2.0 * h * h);
+            c.eps.assign(eps_host, eps_host + n_s);
+            RPA_CUDA(cudaMalloc(&c.vloc64, sizeof(double) * nd));
+            RPA_CUDA(cudaMalloc(&c.vloc32, sizeof(float) * nd));
+            RPA_CUDA(cudaMalloc(&c.psi64, sizeof(double) * nd * n_s));
+            RPA_CUDA(cudaMalloc(&c.eps_dev, sizeof(double) * n_s));
+            RPA_CUDA(cudaMemcpyAsync(c.vloc64, vloc_dev, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s));
+            RPA_CUDA(cudaMemcpyAsync(c.psi64, psi_dev, sizeof(double) * nd * n_s, cudaMemcpyDeviceToDevice, s));
+            RPA_CUDA(cudaMemcpyAsync(c.eps_dev, eps_host, sizeof(double) * n_s, cudaMemcpyHostToDevice, s));
+            k_to_float<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(c.vloc64, c.vloc32, nd);
+            RPA_LAUNCH("setup");
+            RPA_CUDA(cudaMallocHost((void **)&c.h_count, 8 * sizeof(int)));
+            RPA_CUDA(cudaMalloc(&c.d_count, sizeof(int)));
+            RPA_CUDA(cudaMalloc(&c.d_prof_points, sizeof(unsigned long long) * RPA_PROF_SLOTS));
+            RPA_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+            {
+                const char *g = std::getenv("RPA_GRAPHS");
+                c.use_graphs = !(g && g[0] == '0');
+            }
+            RPA_CUDA(cudaStreamSynchronize(s));
+            coulomb_setup(c);
+        } catch (...) {
+            delete ctx;
+            throw;
+        }
+        *out = ctx;
+    });
+}
+
+rpa_status rpa_set_options(rpa_ctx *ctx, const rpa_options *opt) {
+    return guarded([&] {
+        if (!ctx || !opt) fail(RPA_ERR_INVALID, "NULL argument");
+        validate_options(*opt);
+        ctx->impl.opt = *opt;
+    });
+}
+
+void rpa_destroy(rpa_ctx *ctx) { delete ctx; }
+
+rpa_status rpa_coulomb_apply(rpa_ctx *ctx, double power, const double *in_dev, double *out_dev, int ncols,
+                             void *stream) {
+    return guarded([&] {
+        if (!ctx || !in_dev || !out_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        if (ncols < 0) fail(RPA_ERR_INVALID, "ncols must be >= 0");
+        if (!std::isfinite(power)) fail(RPA_ERR_INVALID, "power must be finite");
+        coulomb_apply(ctx->impl, power, in_dev, out_dev, ncols, as_stream(stream));
+        RPA_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    });
+}
+
+rpa_status rpa_sternheimer_solve(rpa_ctx *ctx, double omega, const int *orbital_idx_host, int nsys,
+                                 const double *rhs_dev, int project, double *x_dev, int *iters_dev,
+                                 int *status_dev, void *stream) {
+    int worst = 0;
+    rpa_status st = guarded([&] {
+        if (!ctx || !orbital_idx_host || !rhs_dev || !x_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        if (nsys < 0) fail(RPA_ERR_INVALID, "nsys must be >= 0");
+        if (!std::isfinite(omega)) fail(RPA_ERR_INVALID, "omega must be finite");
+        if (nsys == 0) return;
+        Ctx &c = ctx->impl;
+        cudaStream_t s = as_stream(stream);
+        std::vector<int> it(nsys), stv(nsys);
+        worst = project ? sternheimer_batch_projected(c, omega, orbital_idx_host, nsys, rhs_dev, x_dev, &it, &stv, s)
+                        : sternheimer_batch(c, omega, orbital_idx_host, nsys, rhs_dev, x_dev, &it, &stv, s);
+        if (iters_dev) RPA_CUDA(cudaMemcpyAsync(iters_dev, it.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+        if (status_dev) RPA_CUDA(cudaMemcpyAsync(status_dev, stv.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+        RPA_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st != RPA_OK) return st;
+    if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
+    return (rpa_status)worst;
+}
+
+rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, double *R_dev, int n_r, int symmetric,
+                            void *stream) {
+    int worst = 0;
+    rpa_status st = guarded([&] {
+        if (!ctx || !V_dev || !R_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        if (n_r < 0) fail(RPA_ERR_INVALID, "n_r must be >= 0");
+        if (!std::isfinite(omega)) fail(RPA_ERR_INVALID, "omega must be finite");
+        if (V_dev == R_dev && n_r > 0) fail(RPA_ERR_INVALID, "V and R must not alias");
+        if (n_r == 0) return;
+        Ctx &c = ctx->impl;
+        cudaStream_t s = as_stream(stream);
+        const size_t blk = sizeof(double) * (size_t)n_r * c.nd;
+        double *t1 = (double *)c.blockA.ensure(blk);
+        double *t2 = (double *)c.blockB.ensure(blk);
+        worst = apply_nuchi0_impl(c, omega, V_dev, R_dev, n_r, symmetric, t1, t2, s);
+        RPA_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st != RPA_OK) return st;
+    if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
+    return (rpa_status)worst;
+}
+
+rpa_status rpa_ec(rpa_ctx *ctx, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host,
+                  double *ec_per_omega_host, rpa_stats *stats, void *stream) {
+    int worst = 0;
+    rpa_status st = guarded([&] {
+        if (!ctx || !V0_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        Ctx &c = ctx->impl;
+        if (n_r < 1 || n_r > c.nd) fail(RPA_ERR_INVALID, "n_r must be in [1, N_d]");
+        if (n_r > 1024) fail(RPA_ERR_INVALID, "n_r above 1024 is not supported");
+        cudaStream_t s = as_stream(stream);
+        std::memset(&c.stats, 0, sizeof c.stats);
+        const rpa_options &o = c.opt;
+        const int nw = o.n_omega;
+        double om[kMaxOmega], wt[kMaxOmega];
+        frequency_rule(nw, o.omega0, om, wt);
+        for (int m = 0; m < nw; ++m) {
+            c.stats.omegas[m] = om[m];
+            c.stats.weights[m] = wt[m];
+        }
+        const size_t blk = sizeof(double) * (size_t)n_r * c.nd;
+        double *V = (double *)c.blockA.ensure(blk);
+        double *R = (double *)c.blockB.ensure(blk);
+        double *T1 = (double *)c.blockC.ensure(blk);
+        double *T2 = (double *)c.blockD.ensure(blk);
+        const size_t nn = (size_t)n_r * n_r;
+        char *sm = (char *)c.small.ensure(sizeof(double) * (3 * nn + 4 * (size_t)n_r + 8) + 64);
+        double *Cm = (double *)sm;            // projection / overlap
+        double *Lm = Cm + nn;                 // inverse factor
+        double *Wm = Lm + nn;                 // copy for the eigen solve
+        double *lam = Wm + nn;
+        double *work = lam + n_r;             // 3 n_r
+        double *ecm_dev = work + 3 * (size_t)n_r;
+        int *info = (int *)(ecm_dev + 2);
+        std::vector<double> h_lam(n_r), h_scal(2);
+        int h_info = 0;
+
+        cudaEvent_t t0, t1;
+        RPA_CUDA(cudaEventCreate(&t0));
+        RPA_CUDA(cudaEventCreate(&t1));
+        RPA_CUDA(cudaEventRecord(t0, s));
+
+        // V = V0 L^{-T}, L L^T = V0^T V0 (rows: V = L^{-1} V0)
+        auto orthonormalize = [&](const double *X, double *Y) {
+            gram(X, n_r, X, n_r, c.nd, Cm, s, c.dense_scratch);
+            symmetrize(Cm, n_r, s);
+            cholesky(Cm, n_r, info, s);
+            RPA_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaStreamSynchronize(s));
+            if (h_info != 0) fail(RPA_ERR_NOT_SPD, "overlap matrix not positive definite (pivot %d)", h_info - 1);
+            tri_inverse(Cm, n_r, Lm, s);
+            combine_rows(Lm, n_r, n_r, X, c.nd, Y, s);
+        };
+        orthonormalize(V0_dev, V);
+
+        double ec = 0.0;
+        std::vector<double> ecm_all(nw, 0.0);
+        const double thr = o.eps_c * o.n_atoms / nw;
+        for (int m = nw - 1; m >= 0; --m) {
+            double ecm = 0.0;
+            int it = 0;
+            for (;;) {
+                const double ecm_old = ecm;
+                const int w = apply_nuchi0_impl(c, om[m], V, R, n_r, 1, T1, T2, s);
+                worst = std::max(worst, w);
+                cudaEvent_t a, b;
+                RPA_CUDA(cudaEventCreate(&a));
+                RPA_CUDA(cudaEventCreate(&b));
+                RPA_CUDA(cudaEventRecord(a, s));
+                // Rayleigh-Ritz: C = V^T R, eigenvalues, E_cm = (w_m / 2 pi) sum g(lambda)
+                gram(V, n_r, R, n_r, c.nd, Wm, s, c.dense_scratch);
+                symmetrize(Wm, n_r, s);
+                sym_eigvals(Wm, n_r, lam, work, wt[m] / (2.0 * M_PI), ecm_dev, s);
+                // orthonormalisation: M = R^T R = L L^T, V = R L^{-T}
+                orthonormalize(R, V);
+                RPA_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * n_r, cudaMemcpyDeviceToHost, s));
+                RPA_CUDA(cudaMemcpyAsync(h_scal.data(), ecm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+                RPA_CUDA(cudaEventRecord(b, s));
+                RPA_CUDA(cudaEventSynchronize(b));
+                c.stats.ms_subspace += ms_between(a, b);
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                ecm = h_scal[0];
+                ++it;
+                if (o.fixed_subspace_iters > 0) {
+                    if (it >= o.fixed_subspace_iters) break;
+                } else if (std::fabs(ecm - ecm_old) <= thr || it >= o.max_subspace_iters) {
+                    break;
+                }
+            }
+            c.stats.subspace_iterations[m] = it;
+            ecm_all[m] = ecm;
+            ec += ecm;
+            if (lambdas_host) std::memcpy(lambdas_host + (size_t)m * n_r, h_lam.data(), sizeof(double) * n_r);
+        }
+        RPA_CUDA(cudaEventRecord(t1, s));
+        RPA_CUDA(cudaEventSynchronize(t1));
+        c.stats.ms_total = ms_between(t0, t1);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        if (ec_host) {
+            ec_host[0] = ec;
+            ec_host[1] = ec / o.n_atoms;
+        }
+        if (ec_per_omega_host) std::memcpy(ec_per_omega_host, ecm_all.data(), sizeof(double) * nw);
+        if (stats) *stats = c.stats;
+    });
+    if (st != RPA_OK) return st;
+    if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
+    return (rpa_status)worst;
+}
+
+}  // extern "C"

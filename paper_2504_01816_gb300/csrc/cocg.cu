@@ -1,0 +1,1118 @@
+// Batched COCG for the Sternheimer systems (H - eps_n + i omega) x = b of the real-space RPA
+// method (arXiv 2504.01816: Sternheimer equation, Eq. 9; COCG, Section "Implementation").
+//
+// Persistent slot queue.  A fixed set of S slots holds the systems in flight; each slot owns
+// its Krylov vectors and a small state record.  All systems of a call wait in a queue; when
+// a slot's system is solved its contribution is retired (drho accumulated, or x copied out)
+// and the slot takes the next system.  S is chosen so that the vectors touched every
+// iteration fit in the 126 MB L2, so the Krylov iteration runs out of L2 instead of HBM.
+//
+// One COCG iteration is three kernels over all (slot, chunk) work items (fixed grid,
+// grid-stride; items of idle slots are skipped in a few instructions):
+//   k_cocg_p:  rho = r^T r and ||r|| from the previous partial sums (fixed order), convergence
+//              test, beta = rho / rho_old, p = r + beta p
+//   k_cocg_a:  q = (H - eps_n + i omega) p, partial sums of p^T q
+//   k_cocg_b:  alpha = rho / p^T q, x += alpha p, r -= alpha q, partial sums of r^T r, ||r||^2
+// Reductions are deterministic: every block writes its own partial sums; consumers add them in
+// block order.  Between groups of iterations ("epochs") maintenance kernels refine, retire,
+// refill and load slots.
+//
+// Plain form:  complex FP64 COCG to ||r|| <= tol ||b||.
+// Mixed form:  FP64 iterative refinement around complex FP32 COCG: r64 = b - A x64 in FP64,
+//              FP32 COCG for A d = r64 to a relative reduction inner_tol, x64 += d, repeat until
+//              ||r64|| <= tol ||b||.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "internal.cuh"
+
+namespace rpa {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPPT = 8;
+constexpr int kChunk = kThreads * kPPT;   // grid points per work item
+constexpr int kEpoch = 8;                 // COCG iterations between maintenance passes (even)
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+enum Phase : int { kEmpty = 0, kInner = 1, kInnerDone = 2, kFinished = 3, kLoading = 4 };
+
+struct Slot {
+    double rho_re[2], rho_im[2];    // r^T r of the last two iterations (by parity of the iteration)
+    double alpha_re, alpha_im, beta_re, beta_im;
+    double shift_re, shift_im;
+    double bnorm, ref_norm, rnorm;
+    int phase, sys, n, j;
+    int iters, total_iters, refines, status;
+};
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+
+struct Grid3 {
+    int nx, ny, nz;
+    long long nd;
+};
+
+template <typename T> struct Coef {
+    T a[kRadius + 1];
+};
+
+template <typename T> Coef<T> cast_coef(const StencilCoef &c) {
+    Coef<T> r;
+    for (int k = 0; k <= kRadius; ++k) r.a[k] = (T)c.a[k];
+    return r;
+}
+
+// Everything the kernels need, passed by value.
+struct Params {
+    Slot *slots;
+    int S, nblk;       // items per slot of the streaming kernels
+    int nparta;        // partial sums per slot written by the stencil kernel (its tiles)
+    Grid3 g;
+    double *partA;     // [S][nblk][2]   p^T q
+    double *partB;     // [S][nblk][3]   r^T r (re, im), ||r||^2
+    int *list;         // [2][S] active slots of the current iteration (by parity)
+    int *cnt;          // [2]    their number
+    int mixed;
+    double tol, inner_tol;
+    int maxit, max_refine;
+    int *head;         // next system of the queue
+    int nsys;
+    int *count;        // slots busy + systems waiting (for the host)
+    int *sys_iters, *sys_status, *sys_refines;
+    unsigned long long *prof;   // grid points processed by k_cocg_p/_a/_b (nullptr = off)
+};
+
+__device__ __forceinline__ void prof_add(const Params &P, int which, int chunk) {
+    if (P.prof && threadIdx.x == 0) {
+        const long long left = P.g.nd - (long long)chunk * kChunk;
+        atomicAdd(P.prof + which, (unsigned long long)(left < kChunk ? left : kChunk));
+    }
+}
+
+// Sum N doubles over the block; the result is valid in thread 0.  Fixed order.
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N]) {
+    __shared__ double sh[N][kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    __syncthreads();   // sh may still be read from the previous item
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < N; ++c) sh[c][warp] = v[c];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            v[c] = lane < kWarpsPerBlock ? sh[c][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        }
+    }
+}
+
+// Sum one slot's per-item partials with one warp (fixed order); result in every lane.
+template <int N, int STRIDE>
+__device__ __forceinline__ void warp_slot_sum(const double *part, int nblk, double (&out)[N]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < N; ++c) out[c] = 0.0;
+    for (int b = lane; b < nblk; b += 32)
+#pragma unroll
+        for (int c = 0; c < N; ++c) out[c] += part[(long long)b * STRIDE + c];
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) out[c] += __shfl_xor_sync(0xffffffffu, out[c], o);
+}
+
+__device__ __forceinline__ void coords(long long idx, const Grid3 &g, int &i, int &j, int &k) {
+    const long long pl = (long long)g.nx * g.ny;
+    k = (int)(idx / pl);
+    const long long rem = idx - (long long)k * pl;
+    j = (int)(rem / g.nx);
+    i = (int)(rem - (long long)j * g.nx);
+}
+
+// (H + sigma) p at one point: diagonal (3 a0 + V + sigma) plus 6 x radius neighbours, zero
+// outside the box.
+template <typename T, typename C>
+__device__ __forceinline__ C stencil_at(const C *__restrict__ p, long long idx, int i, int j, int k,
+                                        const Grid3 &g, const Coef<T> &cf, T dre, T dim) {
+    const C c = p[idx];
+    T re = dre * c.x - dim * c.y;
+    T im = dre * c.y + dim * c.x;
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+#pragma unroll
+    for (int s = 1; s <= kRadius; ++s) {
+        T ar = 0, ai = 0;
+        if (i - s >= 0) { C u = p[idx - s]; ar += u.x; ai += u.y; }
+        if (i + s < g.nx) { C u = p[idx + s]; ar += u.x; ai += u.y; }
+        if (j - s >= 0) { C u = p[idx - s * sy]; ar += u.x; ai += u.y; }
+        if (j + s < g.ny) { C u = p[idx + s * sy]; ar += u.x; ai += u.y; }
+        if (k - s >= 0) { C u = p[idx - s * sz]; ar += u.x; ai += u.y; }
+        if (k + s < g.nz) { C u = p[idx + s * sz]; ar += u.x; ai += u.y; }
+        re += cf.a[s] * ar;
+        im += cf.a[s] * ai;
+    }
+    C out;
+    out.x = re;
+    out.y = im;
+    return out;
+}
+
+// ---------------------------------------------------------------------------------------------
+// COCG iteration: two per-slot scalar kernels (one warp per slot, the only writers of the slot
+// state during the iteration) and three kernels over the active (slot, chunk) items.
+// ---------------------------------------------------------------------------------------------
+// rho = r^T r and ||r|| from the partial sums of the last update; convergence test; beta;
+// append the slot to the active list of this iteration.
+__global__ void k_beta(Params P, int par) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= P.S) return;
+    Slot &sl = P.slots[w];
+    if (sl.phase != kInner) return;
+    double v[3];
+    warp_slot_sum<3, 3>(P.partB + (long long)w * P.nblk * 3, P.nblk, v);
+    if (lane != 0) return;
+    const int k = sl.iters;
+    const double rn = sqrt(v[2]);
+    const double thr = P.mixed ? fmax(P.inner_tol * sl.ref_norm, 0.3 * P.tol * sl.bnorm) : P.tol * sl.bnorm;
+    const bool conv = rn <= thr;
+    const bool bad = !isfinite(rn) || !(v[0] * v[0] + v[1] * v[1] > 0.0);
+    sl.rnorm = rn;
+    if (conv || k >= P.maxit || bad) {
+        if (P.mixed) {
+            if (bad && !conv) sl.status = RPA_ERR_BREAKDOWN;
+            sl.phase = kInnerDone;
+        } else {
+            sl.status = conv ? RPA_OK : (bad ? RPA_ERR_BREAKDOWN : RPA_ERR_NOT_CONVERGED);
+            sl.phase = kFinished;
+        }
+        return;
+    }
+    double br = 0.0, bi = 0.0;
+    if (k > 0) {
+        const double orr = sl.rho_re[(k - 1) & 1], ori = sl.rho_im[(k - 1) & 1];
+        const double den = orr * orr + ori * ori;
+        br = (v[0] * orr + v[1] * ori) / den;
+        bi = (v[1] * orr - v[0] * ori) / den;
+    }
+    sl.rho_re[k & 1] = v[0];
+    sl.rho_im[k & 1] = v[1];
+    sl.beta_re = br;
+    sl.beta_im = bi;
+    const int pos = atomicAdd(P.cnt + par, 1);
+    P.list[par * P.S + pos] = w;
+}
+
+// alpha = rho / p^T q for the active slots; breakdown retires the slot.  Also clears the other
+// parity's list counter for the next iteration.
+__global__ void k_alpha(Params P, int par) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.cnt[par ^ 1] = 0;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= P.cnt[par]) return;
+    const int s = P.list[par * P.S + w];
+    Slot &sl = P.slots[s];
+    double mu[2];
+    warp_slot_sum<2, 2>(P.partA + (long long)s * P.nparta * 2, P.nparta, mu);
+    if (lane != 0) return;
+    const int k = sl.iters;
+    const double den = mu[0] * mu[0] + mu[1] * mu[1];
+    if (!(den > 0.0) || !isfinite(den)) {
+        sl.status = RPA_ERR_BREAKDOWN;
+        sl.phase = P.mixed ? kInnerDone : kFinished;
+        return;
+    }
+    const double rr = sl.rho_re[k & 1], ri = sl.rho_im[k & 1];
+    sl.alpha_re = (rr * mu[0] + ri * mu[1]) / den;
+    sl.alpha_im = (ri * mu[0] - rr * mu[1]) / den;
+}
+
+// x += alpha p ; r -= alpha q ; partial sums of r^T r and ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename Cx<T>::t *__restrict__ x,
+                                                     typename Cx<T>::t *__restrict__ r,
+                                                     const typename Cx<T>::t *__restrict__ pbuf, long long pstride,
+                                                     const typename Cx<T>::t *__restrict__ q) {
+    using C = typename Cx<T>::t;
+    const long long items = (long long)P.cnt[par] * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = P.list[par * P.S + (int)(it / P.nblk)], chunk = (int)(it % P.nblk);
+        Slot &sl = P.slots[s];
+        if (sl.phase != kInner) continue;      // breakdown in k_alpha (stable during this kernel)
+        const T ar = (T)sl.alpha_re, ai = (T)sl.alpha_im;
+        const long long off = (long long)s * P.g.nd;
+        const C *p = pbuf + (long long)((sl.iters + 1) & 1) * pstride;   // the new direction
+        double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            if (idx < P.g.nd) {
+                const C pv = p[off + idx], qv = q[off + idx];
+                C xv = x[off + idx], rv = r[off + idx];
+                xv.x += ar * pv.x - ai * pv.y;
+                xv.y += ar * pv.y + ai * pv.x;
+                rv.x -= ar * qv.x - ai * qv.y;
+                rv.y -= ar * qv.y + ai * qv.x;
+                x[off + idx] = xv;
+                r[off + idx] = rv;
+                v[0] += (double)(rv.x * rv.x - rv.y * rv.y);
+                v[1] += (double)(2 * rv.x * rv.y);
+                v[2] += (double)(rv.x * rv.x + rv.y * rv.y);
+            }
+        }
+        block_sum<3>(v);
+        if (threadIdx.x == 0) {
+            double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
+            o[0] = v[0];
+            o[1] = v[1];
+            o[2] = v[2];
+            if (chunk == 0) {
+                sl.iters += 1;
+                sl.total_iters += 1;
+            }
+        }
+        prof_add(P, 2, chunk);
+    }
+}
+
+// Block-wide sum for any block size (<= 1024 threads); result valid in thread 0.  Fixed order.
+template <int N>
+__device__ __forceinline__ void block_sum_any(double (&v)[N]) {
+    __shared__ double sh[N][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < N; ++c) sh[c][warp] = v[c];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            v[c] = lane < nw ? sh[c][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        }
+    }
+}
+
+// xy tiling of the fused stencil kernel: a tile of tx x ty grid columns, one thread per column.
+struct Tiles {
+    int tx, ty, ntx, nty;
+};
+
+// Fused direction update and stencil (one COCG half-step), for the slots of the active list:
+//   p_new = r + beta p_old          (p is double-buffered per slot by iteration parity)
+//   q     = (H - eps_n + i omega) p_new ,  partial sums of p_new^T q
+// Work item = (slot, xy tile).  The block marches along z; each thread keeps the 13 values of
+// p_new on its own column (z-6 .. z+6) in registers, and the centre plane of the tile plus a
+// 6-point halo (computed from r and p_old, never read back from p_new) is staged in shared
+// memory for the x and y neighbours.  Values outside the box are zero.
+template <typename T>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_cocg_pa(Params P, int par, Tiles tl, const typename Cx<T>::t *__restrict__ r,
+                                                    typename Cx<T>::t *__restrict__ pbuf, long long pstride,
+                                                    typename Cx<T>::t *__restrict__ q, const T *__restrict__ vloc,
+                                                    Coef<T> cf) {
+    using C = typename Cx<T>::t;
+    extern __shared__ unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    constexpr int R = kRadius;
+    const int W = tl.tx + 2 * R;
+    const int lx = threadIdx.x % tl.tx, ly = threadIdx.x / tl.tx;
+    const int ntiles = tl.ntx * tl.nty;
+    const long long items = (long long)P.cnt[par] * ntiles;
+    const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz;
+    const int plane = nx * ny;                 // grid functions have < 2^31 points
+    const int nhalo = 2 * R * (tl.tx + tl.ty); // top/bottom (tx x R) and left/right (R x ty) strips
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = P.list[par * P.S + (int)(it / ntiles)], tile = (int)(it % ntiles);
+        const Slot &sl = P.slots[s];
+        const int k = sl.iters;
+        const T br = (T)sl.beta_re, bi = (T)sl.beta_im;
+        const T sre = (T)sl.shift_re, sim = (T)sl.shift_im;
+        const long long off = (long long)s * P.g.nd;
+        const C *__restrict__ rs = r + off;
+        const C *__restrict__ po = pbuf + (long long)(k & 1) * pstride + off;
+        C *__restrict__ pn = pbuf + (long long)((k + 1) & 1) * pstride + off;
+        C *__restrict__ qs = q + off;
+        const int x0 = (tile % tl.ntx) * tl.tx, y0 = (tile / tl.ntx) * tl.ty;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool own = gx < nx && gy < ny;
+        const int col = gy * nx + gx;
+        C qv[2 * R + 1];
+#pragma unroll
+        for (int m = 0; m < 2 * R + 1; ++m) {
+            const int z = m - R;
+            C v;
+            v.x = 0;
+            v.y = 0;
+            if (own && z >= 0 && z < nz) {
+                const C a = rs[col + z * plane], b = po[col + z * plane];
+                v.x = a.x + br * b.x - bi * b.y;
+                v.y = a.y + br * b.y + bi * b.x;
+            }
+            qv[m] = v;
+        }
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int z = 0; z < nz; ++z) {
+            __syncthreads();                                   // previous plane's readers are done
+            sm[(ly + R) * W + lx + R] = qv[R];
+            for (int e = threadIdx.x; e < nhalo; e += blockDim.x) {
+                int hx, hy;                                    // frame coordinates
+                if (e < 2 * R * tl.tx) {                       // top / bottom strips
+                    const int rr = e / tl.tx;
+                    hx = e - rr * tl.tx + R;
+                    hy = rr < R ? rr : tl.ty + rr;
+                } else {                                       // left / right strips
+                    const int e2 = e - 2 * R * tl.tx;
+                    const int cc = e2 / tl.ty;
+                    hy = e2 - cc * tl.ty + R;
+                    hx = cc < R ? cc : tl.tx + cc;
+                }
+                const int ax = x0 + hx - R, ay = y0 + hy - R;
+                C v;
+                v.x = 0;
+                v.y = 0;
+                if (ax >= 0 && ax < nx && ay >= 0 && ay < ny) {
+                    const int idx = z * plane + ay * nx + ax;
+                    const C a = rs[idx], b = po[idx];
+                    v.x = a.x + br * b.x - bi * b.y;
+                    v.y = a.y + br * b.y + bi * b.x;
+                }
+                sm[hy * W + hx] = v;
+            }
+            __syncthreads();
+            if (own) {
+                const int idx = col + z * plane;
+                const C c = qv[R];
+                const T dre = (T)3 * cf.a[0] + vloc[idx] + sre;
+                T re = dre * c.x - sim * c.y;
+                T im = dre * c.y + sim * c.x;
+                const C *cs = sm + (ly + R) * W + lx + R;
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    const C a1 = cs[-d], a2 = cs[d], a3 = cs[-d * W], a4 = cs[d * W], a5 = qv[R - d], a6 = qv[R + d];
+                    re += cf.a[d] * (((a1.x + a2.x) + (a3.x + a4.x)) + (a5.x + a6.x));
+                    im += cf.a[d] * (((a1.y + a2.y) + (a3.y + a4.y)) + (a5.y + a6.y));
+                }
+                C y;
+                y.x = re;
+                y.y = im;
+                qs[idx] = y;
+                pn[idx] = c;
+                acc0 += (double)(c.x * y.x - c.y * y.y);
+                acc1 += (double)(c.x * y.y + c.y * y.x);
+            }
+            // advance the column window
+#pragma unroll
+            for (int m = 0; m < 2 * R; ++m) qv[m] = qv[m + 1];
+            C v;
+            v.x = 0;
+            v.y = 0;
+            const int zn = z + R + 1;
+            if (own && zn < nz) {
+                const C a = rs[col + zn * plane], b = po[col + zn * plane];
+                v.x = a.x + br * b.x - bi * b.y;
+                v.y = a.y + br * b.y + bi * b.x;
+            }
+            qv[2 * R] = v;
+        }
+        double acc[2] = {acc0, acc1};
+        block_sum_any<2>(acc);
+        if (threadIdx.x == 0) {
+            double *o = P.partA + ((long long)s * P.nparta + tile) * 2;
+            o[0] = acc[0];
+            o[1] = acc[1];
+            if (P.prof) {
+                const long long w = (long long)min(tl.tx, nx - x0) * min(tl.ty, ny - y0) * nz;
+                atomicAdd(P.prof + 1, (unsigned long long)w);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Maintenance kernels (between epochs).  Slot phases do not change while these item kernels
+// run, so every thread of a block reads the same phase.
+// ---------------------------------------------------------------------------------------------
+// Mixed form, slots whose inner solve ended: x64 += d.
+__global__ void __launch_bounds__(kThreads) k_refine_x(Params P, double2 *__restrict__ x64, const float2 *__restrict__ d) {
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        if (P.slots[s].phase != kInnerDone) continue;
+        const long long off = (long long)s * P.g.nd;
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            if (idx < P.g.nd) {
+                double2 xv = x64[off + idx];
+                const float2 dv = d[off + idx];
+                xv.x += (double)dv.x;
+                xv.y += (double)dv.y;
+                x64[off + idx] = xv;
+            }
+        }
+    }
+}
+
+// Mixed form: r64 = b - (H + sigma) x64 in FP64; the next inner solve starts from d = 0,
+// r32 = r64, p = 0.  Partials (into partB): r32^T r32 and ||r64||^2.
+__global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double *__restrict__ b,
+                                                         const double2 *__restrict__ x64, float2 *__restrict__ d,
+                                                         float2 *__restrict__ r32, float2 *__restrict__ p32,
+                                                         const double *__restrict__ vloc, Coef<double> cf) {
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        const Slot &sl = P.slots[s];
+        if (sl.phase != kInnerDone) continue;
+        const double sre = sl.shift_re, sim = sl.shift_im;
+        const long long off = (long long)s * P.g.nd;
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            if (idx < P.g.nd) {
+                int i, j, k;
+                coords(idx, P.g, i, j, k);
+                const double dre = 3.0 * cf.a[0] + vloc[idx] + sre;
+                const double2 ax = stencil_at<double, double2>(x64 + off, idx, i, j, k, P.g, cf, dre, sim);
+                const double rr = b[off + idx] - ax.x, ri = -ax.y;
+                const float2 rf = make_float2((float)rr, (float)ri);
+                r32[off + idx] = rf;
+                d[off + idx] = make_float2(0.f, 0.f);
+                p32[off + idx] = make_float2(0.f, 0.f);         // direction buffer of iteration 0
+                v[0] += (double)rf.x * rf.x - (double)rf.y * rf.y;
+                v[1] += 2.0 * (double)rf.x * rf.y;
+                v[2] += rr * rr + ri * ri;
+            }
+        }
+        block_sum<3>(v);
+        if (threadIdx.x == 0) {
+            double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
+            o[0] = v[0];
+            o[1] = v[1];
+            o[2] = v[2];
+        }
+    }
+}
+
+// Per-slot transitions after a refinement or a load (one warp per slot).
+__global__ void k_state(Params P) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= P.S) return;
+    Slot &sl = P.slots[w];
+    const int ph = sl.phase;
+    if (ph != kInnerDone && ph != kLoading) return;
+    double v[3];
+    warp_slot_sum<3, 3>(P.partB + (long long)w * P.nblk * 3, P.nblk, v);
+    if (lane != 0) return;
+    const double rn = sqrt(v[2]);
+    if (ph == kLoading) {
+        sl.bnorm = rn;
+        sl.ref_norm = rn;
+        sl.rnorm = rn;
+        sl.iters = 0;
+        sl.total_iters = 0;
+        sl.refines = 0;
+        sl.status = RPA_OK;
+        sl.phase = (rn > 0.0) ? kInner : kFinished;
+        return;
+    }
+    // kInnerDone (mixed form): rn = ||b - A x64||
+    sl.refines += 1;
+    sl.rnorm = rn;
+    if (rn <= P.tol * sl.bnorm) {
+        sl.status = RPA_OK;
+        sl.phase = kFinished;
+    } else if (sl.status == RPA_ERR_BREAKDOWN) {
+        sl.phase = kFinished;
+    } else if (sl.refines >= P.max_refine || !isfinite(rn)) {
+        sl.status = RPA_ERR_NOT_CONVERGED;
+        sl.phase = kFinished;
+    } else {
+        sl.ref_norm = rn;
+        sl.iters = 0;
+        sl.phase = kInner;
+    }
+}
+
+// drho_j += (4/h^3) u_n (.) Re x64 for every finished slot, slots added in slot order.
+__global__ void k_retire_drho(Params P, const double2 *__restrict__ x64, const double *__restrict__ psi,
+                              double *__restrict__ drho, double scale) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P.g.nd;
+         idx += (long long)gridDim.x * blockDim.x)
+        for (int s = 0; s < P.S; ++s) {
+            const Slot &sl = P.slots[s];
+            if (sl.phase != kFinished) continue;
+            drho[(long long)sl.j * P.g.nd + idx] +=
+                scale * psi[(long long)sl.n * P.g.nd + idx] * x64[(long long)s * P.g.nd + idx].x;
+        }
+}
+
+// x_out[sys] = x64 for every finished slot.
+__global__ void k_retire_copy(Params P, const double2 *__restrict__ x64, double2 *__restrict__ xout) {
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        const Slot &sl = P.slots[s];
+        if (sl.phase != kFinished) continue;
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            if (idx < P.g.nd) xout[(long long)sl.sys * P.g.nd + idx] = x64[(long long)s * P.g.nd + idx];
+        }
+    }
+}
+
+// Finished slots report and empty; empty slots take the next systems in slot order (a block
+// scan keeps the assignment deterministic); count what is left.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_refill(Params P, const int *__restrict__ sys_n,
+                                                 const int *__restrict__ sys_j, const double *__restrict__ eps,
+                                                 double omega) {
+    __shared__ int wsum[32];
+    __shared__ int base_head, busy_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        base_head = *P.head;
+        busy_total = 0;
+        P.cnt[0] = 0;
+    }
+    __syncthreads();
+    for (int s0 = 0; s0 < P.S; s0 += blockDim.x) {
+        const int s = s0 + tid;
+        int want = 0;
+        Slot *sl = s < P.S ? P.slots + s : nullptr;
+        if (sl) {
+            if (sl->phase == kFinished) {
+                if (sl->sys >= 0) {
+                    P.sys_iters[sl->sys] = sl->total_iters;
+                    P.sys_status[sl->sys] = sl->status;
+                    P.sys_refines[sl->sys] = sl->refines;
+                }
+                sl->phase = kEmpty;
+                sl->sys = -1;
+            }
+            want = sl->phase == kEmpty;
+        }
+        // exclusive scan of want over the block
+        int x = want;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;    // inclusive prefix over warps
+        }
+        __syncthreads();
+        const int excl = x - want + (warp > 0 ? wsum[warp - 1] : 0);
+        const int total = wsum[(blockDim.x >> 5) - 1];
+        if (sl && want) {
+            const int q = base_head + excl;
+            if (q < P.nsys) {
+                sl->sys = q;
+                sl->n = sys_n[q];
+                sl->j = sys_j[q];
+                sl->shift_re = -eps[sl->n];
+                sl->shift_im = omega;
+                sl->status = RPA_OK;
+                sl->phase = kLoading;
+            }
+        }
+        const int busy = (sl && sl->phase != kEmpty) ? 1 : 0;
+        if (busy) atomicAdd(&busy_total, 1);
+        __syncthreads();
+        if (tid == 0) base_head = min(P.nsys, base_head + total);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *P.head = base_head;
+        *P.count = busy_total + (P.nsys - base_head);
+    }
+}
+
+// Load the right-hand side of every loading slot:
+//   b = sign * (base - sum_k T[sys][k] u_k),  base = u_n (.) vt_j (pair) or rhs[sys]
+// then x64 = 0 and the inner vectors start from r = b, x = 0, p = 0.  Partials: r^T r, ||b||^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_load(Params P, const double *__restrict__ psi, int ns,
+                                                   const double *__restrict__ vt, const double *__restrict__ rhs,
+                                                   const double *__restrict__ Tc, double sign, double *__restrict__ b,
+                                                   double2 *__restrict__ x64, typename Cx<T>::t *__restrict__ xin,
+                                                   typename Cx<T>::t *__restrict__ r, typename Cx<T>::t *__restrict__ p,
+                                                   long long pstride) {
+    using C = typename Cx<T>::t;
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        const Slot &sl = P.slots[s];
+        if (sl.phase != kLoading) continue;
+        const long long off = (long long)s * P.g.nd;
+        const double *tc = Tc ? Tc + (long long)sl.sys * ns : nullptr;
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            if (idx < P.g.nd) {
+                double base = vt ? psi[(long long)sl.n * P.g.nd + idx] * vt[(long long)sl.j * P.g.nd + idx]
+                                 : rhs[(long long)sl.sys * P.g.nd + idx];
+                if (tc)
+                    for (int k = 0; k < ns; ++k) base -= tc[k] * psi[(long long)k * P.g.nd + idx];
+                const double bv = sign * base;
+                b[off + idx] = bv;
+                x64[off + idx] = make_double2(0.0, 0.0);
+                C z;
+                z.x = (T)0;
+                z.y = (T)0;
+                C rv;
+                rv.x = (T)bv;
+                rv.y = (T)0;
+                if ((const void *)xin != (const void *)x64) xin[off + idx] = z;
+                r[off + idx] = rv;
+                p[off + idx] = z;
+                p[pstride + off + idx] = z;
+                v[0] += (double)rv.x * rv.x;
+                v[2] += bv * bv;
+            }
+        }
+        block_sum<3>(v);
+        if (threadIdx.x == 0) {
+            double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
+            o[0] = v[0];
+            o[1] = v[1];
+            o[2] = v[2];
+        }
+    }
+}
+
+__global__ void k_init_slots(Slot *slots, int S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    Slot z = {};
+    z.phase = kEmpty;
+    z.sys = -1;
+    slots[s] = z;
+}
+
+// rows[j] = u_n (.) dv_j for j < ncols (right-hand sides before projection, for one orbital).
+__global__ void k_pair_rows(const double *__restrict__ psi, const double *__restrict__ dv, int n, long long nd,
+                            double *__restrict__ rows) {
+    const int j = blockIdx.y;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nd;
+         idx += (long long)gridDim.x * blockDim.x)
+        rows[(long long)j * nd + idx] = psi[(long long)n * nd + idx] * dv[(long long)j * nd + idx];
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+struct SolveSpec {
+    const double *vt = nullptr;     // chi0 mode: dV block (ncols x nd); drho accumulated
+    double *drho = nullptr;
+    const double *rhs = nullptr;    // solve mode: right-hand side per system; x copied out
+    double2 *xout = nullptr;
+    const double *Tc = nullptr;     // P_c coefficients per system (nullptr = no projection)
+    double sign = 1.0;
+    double omega = 0.0;
+    std::vector<int> n, j;
+};
+
+// xy tiles of the stencil kernel: at most 64 columns wide, about 512 threads per block.
+Tiles pick_tiles(int nx, int ny) {
+    Tiles t;
+    t.ntx = (nx + 63) / 64;
+    t.tx = (nx + t.ntx - 1) / t.ntx;
+    int nty = (int)std::max(1LL, ((long long)ny * t.tx + 511) / 512);
+    t.ty = std::max(1, std::min((ny + nty - 1) / nty, 512 / t.tx));
+    t.nty = (ny + t.ty - 1) / t.ty;
+    return t;
+}
+
+int choose_slots(const Ctx &c, int nsys) {
+    if (c.opt.batch_systems > 0) return std::max(1, std::min(nsys, c.opt.batch_systems));
+    // All systems of a call in flight when they fit in 8 GB of slot storage; otherwise as many
+    // as fit (the queue refills the slots).
+    const double slot_bytes = (double)c.nd * (c.opt.prec == RPA_MIXED ? 64.0 : 88.0);
+    long long S = std::max(1LL, (long long)(8.0e9 / slot_bytes));
+    return (int)std::min<long long>(S, nsys);
+}
+
+// Carve aligned pieces out of one allocation.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T> T *take(size_t count) {
+        off = (off + 255) / 256 * 256;
+        T *p = (T *)(base + off);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+size_t slot_storage_bytes(bool mixed, long long nd, int S) {
+    const size_t n = (size_t)nd * S;
+    return 16 * n + 8 * n + (mixed ? 5 * 8 * n : 4 * 16 * n) + 8 * 256;
+}
+
+int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
+    const int nsys = (int)sp.n.size();
+    if (nsys == 0) return RPA_OK;
+    const int S = choose_slots(c, nsys);
+    const bool mixed = c.opt.prec == RPA_MIXED;
+    const long long nd = c.nd;
+    const int nblk = (int)cdiv(nd, kChunk);
+    const size_t n = (size_t)nd * S;
+
+    // slot storage: x64, b, then the inner vectors x, r, p, q (FP32 complex, or FP64 sharing x64)
+    Carver cv{(char *)c.cocg_state.ensure(slot_storage_bytes(mixed, nd, S))};
+    double2 *x64 = cv.take<double2>(n);
+    double *b = cv.take<double>(n);
+    void *xin, *r, *p, *q;           // p: two direction buffers, pstride elements apart
+    if (mixed) {
+        xin = cv.take<float2>(n);
+        r = cv.take<float2>(n);
+        p = cv.take<float2>(2 * n);
+        q = cv.take<float2>(n);
+    } else {
+        xin = x64;
+        r = cv.take<double2>(n);
+        p = cv.take<double2>(2 * n);
+        q = cv.take<double2>(n);
+    }
+    const long long pstride = (long long)n;
+    const Tiles tl = pick_tiles(c.nx, c.ny);
+    const int ntiles = tl.ntx * tl.nty;
+    double *partA = (double *)c.cocg_partials.ensure(sizeof(double) * (size_t)S * (2 * ntiles + 3 * nblk));
+    double *partB = partA + (size_t)S * ntiles * 2;
+    Slot *slots = (Slot *)c.sys_state.ensure(sizeof(Slot) * S);
+    // ints: head, count, cnt[2], list[2][S], then per system: n, j, iters, status, refines
+    const size_t nint = 4 + 2 * (size_t)S + 5 * (size_t)nsys;
+    int *qi = (int *)c.slot_idx.ensure(sizeof(int) * nint);
+    int *head = qi, *count = qi + 1, *cnt = qi + 2, *list = qi + 4;
+    int *sys_n = list + 2 * S, *sys_j = sys_n + nsys, *sys_it = sys_j + nsys, *sys_st = sys_it + nsys,
+        *sys_rf = sys_st + nsys;
+    RPA_CUDA(cudaMemsetAsync(qi, 0, sizeof(int) * nint, st));
+    RPA_CUDA(cudaMemcpyAsync(sys_n, sp.n.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+    RPA_CUDA(cudaMemcpyAsync(sys_j, sp.j.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+    k_init_slots<<<cdiv(S, 128), 128, 0, st>>>(slots, S);
+    RPA_LAUNCH("init slots");
+
+    Params P{};
+    P.slots = slots;
+    P.S = S;
+    P.nblk = nblk;
+    P.nparta = ntiles;
+    P.g = Grid3{c.nx, c.ny, c.nz, nd};
+    P.partA = partA;
+    P.partB = partB;
+    P.list = list;
+    P.cnt = cnt;
+    P.mixed = mixed;
+    P.tol = c.opt.tol;
+    P.inner_tol = c.opt.inner_tol;
+    P.maxit = c.opt.maxit;
+    P.max_refine = c.opt.max_refine;
+    P.head = head;
+    P.nsys = nsys;
+    P.count = count;
+    P.sys_iters = sys_it;
+    P.sys_status = sys_st;
+    P.sys_refines = sys_rf;
+
+    int dev_sms = 0;
+    RPA_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
+    const long long items = (long long)S * nblk;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, (long long)dev_sms * 8));
+    const unsigned wgrid = cdiv(S, kWarpsPerBlock);      // one warp per slot
+    const int pa_threads = tl.tx * tl.ty;
+    const size_t pa_smem = (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);
+    int pa_per_sm = 1;
+    if (mixed)
+        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, k_cocg_pa<float>, pa_threads, pa_smem));
+    else
+        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, k_cocg_pa<double>, pa_threads, pa_smem));
+    const unsigned pa_grid = (unsigned)std::max<long long>(
+        1, std::min<long long>((long long)S * ntiles, (long long)dev_sms * std::max(1, pa_per_sm)));
+    const Coef<float> cf32 = cast_coef<float>(c.coef);
+    const Coef<double> cf64 = cast_coef<double>(c.coef);
+    const double scale = 4.0 / (c.h * c.h * c.h);
+
+    // profiling: events around every launch of the three item kernels
+    const bool prof = c.opt.profile != 0;
+    const char *tn = mixed ? "c64" : "c128";
+    char names[3][32];
+    std::snprintf(names[0], 32, "-");
+    std::snprintf(names[1], 32, "k_cocg_pa<%s>", tn);
+    std::snprintf(names[2], 32, "k_cocg_b<%s>", tn);
+    const double csz = mixed ? 8.0 : 16.0, rsz = mixed ? 4.0 : 8.0;
+    // algorithmic bytes per grid point: pa reads r, p_old, V and writes p_new, q; b reads x, r, p, q
+    // and writes x, r
+    const double bytes_per_point[3] = {0.0, 4 * csz + rsz, 6 * csz};
+    if (prof) {
+        RPA_CUDA(cudaMemsetAsync(c.d_prof_points, 0, sizeof(unsigned long long) * 3, st));
+        P.prof = c.d_prof_points;
+    }
+    // Two graph instances of one epoch (alternating, so that the events of one can be read while
+    // the other runs); without graphs the same launches go straight to the stream.
+    const bool use_graph = c.use_graphs;
+    constexpr int kTimed = 2 * kEpoch;
+    std::vector<cudaEvent_t> evs;      // [2][kTimed][2]
+    if (prof) {
+        evs.resize(2 * kTimed * 2);
+        for (auto &e : evs) {
+            RPA_CUDA(cudaEventCreate(&e));
+        }
+    }
+    long long launches = 0;
+    double prof_ms[3] = {0, 0, 0};
+    long long prof_n[3] = {0, 0, 0};
+
+    auto maintenance = [&](cudaStream_t ss) {
+        if (mixed) {
+            k_refine_x<<<grid, kThreads, 0, ss>>>(P, x64, (const float2 *)xin);
+            k_residual64<<<grid, kThreads, 0, ss>>>(P, b, x64, (float2 *)xin, (float2 *)r, (float2 *)p, c.vloc64,
+                                                    cf64);   // p = direction buffer 0
+            k_state<<<wgrid, kThreads, 0, ss>>>(P);
+        }
+        if (sp.drho)
+            k_retire_drho<<<std::min<unsigned>(cdiv(nd, 256), 2048u), 256, 0, ss>>>(P, x64, c.psi64, sp.drho, scale);
+        else
+            k_retire_copy<<<grid, kThreads, 0, ss>>>(P, x64, sp.xout);
+        k_refill<<<1, 1024, 0, ss>>>(P, sys_n, sys_j, c.eps_dev, sp.omega);
+        if (mixed)
+            k_load<float><<<grid, kThreads, 0, ss>>>(P, c.psi64, c.ns, sp.vt, sp.rhs, sp.Tc, sp.sign, b, x64,
+                                                     (float2 *)xin, (float2 *)r, (float2 *)p, pstride);
+        else
+            k_load<double><<<grid, kThreads, 0, ss>>>(P, c.psi64, c.ns, sp.vt, sp.rhs, sp.Tc, sp.sign, b, x64,
+                                                      (double2 *)xin, (double2 *)r, (double2 *)p, pstride);
+        k_state<<<wgrid, kThreads, 0, ss>>>(P);
+        RPA_LAUNCH("cocg maintenance");
+    };
+    auto epoch = [&](cudaStream_t ss, int evset) {
+        const bool capturing = use_graph && ss == c.cap_stream;
+        auto rec = [&](int slot) {
+            if (!prof) return;
+            cudaEvent_t e = evs[(size_t)evset * kTimed * 2 + slot];
+            if (capturing) RPA_CUDA(cudaEventRecordWithFlags(e, ss, cudaEventRecordExternal));
+            else RPA_CUDA(cudaEventRecord(e, ss));
+        };
+        for (int e = 0; e < kEpoch; ++e) {
+            const int par = e & 1;
+            const int t0 = 2 * e * 2;
+            k_beta<<<wgrid, kThreads, 0, ss>>>(P, par);
+            if (mixed) {
+                rec(t0 + 0);
+                k_cocg_pa<float><<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const float2 *)r, (float2 *)p,
+                                                                      pstride, (float2 *)q, c.vloc32, cf32);
+                rec(t0 + 1);
+                k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
+                rec(t0 + 2);
+                k_cocg_b<float><<<grid, kThreads, 0, ss>>>(P, par, (float2 *)xin, (float2 *)r, (const float2 *)p,
+                                                           pstride, (const float2 *)q);
+                rec(t0 + 3);
+            } else {
+                rec(t0 + 0);
+                k_cocg_pa<double><<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const double2 *)r, (double2 *)p,
+                                                                        pstride, (double2 *)q, c.vloc64, cf64);
+                rec(t0 + 1);
+                k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
+                rec(t0 + 2);
+                k_cocg_b<double><<<grid, kThreads, 0, ss>>>(P, par, (double2 *)xin, (double2 *)r, (const double2 *)p,
+                                                            pstride, (const double2 *)q);
+                rec(t0 + 3);
+            }
+        }
+        RPA_LAUNCH("cocg iterations");
+        maintenance(ss);
+    };
+    const int per_epoch = 4 * kEpoch + (mixed ? 7 : 4);
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    if (use_graph) {
+        for (int g = 0; g < (prof ? 2 : 1); ++g) {
+            cudaGraph_t graph;
+            RPA_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+            epoch(c.cap_stream, g);
+            RPA_CUDA(cudaStreamEndCapture(c.cap_stream, &graph));
+            RPA_CUDA(cudaGraphInstantiate(&gexec[g], graph, 0));
+            cudaGraphDestroy(graph);
+        }
+        if (!prof) gexec[1] = gexec[0];
+    }
+    auto run_epoch = [&](long long k) {
+        if (use_graph) RPA_CUDA(cudaGraphLaunch(gexec[k & 1], st));
+        else epoch(st, (int)(k & 1));
+        launches += per_epoch;
+    };
+    auto collect_epoch = [&](long long k) {
+        if (!prof) return;
+        const int set = (int)(k & 1);
+        for (int t = 0; t < kTimed; ++t) {
+            float ms = 0.f;
+            RPA_CUDA(cudaEventElapsedTime(&ms, evs[((size_t)set * kTimed + t) * 2], evs[((size_t)set * kTimed + t) * 2 + 1]));
+            prof_ms[1 + t % 2] += ms;
+            prof_n[1 + t % 2] += 1;
+        }
+    };
+
+    maintenance(st);   // first fill of the slots
+    launches += mixed ? 7 : 4;
+    // Epochs are enqueued up to two ahead of the host's check of the busy count.
+    constexpr int kRing = 4;
+    int *hc = c.h_count;
+    cudaEvent_t ev[kRing];
+    for (auto &e : ev) RPA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    long long issued = 0, checked = 0;
+    const long long per_sys = (long long)c.opt.maxit * (mixed ? c.opt.max_refine : 1) / kEpoch + 3;
+    const long long max_epochs = ((long long)nsys + S - 1) / S * per_sys + 4;
+    bool done = false;
+    while (!done) {
+        while (issued - checked < 2 && issued < max_epochs) {
+            run_epoch(issued);
+            RPA_CUDA(cudaMemcpyAsync(hc + (issued % kRing), count, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RPA_CUDA(cudaEventRecord(ev[issued % kRing], st));
+            ++issued;
+        }
+        if (checked >= issued) break;
+        RPA_CUDA(cudaEventSynchronize(ev[checked % kRing]));
+        collect_epoch(checked);
+        if (hc[checked % kRing] == 0) done = true;
+        ++checked;
+    }
+    RPA_CUDA(cudaStreamSynchronize(st));
+    while (checked < issued) collect_epoch(checked++);
+    for (auto &e : ev) cudaEventDestroy(e);
+    for (int g = 0; g < 2; ++g)
+        if (gexec[g] && (g == 0 || gexec[1] != gexec[0])) cudaGraphExecDestroy(gexec[g]);
+    for (auto &e : evs) cudaEventDestroy(e);
+    c.stats.launches += launches + 1;
+    if (prof) {
+        unsigned long long pts[3];
+        RPA_CUDA(cudaMemcpy(pts, c.d_prof_points, sizeof pts, cudaMemcpyDeviceToHost));
+        for (int k = 1; k < 3; ++k) {
+            const int sl = prof_slot(c, names[k]);
+            c.stats.prof_ms[sl] += prof_ms[k];
+            c.stats.prof_launches[sl] += prof_n[k];
+            c.stats.prof_points[sl] += (double)pts[k];
+            c.stats.prof_bytes[sl] += (double)pts[k] * bytes_per_point[k];
+        }
+    }
+
+    std::vector<int> h(3 * (size_t)nsys);
+    RPA_CUDA(cudaMemcpy(h.data(), sys_it, sizeof(int) * 3 * nsys, cudaMemcpyDeviceToHost));
+    int worst = 0;
+    for (int i = 0; i < nsys; ++i) {
+        const int it = h[i], stt = h[nsys + i], rf = h[2 * nsys + i];
+        worst = std::max(worst, stt);
+        c.stats.sternheimer_solves += 1;
+        c.stats.cocg_iterations += it;
+        c.stats.refinement_steps += rf;
+        c.stats.stencil_points += (long long)(it + rf) * nd;
+        c.stats.worst_status = std::max(c.stats.worst_status, stt);
+        if (iters_out) (*iters_out)[i] = it;
+        if (status_out) (*status_out)[i] = stt;
+    }
+    if (!done) {
+        worst = std::max(worst, (int)RPA_ERR_NOT_CONVERGED);
+        c.stats.worst_status = std::max(c.stats.worst_status, (int)RPA_ERR_NOT_CONVERGED);
+    }
+    return worst;
+}
+
+// T[s][k] = u_k . rows[s] for nrows rows.
+void pc_coefficients(Ctx &c, const double *rows, int nrows, double *T, cudaStream_t st) {
+    gram(rows, nrows, c.psi64, c.ns, c.nd, T, st, c.dense_scratch);
+}
+
+void check_orbitals(const Ctx &c, const int *orb, int nsys) {
+    for (int i = 0; i < nsys; ++i)
+        if (orb[i] < 0 || orb[i] >= c.ns) fail(RPA_ERR_INVALID, "orbital index %d out of range", orb[i]);
+}
+
+}  // namespace
+
+int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
+                      std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {
+    check_orbitals(c, orb, nsys);
+    SolveSpec sp;
+    sp.rhs = b;
+    sp.xout = (double2 *)x;
+    sp.omega = omega;
+    sp.n.assign(orb, orb + nsys);
+    sp.j.resize(nsys);
+    for (int i = 0; i < nsys; ++i) sp.j[i] = i;
+    return run_queue(c, sp, s, iters, status);
+}
+
+int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
+                                std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {
+    check_orbitals(c, orb, nsys);
+    double *T = (double *)c.pc_coef.ensure(sizeof(double) * (size_t)nsys * c.ns);
+    pc_coefficients(c, b, nsys, T, s);
+    SolveSpec sp;
+    sp.rhs = b;
+    sp.xout = (double2 *)x;
+    sp.Tc = T;
+    sp.omega = omega;
+    sp.n.assign(orb, orb + nsys);
+    sp.j.resize(nsys);
+    for (int i = 0; i < nsys; ++i) sp.j[i] = i;
+    return run_queue(c, sp, s, iters, status);
+}
+
+int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
+    const int nsys = c.ns * ncols;
+    // P_c coefficients T[(n, j)][k] = u_k . (u_n (.) dv_j), one Gram per orbital n
+    double *T = (double *)c.pc_coef.ensure(sizeof(double) * (size_t)nsys * c.ns);
+    double *rows = (double *)c.rhs.ensure(sizeof(double) * (size_t)ncols * c.nd);
+    for (int n = 0; n < c.ns; ++n) {
+        k_pair_rows<<<dim3(std::min<unsigned>(cdiv(c.nd, 256), 1024u), ncols), 256, 0, s>>>(c.psi64, dv, n, c.nd,
+                                                                                             rows);
+        RPA_LAUNCH("pair rows");
+        pc_coefficients(c, rows, ncols, T + (size_t)n * ncols * c.ns, s);
+    }
+    SolveSpec sp;
+    sp.vt = dv;
+    sp.drho = drho;
+    sp.Tc = T;
+    sp.sign = -1.0;
+    sp.omega = omega;
+    sp.n.resize(nsys);
+    sp.j.resize(nsys);
+    for (int n = 0; n < c.ns; ++n)
+        for (int j = 0; j < ncols; ++j) {
+            sp.n[n * ncols + j] = n;
+            sp.j[n * ncols + j] = j;
+        }
+    return run_queue(c, sp, s, nullptr, nullptr);
+}
+
+}  // namespace rpa

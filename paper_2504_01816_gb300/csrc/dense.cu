@@ -1,0 +1,313 @@
+// Dense FP64 kernels of the subspace step (Algorithm 1 of arXiv 2504.01816): projection
+// C = V^T R, overlap M = R^T R, Cholesky L L^T = M, the inverse L^{-1} used for
+// V = R L^{-T}, and the Rayleigh-Ritz eigenvalues of the symmetric N_r x N_r matrix C with
+// the energy sum E = w sum_i [log(1 - lambda_i) + lambda_i] (Eq. 10).
+//
+// Blocks of grid functions are stored as rows (row c = column c of the N_d x K matrix), so
+// V^T R becomes G = V R^T over rows.  Long contractions are split over the grid and the
+// partial sums are added in a fixed order (deterministic).
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace rpa {
+
+namespace {
+
+constexpr int kTile = 32;     // output tile of the Gram kernel
+constexpr int kKc = 32;       // contraction chunk staged in shared memory
+
+// partial[z][a][b] = sum_{r in chunk z} A[a][r] B[b][r]
+__global__ void __launch_bounds__(256) k_gram(const double *__restrict__ A, int na, const double *__restrict__ B,
+                                              int nb, long long len, long long chunk, double *__restrict__ part) {
+    __shared__ double sa[kKc][kTile + 1];
+    __shared__ double sb[kKc][kTile + 1];
+    const int a0 = blockIdx.x * kTile, b0 = blockIdx.y * kTile;
+    const long long r0 = (long long)blockIdx.z * chunk;
+    const long long r1 = min(len, r0 + chunk);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 2 x 2 outputs each
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    for (long long rb = r0; rb < r1; rb += kKc) {
+        for (int e = threadIdx.x; e < kTile * kKc; e += 256) {
+            const int row = e / kKc, kk = e % kKc;
+            const long long r = rb + kk;
+            sa[kk][row] = (a0 + row < na && r < r1) ? A[(long long)(a0 + row) * len + r] : 0.0;
+            sb[kk][row] = (b0 + row < nb && r < r1) ? B[(long long)(b0 + row) * len + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kKc; ++kk) {
+            const double x0 = sa[kk][ty], x1 = sa[kk][ty + 16];
+            const double y0 = sb[kk][tx], y1 = sb[kk][tx + 16];
+            acc[0][0] += x0 * y0;
+            acc[0][1] += x0 * y1;
+            acc[1][0] += x1 * y0;
+            acc[1][1] += x1 * y1;
+        }
+        __syncthreads();
+    }
+    double *out = part + (long long)blockIdx.z * na * nb;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
+            if (a < na && b < nb) out[(long long)a * nb + b] = acc[u][v];
+        }
+}
+
+__global__ void k_sum_splits(const double *__restrict__ part, int splits, long long n, double *__restrict__ G) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < splits; ++z) s += part[(long long)z * n + e];
+        G[e] = s;
+    }
+}
+
+// Y[c][r] = sum_k S[c][k] X[k][r]; blockIdx.y picks 16 output rows.
+__global__ void __launch_bounds__(256) k_combine(const double *__restrict__ S, int nc, int nk,
+                                                 const double *__restrict__ X, long long len, double *__restrict__ Y) {
+    extern __shared__ double ssh[];    // 16 x nk
+    const int c0 = blockIdx.y * 16;
+    for (int e = threadIdx.x; e < 16 * nk; e += blockDim.x) {
+        const int c = e / nk, k = e % nk;
+        ssh[e] = (c0 + c < nc) ? S[(long long)(c0 + c) * nk + k] : 0.0;
+    }
+    __syncthreads();
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < len; r += (long long)gridDim.x * blockDim.x) {
+        double acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+        for (int k = 0; k < nk; ++k) {
+            const double x = X[(long long)k * len + r];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] += ssh[c * nk + k] * x;
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c0 + c < nc) Y[(long long)(c0 + c) * len + r] = acc[c];
+    }
+}
+
+// In-place Cholesky (lower) of an n x n row-major SPD matrix by one block.
+__global__ void __launch_bounds__(1024) k_cholesky(double *__restrict__ M, int n, int *__restrict__ info) {
+    __shared__ int bad;
+    __shared__ double floor_;
+    if (threadIdx.x == 0) {
+        // a pivot at or below n * eps * max diagonal means the columns are linearly dependent
+        double mx = 0.0;
+        for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(M[(long long)i * n + i]));
+        floor_ = (double)n * 2.220446049250313e-16 * mx;
+        bad = 0;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = M[(long long)j * n + j];
+            if (!(d > floor_) || !isfinite(d)) bad = j + 1;
+            else M[(long long)j * n + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double piv = M[(long long)j * n + j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(long long)i * n + j] /= piv;
+        __syncthreads();
+        const int m = n - j - 1;                       // trailing block (j+1..n-1)^2, lower part
+        for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+            const int i = j + 1 + (int)(e / m), k = j + 1 + (int)(e % m);
+            if (k <= i) M[(long long)i * n + k] -= M[(long long)i * n + j] * M[(long long)k * n + j];
+        }
+        __syncthreads();
+    }
+    if (!bad)
+        for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+            const int i = (int)(e / n), k = (int)(e % n);
+            if (k > i) M[e] = 0.0;
+        }
+    if (threadIdx.x == 0) *info = bad;
+}
+
+// Linv = L^{-1} for lower-triangular L; one thread per column (forward substitution).
+__global__ void k_tri_inverse(const double *__restrict__ L, int n, double *__restrict__ X) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    for (int i = 0; i < n; ++i) {
+        if (i < c) {
+            X[(long long)i * n + c] = 0.0;
+            continue;
+        }
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) s -= L[(long long)i * n + k] * X[(long long)k * n + c];
+        X[(long long)i * n + c] = s / L[(long long)i * n + i];
+    }
+}
+
+__global__ void k_symmetrize(double *C, int n) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * n) return;
+    const int i = (int)(e / n), k = (int)(e % n);
+    if (k > i) {
+        const double v = 0.5 * (C[(long long)i * n + k] + C[(long long)k * n + i]);
+        C[(long long)i * n + k] = v;
+        C[(long long)k * n + i] = v;
+    }
+}
+
+// Householder reduction of the symmetric matrix A (n x n, row-major, destroyed) to tridiagonal
+// form, then every eigenvalue by bisection on Sturm counts (one thread per eigenvalue), then
+// the energy sum in ascending order.  One block.  work: 3n doubles.
+__global__ void __launch_bounds__(1024) k_sym_eigvals(double *__restrict__ A, int n, double *__restrict__ lam,
+                                                      double *__restrict__ work, double weight,
+                                                      double *__restrict__ e_out) {
+    __shared__ double red[32];
+    __shared__ double sh_scalar[2];
+    double *v = work;           // Householder vector (length n, entries k+1..n-1 used)
+    double *p = work + n;       // A v
+    double *d = work + 2 * n;   // diagonal, then off-diagonal in A's subdiagonal
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto block_sum = [&](double x) -> double {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((tid & 31) == 0) red[tid >> 5] = x;
+        __syncthreads();
+        double t = 0.0;
+        if (tid == 0) {
+            for (int w = 0; w < (nt + 31) / 32; ++w) t += red[w];
+            sh_scalar[0] = t;
+        }
+        __syncthreads();
+        t = sh_scalar[0];
+        __syncthreads();
+        return t;
+    };
+    for (int k = 0; k + 2 < n; ++k) {
+        // x = A[k+1..n-1][k]
+        double part = 0.0;
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            const double x = A[(long long)i * n + k];
+            part += x * x;
+        }
+        const double xnorm = sqrt(block_sum(part));
+        const double x0 = A[(long long)(k + 1) * n + k];
+        if (xnorm == 0.0) continue;
+        const double alpha = x0 > 0 ? -xnorm : xnorm;
+        for (int i = k + 1 + tid; i < n; i += nt) v[i] = A[(long long)i * n + k] - (i == k + 1 ? alpha : 0.0);
+        __syncthreads();
+        part = 0.0;
+        for (int i = k + 1 + tid; i < n; i += nt) part += v[i] * v[i];
+        const double vv = block_sum(part);
+        if (vv == 0.0) continue;
+        // p = (2/vv) A22 v
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            double s = 0.0;
+            for (int j = k + 1; j < n; ++j) s += A[(long long)i * n + j] * v[j];
+            p[i] = 2.0 * s / vv;
+        }
+        __syncthreads();
+        part = 0.0;
+        for (int i = k + 1 + tid; i < n; i += nt) part += v[i] * p[i];
+        const double K = block_sum(part) / vv;
+        for (int i = k + 1 + tid; i < n; i += nt) p[i] -= K * v[i];     // q
+        __syncthreads();
+        const int m = n - k - 1;
+        for (long long e = tid; e < (long long)m * m; e += nt) {
+            const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+            A[(long long)i * n + j] -= v[i] * p[j] + p[i] * v[j];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            A[(long long)(k + 1) * n + k] = alpha;
+            A[(long long)k * n + k + 1] = alpha;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += nt) {
+        d[i] = A[(long long)i * n + i];
+        v[i] = (i + 1 < n) ? A[(long long)(i + 1) * n + i] : 0.0;   // off-diagonal e_i
+    }
+    __syncthreads();
+    // Gershgorin bounds
+    if (tid == 0) {
+        double lo = 1e300, hi = -1e300;
+        for (int i = 0; i < n; ++i) {
+            const double r = (i > 0 ? fabs(v[i - 1]) : 0.0) + (i + 1 < n ? fabs(v[i]) : 0.0);
+            lo = fmin(lo, d[i] - r);
+            hi = fmax(hi, d[i] + r);
+        }
+        const double pad = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+        sh_scalar[0] = lo - pad;
+        sh_scalar[1] = hi + pad;
+    }
+    __syncthreads();
+    const double glo = sh_scalar[0], ghi = sh_scalar[1];
+    for (int t = tid; t < n; t += nt) {
+        double lo = glo, hi = ghi;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            // number of eigenvalues < mid
+            int cnt = 0;
+            double q = d[0] - mid;
+            if (q < 0) ++cnt;
+            for (int i = 1; i < n; ++i) {
+                if (q == 0.0) q = 1e-300;
+                q = d[i] - mid - v[i - 1] * v[i - 1] / q;
+                if (q < 0) ++cnt;
+            }
+            if (cnt > t) hi = mid;
+            else lo = mid;
+        }
+        lam[t] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += log1p(-lam[i]) + lam[i];
+        *e_out = weight * s;
+    }
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+void gram(const double *A, int na, const double *B, int nb, long long len, double *G, cudaStream_t s,
+          DevBuf &scratch) {
+    const int ta = cdiv(na, kTile), tb = cdiv(nb, kTile);
+    long long splits = std::max(1LL, std::min<long long>(len / 512, 1200 / std::max(1, ta * tb)));
+    const long long chunk = ((len + splits - 1) / splits + kKc - 1) / kKc * kKc;
+    splits = (len + chunk - 1) / chunk;
+    double *part = (double *)scratch.ensure(sizeof(double) * (size_t)splits * na * nb);
+    k_gram<<<dim3(ta, tb, (unsigned)splits), 256, 0, s>>>(A, na, B, nb, len, chunk, part);
+    const long long n = (long long)na * nb;
+    k_sum_splits<<<std::min<unsigned>(cdiv(n, 256), 4096u), 256, 0, s>>>(part, (int)splits, n, G);
+    RPA_LAUNCH("gram");
+}
+
+void combine_rows(const double *S, int nc, int nk, const double *X, long long len, double *Y, cudaStream_t s) {
+    const size_t sh = sizeof(double) * 16 * nk;
+    if (sh > 48 * 1024) RPA_CUDA(cudaFuncSetAttribute(k_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_combine<<<dim3(std::min<unsigned>(cdiv(len, 256), 2048u), cdiv(nc, 16)), 256, sh, s>>>(S, nc, nk, X, len, Y);
+    RPA_LAUNCH("combine_rows");
+}
+
+void cholesky(double *M, int n, int *dev_info, cudaStream_t s) {
+    k_cholesky<<<1, 1024, 0, s>>>(M, n, dev_info);
+    RPA_LAUNCH("cholesky");
+}
+
+void tri_inverse(const double *L, int n, double *Linv, cudaStream_t s) {
+    k_tri_inverse<<<cdiv(n, 64), 64, 0, s>>>(L, n, Linv);
+    RPA_LAUNCH("tri_inverse");
+}
+
+void symmetrize(double *C, int n, cudaStream_t s) {
+    k_symmetrize<<<cdiv((long long)n * n, 256), 256, 0, s>>>(C, n);
+    RPA_LAUNCH("symmetrize");
+}
+
+void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out, cudaStream_t s) {
+    k_sym_eigvals<<<1, 1024, 0, s>>>(C, n, lam, work, weight, e_out);
+    RPA_LAUNCH("sym_eigvals");
+}
+
+}  // namespace rpa

@@ -1,0 +1,166 @@
+// Internal declarations shared by the translation units of librpa.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "rpa.h"
+
+namespace rpa {
+
+constexpr int kRadius = 6;              // 12th-order centred differences
+constexpr int kMaxOmega = 64;
+
+// ------------------------------------------------------------------------------------------
+// Errors: every internal failure throws rpa::Error; the C entry points catch it and turn it
+// into a status code plus a thread-local message.
+// ------------------------------------------------------------------------------------------
+struct Error {
+    rpa_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(rpa_status st, const char *fmt, ...);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+#define RPA_CUDA(call) ::rpa::check_cuda((call), #call, __FILE__, __LINE__)
+#define RPA_LAUNCH(what) ::rpa::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
+
+// ------------------------------------------------------------------------------------------
+// Device buffer that only grows.
+// ------------------------------------------------------------------------------------------
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    void *ensure(size_t need);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Shifted Hamiltonian stencil: (H + sigma) v = (diag + V + sigma) v + sum_k a_k (six neighbours
+// at distance k), with a_k = -w_k / (2 h^2) and diag = 3 a_0.
+struct StencilCoef {
+    double a[kRadius + 1];
+};
+
+// Per-system COCG scalars (one slot of a batch).
+struct SysState {
+    double rho_re, rho_im;        // r^T r (unconjugated)
+    double alpha_re, alpha_im;
+    double beta_re, beta_im;
+    double ref_norm;              // ||b|| (outer) for the FP64 form; ||r64|| for a mixed inner solve
+    double bnorm;                 // ||b||
+    double rnorm;                 // latest ||r||
+    double shift_re, shift_im;    // sigma = -eps_n + i omega
+    int n, j;                     // orbital, column
+    int active;                   // inner COCG running
+    int outer_active;             // mixed: refinement running
+    int iters;                    // inner iterations in the current solve
+    int total_iters;              // all inner iterations
+    int refines;                  // FP64 residual evaluations
+    int status;
+};
+
+// ------------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------------
+struct Ctx {
+    int nx = 0, ny = 0, nz = 0, ns = 0;
+    long long nd = 0;
+    double h = 0;
+    rpa_options opt{};
+    StencilCoef coef{};
+    int device = 0;
+
+    // inputs (device copies)
+    double *vloc64 = nullptr;
+    float *vloc32 = nullptr;
+    double *psi64 = nullptr;      // ns x nd (row s = orbital s)
+    std::vector<double> eps;
+    double *eps_dev = nullptr;
+
+    // Kronecker Coulomb operator: 1D eigenvectors Q_a (n_a x n_a, row-major Q[i*n+a]) and the
+    // summed eigenvalue grid lam = mu_x + mu_y + mu_z (nd).
+    double *Q[3] = {nullptr, nullptr, nullptr};
+    double *lam = nullptr;
+
+    // workspaces
+    DevBuf cocg_state;            // complex vectors of the systems in flight
+    DevBuf cocg_partials;
+    DevBuf sys_state;             // SysState[slots]
+    DevBuf rhs;                   // real right-hand sides of the systems in flight
+    DevBuf pc_coef;               // P_c coefficients
+    DevBuf coul_tmp;              // Kronecker scratch
+    DevBuf blockA, blockB, blockC, blockD;   // N_d x N_r blocks for rpa_ec / apply
+    DevBuf small;                 // N_r x N_r matrices and scalars
+    DevBuf slot_idx;              // (n, j) of the slots
+    DevBuf dense_scratch;         // split-K partial sums
+    SysState *h_state = nullptr;  // pinned host mirror of the slot states
+    size_t h_state_cap = 0;
+    int *h_count = nullptr;       // pinned host counter
+    int *d_count = nullptr;
+
+    // per-call statistics
+    rpa_stats stats{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // profiling (rpa_options.profile): event pool and per-kernel point counters on the device
+    std::vector<cudaEvent_t> ev_pool;
+    unsigned long long *d_prof_points = nullptr;   // RPA_PROF_SLOTS counters
+    // CUDA graphs: epochs of COCG iterations are captured on a private stream and replayed
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+
+    ~Ctx();
+};
+
+// ------------------------------------------------------------------------------------------
+// Operations (each enqueues work on `stream`)
+// ------------------------------------------------------------------------------------------
+// Kronecker Coulomb operator nu^power on ncols columns.
+void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s);
+void coulomb_setup(Ctx &c);
+
+// Sternheimer solves for the systems given by (n, j) pairs with real right-hand sides b
+// (nsys x nd, row per system) -> complex solutions x (nsys x nd interleaved, FP64).
+// Returns the worst per-system status; fills per-system iterations/status (host vectors).
+int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
+                      std::vector<int> *iters, std::vector<int> *status, cudaStream_t s);
+
+// chi0 on ncols real columns: drho = (4/h^3) Re sum_n u_n x_n with the projected right-hand
+// sides -P_c(u_n dV_j).  Returns the worst status.
+int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s);
+
+// Same as sternheimer_batch, with b replaced by P_c b first.
+int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
+                                std::vector<int> *iters, std::vector<int> *status, cudaStream_t s);
+
+// Dense FP64 helpers (dense.cu)
+// G (na x nb, row-major) = A B^T with A: na rows of length len, B: nb rows of length len.
+void gram(const double *A, int na, const double *B, int nb, long long len, double *G, cudaStream_t s,
+          DevBuf &scratch);
+// Y (nc rows) = S X, S: nc x nk row-major (device), X: nk rows of length len.
+void combine_rows(const double *S, int nc, int nk, const double *X, long long len, double *Y,
+                  cudaStream_t s);
+// Cholesky of the n x n SPD matrix M (row-major, device) in place -> lower L; returns via
+// *dev_info (0 ok, k+1 = failed pivot k).
+void cholesky(double *M, int n, int *dev_info, cudaStream_t s);
+// Linv = L^{-1} (lower), n x n row-major.
+void tri_inverse(const double *L, int n, double *Linv, cudaStream_t s);
+// Ascending eigenvalues of the symmetric n x n matrix C (row-major, destroyed), then
+// e_out = weight * sum_i [log1p(-lam_i) + lam_i].
+void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out,
+                 cudaStream_t s);
+void symmetrize(double *C, int n, cudaStream_t s);
+
+// Profiling helpers: register a kernel name in the stats table (returns its slot) and add
+// launches/time/points/bytes to it.
+int prof_slot(Ctx &c, const char *name);
+
+}  // namespace rpa
+
+struct rpa_ctx {
+    rpa::Ctx impl;
+};

@@ -1,0 +1,228 @@
+"""Parity of the CUDA library (through the C interface) with the FP64 CPU oracle.
+
+Tolerances.  The FP64 form solves every Sternheimer system to the relative residual tol;
+two solvers that both meet tol differ in x by at most ~2 tol cond(A), and chi0 inherits
+that bound through a sum of N_s solves.  The tests use tol = 1e-11..1e-12 so that the
+parity bound (1e-8 relative) is far above the solver error and far below any real
+mistake.  The mixed form reaches the same FP64 residual tolerance through refinement, so
+it is held to the same bounds.  Ritz values and energies are compared in absolute terms:
+1e-8 (FP64) and 1e-7 (mixed) for lambda_i, which the method's own target (1e-6) exceeds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rpa():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_01816_gb300 as m
+    return m
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def opts(rpa, **kw):
+    o = rpa.default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.workload("tiny15").system
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    # odd, non-cubic grid: N_d = 1001 is not a multiple of any tile size
+    return synth.small_system((13, 11, 7), h=0.5, n_s=3, n_wells=3, seed=31)
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ------------------------------------------------------------------------- Coulomb
+@pytest.mark.parametrize("which", ["tiny", "ragged"])
+def test_coulomb_matches_oracle(rpa, which, tiny, ragged):
+    s = tiny if which == "tiny" else ragged
+    o = oracle.Oracle.from_system(s)
+    X = synth.random_block(1, 5, s.n_d)
+    with rpa.Context.from_system(s) as ctx:
+        for p in (0.5, 1.0, -1.0):
+            got = ctx.coulomb_apply(p, cuda(X)).cpu().numpy()
+            assert relerr(got, o.coulomb.apply(X, p)) < 1e-12, p
+        # in-place
+        Xd = cuda(X)
+        ctx.coulomb_apply(0.5, Xd, out=Xd)
+        assert relerr(Xd.cpu().numpy(), o.coulomb.apply(X, 0.5)) < 1e-12
+
+
+# ------------------------------------------------------------------------- Sternheimer
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("which", ["tiny", "ragged"])
+def test_sternheimer_matches_oracle(rpa, prec, which, tiny, ragged):
+    s = tiny if which == "tiny" else ragged
+    g = oracle.Grid(s.nx, s.ny, s.nz, s.h)
+    rng = np.random.default_rng(4)
+    nsys = 7
+    orbs = np.arange(nsys) % s.n_s
+    b = rng.standard_normal((nsys, s.n_d))
+    omega = 0.3
+    tol = 1e-11
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=p)) as ctx:
+        x, it, st, code = ctx.sternheimer_solve(omega, orbs, cuda(b), project=False)
+        x = x.cpu().numpy()
+        assert code == rpa.RPA_OK and np.all(st.cpu().numpy() == 0)
+        xp, _, st2, code2 = ctx.sternheimer_solve(omega, orbs, cuda(b), project=True)
+        xp = xp.cpu().numpy()
+    sig = -s.eps[orbs] + 1j * omega
+    ref, rit, rst = oracle.cocg(g, s.vloc, sig, b.astype(complex), tol, 100000)
+    assert np.all(rst == 0)
+    assert relerr(x, ref) < 1e-8
+    # true residual of the GPU solution, evaluated by the oracle's operator
+    for k in range(nsys):
+        r = b[k] - oracle.apply_h(g, s.vloc, x[k], sig[k])
+        assert np.linalg.norm(r) <= 1.5 * tol * np.linalg.norm(b[k])
+    if prec == "fp64":
+        # same algorithm, different summation order: counts agree up to the last few iterations
+        assert np.all(np.abs(it.cpu().numpy() - rit) <= np.maximum(3, 0.1 * rit))
+    # projected right-hand sides: b - U U^T b
+    bp = b - (b @ s.psi.T) @ s.psi
+    refp, _, _ = oracle.cocg(g, s.vloc, sig, bp.astype(complex), tol, 100000)
+    assert relerr(xp, refp) < 1e-8
+
+
+def test_sternheimer_status_codes(rpa, ragged):
+    s = ragged
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((3, s.n_d))
+    b[1] = 0.0
+    with rpa.Context.from_system(s, opts(rpa, tol=1e-12, maxit=2)) as ctx:
+        x, it, st, code = ctx.sternheimer_solve(0.1, [0, 1, 2], cuda(b), project=False)
+    st = st.cpu().numpy()
+    assert code == rpa.RPA_ERR_NOT_CONVERGED
+    assert st[0] == rpa.RPA_ERR_NOT_CONVERGED and st[1] == rpa.RPA_OK and st[2] == rpa.RPA_ERR_NOT_CONVERGED
+    assert np.all(x[1].cpu().numpy() == 0)
+    assert it.cpu().numpy()[0] == 2
+
+
+def test_sternheimer_rejects_bad_orbital(rpa, ragged):
+    s = ragged
+    with rpa.Context.from_system(s) as ctx:
+        with pytest.raises(rpa.RpaError):
+            ctx.sternheimer_solve(0.1, [s.n_s], cuda(np.ones((1, s.n_d))), project=False)
+
+
+# ------------------------------------------------------------------------- chi0 application
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_apply_nuchi0_matches_oracle(rpa, prec, tiny):
+    s = tiny
+    o = oracle.Oracle.from_system(s)
+    V = synth.random_block(8, 6, s.n_d)
+    tol = 1e-11
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=p)) as ctx:
+        for omega in (0.05, 1.7):
+            R, code = ctx.apply_nuchi0(omega, cuda(V), symmetric=True)
+            assert code == rpa.RPA_OK
+            assert relerr(R.cpu().numpy(), o.chi_tilde(V, omega, tol)) < 1e-8
+        R2, code = ctx.apply_nuchi0(0.4, cuda(V), symmetric=False)
+        assert relerr(R2.cpu().numpy(), o.nu_chi0(V, 0.4, tol)) < 1e-8
+
+
+def test_apply_nuchi0_small_batches_agree(rpa, ragged):
+    """Waves of 5 systems (several per orbital, ragged last wave) give the same result."""
+    s = ragged
+    V = synth.random_block(9, 7, s.n_d)
+    with rpa.Context.from_system(s, opts(rpa, tol=1e-12)) as ctx:
+        Ra, _ = ctx.apply_nuchi0(0.6, cuda(V))
+        ctx.set_options(opts(rpa, tol=1e-12, batch_systems=5))
+        Rb, _ = ctx.apply_nuchi0(0.6, cuda(V))
+    assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
+
+
+def test_apply_nuchi0_deterministic(rpa, tiny):
+    V = synth.random_block(10, 4, tiny.n_d)
+    with rpa.Context.from_system(tiny, opts(rpa, prec=rpa.RPA_MIXED)) as ctx:
+        a, _ = ctx.apply_nuchi0(0.3, cuda(V))
+        b, _ = ctx.apply_nuchi0(0.3, cuda(V))
+    assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------------------- E_c
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ec_matches_oracle_fixed_iterations(rpa, prec, tiny):
+    s = tiny
+    n_r, n_omega, iters, tol = 8, 4, 3, 1e-10
+    V0 = synth.trial_vectors(0, n_r, s.n_d)
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms)
+    with rpa.Context.from_system(s, o) as ctx:
+        res = ctx.ec(cuda(V0))
+    ref = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, n_omega, tol=tol, eps_c=0.0, fixed_iters=iters)
+    lam_tol = 1e-8 if prec == "fp64" else 1e-7
+    assert np.max(np.abs(res.lambdas - ref.lambdas)) < lam_tol
+    assert abs(res.e_c - ref.e_c) < 1e-8
+    assert np.max(np.abs(res.e_c_per_omega - ref.e_c_per_omega)) < 1e-8
+    assert np.allclose(res.stats["omegas"], ref.omegas, rtol=1e-14)
+    assert np.allclose(res.stats["weights"], ref.weights, rtol=1e-13)
+    assert res.stats["subspace_iterations"] == [iters] * n_omega
+    assert np.all(res.lambdas <= 1e-12) and res.e_c < 0
+
+
+def test_ec_converged_mode_matches_oracle(rpa, ragged):
+    s = ragged
+    n_r, n_omega = 6, 3
+    V0 = synth.trial_vectors(3, n_r, s.n_d)
+    o = opts(rpa, tol=1e-11, n_omega=n_omega, eps_c=1e-9, n_atoms=s.n_atoms)
+    with rpa.Context.from_system(s, o) as ctx:
+        res = ctx.ec(cuda(V0))
+    ref = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, n_omega, tol=1e-11, eps_c=1e-9)
+    assert list(res.stats["subspace_iterations"]) == list(ref.subspace_iterations)
+    assert abs(res.e_c - ref.e_c) < 1e-8
+    assert np.max(np.abs(res.lambdas - ref.lambdas)) < 1e-7
+
+
+def test_ec_rejects_rank_deficient_start(rpa, ragged):
+    s = ragged
+    V0 = np.tile(synth.trial_vectors(3, 1, s.n_d), (3, 1))
+    with rpa.Context.from_system(s, opts(rpa, n_omega=1)) as ctx:
+        with pytest.raises(rpa.RpaError) as e:
+            ctx.ec(cuda(V0))
+    assert e.value.status == rpa.RPA_ERR_NOT_SPD
+
+
+# ------------------------------------------------------------------------- full-size sample
+@pytest.mark.slow
+def test_mixed40_sampled_columns_match_oracle(rpa):
+    """40^3 grid, 16 orbitals, 64 trial vectors, mixed precision at the benchmark's launch
+    configuration: sampled columns of nu^1/2 chi0 nu^1/2 V against the oracle (each column
+    of R depends on the same column of V only)."""
+    w = synth.workload("mixed40")
+    s = w.system
+    V = synth.trial_vectors(w.seed, w.n_r, s.n_d)
+    omega = oracle.frequency_quadrature(w.n_omega)[0][2]
+    with rpa.Context.from_system(s, opts(rpa, prec=rpa.RPA_MIXED, tol=1e-10)) as ctx:
+        R, code = ctx.apply_nuchi0(omega, cuda(V))
+    assert code == rpa.RPA_OK
+    R = R.cpu().numpy()
+    cols = [0, 37]
+    ref = oracle.Oracle.from_system(s).chi_tilde(V[cols], omega, 1e-10)
+    assert relerr(R[cols], ref) < 1e-7
