@@ -214,8 +214,8 @@ __global__ void k_beta(Params P, int par) {
     P.list[par * P.S + pos] = w;
 }
 
-// alpha = rho / p^T q for the active slots; breakdown retires the slot.  Also clears the other
-// parity's list counter for the next iteration.
+// alpha = rho / p^T q for the active slots; breakdown retires the slot; the iteration is
+// counted.  Also clears the other parity's list counter for the next iteration.
 __global__ void k_alpha(Params P, int par) {
     if (blockIdx.x == 0 && threadIdx.x == 0) P.cnt[par ^ 1] = 0;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -236,6 +236,9 @@ __global__ void k_alpha(Params P, int par) {
     const double rr = sl.rho_re[k & 1], ri = sl.rho_im[k & 1];
     sl.alpha_re = (rr * mu[0] + ri * mu[1]) / den;
     sl.alpha_im = (ri * mu[0] - rr * mu[1]) / den;
+    // the iteration is counted here, by the slot's single writer, before k_cocg_b reads it
+    sl.iters = k + 1;
+    sl.total_iters += 1;
 }
 
 // x += alpha p ; r -= alpha q ; partial sums of r^T r and ||r||^2
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename
         if (sl.phase != kInner) continue;      // breakdown in k_alpha (stable during this kernel)
         const T ar = (T)sl.alpha_re, ai = (T)sl.alpha_im;
         const long long off = (long long)s * P.g.nd;
-        const C *p = pbuf + (long long)((sl.iters + 1) & 1) * pstride;   // the new direction
+        const C *p = pbuf + (long long)(sl.iters & 1) * pstride;   // the new direction (iters counted in k_alpha)
         double v[3] = {0.0, 0.0, 0.0};
 #pragma unroll 4
         for (int t = 0; t < kPPT; ++t) {
@@ -277,10 +280,6 @@ __global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename
             o[0] = v[0];
             o[1] = v[1];
             o[2] = v[2];
-            if (chunk == 0) {
-                sl.iters += 1;
-                sl.total_iters += 1;
-            }
         }
         prof_add(P, 2, chunk);
     }
@@ -332,7 +331,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_cocg_pa(Params 
     C *sm = reinterpret_cast<C *>(smraw);
     constexpr int R = kRadius;
     const int W = tl.tx + 2 * R;
-    const int lx = threadIdx.x % tl.tx, ly = threadIdx.x / tl.tx;
+    // the block is rounded up to whole warps; threads past tx * ty only help with the halo
+    const bool in_tile = threadIdx.x < tl.tx * tl.ty;
+    const int lx = threadIdx.x % tl.tx, ly = in_tile ? threadIdx.x / tl.tx : 0;
     const int ntiles = tl.ntx * tl.nty;
     const long long items = (long long)P.cnt[par] * ntiles;
     const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_cocg_pa(Params 
         C *__restrict__ qs = q + off;
         const int x0 = (tile % tl.ntx) * tl.tx, y0 = (tile / tl.ntx) * tl.ty;
         const int gx = x0 + lx, gy = y0 + ly;
-        const bool own = gx < nx && gy < ny;
+        const bool own = in_tile && gx < nx && gy < ny;
         const int col = gy * nx + gx;
         C qv[2 * R + 1];
 #pragma unroll
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_cocg_pa(Params 
         double acc0 = 0.0, acc1 = 0.0;
         for (int z = 0; z < nz; ++z) {
             __syncthreads();                                   // previous plane's readers are done
-            sm[(ly + R) * W + lx + R] = qv[R];
+            if (in_tile) sm[(ly + R) * W + lx + R] = qv[R];
             for (int e = threadIdx.x; e < nhalo; e += blockDim.x) {
                 int hx, hy;                                    // frame coordinates
                 if (e < 2 * R * tl.tx) {                       // top / bottom strips
@@ -750,7 +751,7 @@ Tiles pick_tiles(int nx, int ny) {
     t.ntx = (nx + 63) / 64;
     t.tx = (nx + t.ntx - 1) / t.ntx;
     int nty = (int)std::max(1LL, ((long long)ny * t.tx + 511) / 512);
-    t.ty = std::max(1, std::min((ny + nty - 1) / nty, 512 / t.tx));
+    t.ty = std::max(1, std::min((ny + nty - 1) / nty, 480 / t.tx));
     t.nty = (ny + t.ty - 1) / t.ty;
     return t;
 }
@@ -851,7 +852,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const long long items = (long long)S * nblk;
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, (long long)dev_sms * 8));
     const unsigned wgrid = cdiv(S, kWarpsPerBlock);      // one warp per slot
-    const int pa_threads = tl.tx * tl.ty;
+    const int pa_threads = (tl.tx * tl.ty + 31) / 32 * 32;
     const size_t pa_smem = (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);
     int pa_per_sm = 1;
     if (mixed)

@@ -109,6 +109,26 @@ def test_sternheimer_matches_oracle(rpa, prec, which, tiny, ragged):
     assert relerr(xp, refp) < 1e-8
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sternheimer_multi_tile_grid(rpa, prec):
+    """nx > 64 and ny > one tile: several x and y tiles of the stencil kernel, the last ones
+    partial, with halos between tiles."""
+    s = synth.small_system((70, 31, 9), h=0.5, n_s=2, n_wells=3, seed=17)
+    g = oracle.Grid(s.nx, s.ny, s.nz, s.h)
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal((3, s.n_d))
+    orbs = np.array([0, 1, 1])
+    tol = 1e-11
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=p)) as ctx:
+        x, it, st, code = ctx.sternheimer_solve(0.4, orbs, cuda(b), project=True)
+    assert code == rpa.RPA_OK
+    bp = b - (b @ s.psi.T) @ s.psi
+    sig = -s.eps[orbs] + 0.4j
+    ref, _, rst = oracle.cocg(g, s.vloc, sig, bp.astype(complex), tol, 100000)
+    assert relerr(x.cpu().numpy(), ref) < 1e-8
+
+
 def test_sternheimer_status_codes(rpa, ragged):
     s = ragged
     rng = np.random.default_rng(5)
