@@ -154,6 +154,32 @@ rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, dou
 rpa_status rpa_ec(rpa_ctx *ctx, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host,
                   double *ec_per_omega_host, rpa_stats *stats, void *stream);
 
+/* Size of the fixed device scratch array used by rpa_coulomb_apply_noalloc (64 MiB).  Every
+ * GPU on which the library is loaded keeps this much memory reserved until the process exits. */
+#define RPA_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* rpa_coulomb_apply without any device allocation inside the call.
+ *
+ * For callers that cannot let the library call cudaMalloc at that point: applications whose
+ * device memory is already fully reserved by their own allocator or memory pool (so a fresh
+ * cudaMalloc would fail), and latency-bound loops that cannot afford the device-wide
+ * synchronisation a cudaMalloc/cudaFree pair can cause.  The paper has no counterpart of this
+ * entry point; it computes exactly what rpa_coulomb_apply computes.
+ *
+ * Scratch: the library's own statically sized device array of RPA_STATIC_SCRATCH_BYTES.  A call
+ * needs 2 * ncols * N_d + N_d doubles (each of the two column blocks rounded up to 256 bytes);
+ * larger requests return RPA_ERR_INVALID with a message and do nothing.  The caller still
+ * provides in_dev and out_dev (N_d x ncols, column-major; they may alias).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  The context's device
+ * must be the current device.
+ * All calls share the one array and it keeps the last call's contents; every scratch word is
+ * written before it is read, so nothing needs clearing.  Calls whose work overlaps on the GPU
+ * (different streams or threads, any context) race on the array and give wrong results:
+ * serialise them. */
+rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *in_dev, double *out_dev,
+                                     int ncols, void *stream);
+
 /* Release the context and its device workspaces.  NULL is ignored. */
 void rpa_destroy(rpa_ctx *ctx);
 

@@ -303,6 +303,17 @@ rpa_status rpa_coulomb_apply(rpa_ctx *ctx, double power, const double *in_dev, d
     });
 }
 
+rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *in_dev, double *out_dev, int ncols,
+                                     void *stream) {
+    return guarded([&] {
+        if (!ctx || !in_dev || !out_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        if (ncols < 0) fail(RPA_ERR_INVALID, "ncols must be >= 0");
+        if (!std::isfinite(power)) fail(RPA_ERR_INVALID, "power must be finite");
+        coulomb_apply_noalloc(ctx->impl, power, in_dev, out_dev, ncols, as_stream(stream));
+        RPA_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    });
+}
+
 rpa_status rpa_sternheimer_solve(rpa_ctx *ctx, double omega, const int *orbital_idx_host, int nsys,
                                  const double *rhs_dev, int project, double *x_dev, int *iters_dev,
                                  int *status_dev, void *stream) {

@@ -9,6 +9,7 @@
 // The 1D eigendecompositions are computed once per context on the host (cyclic Jacobi in
 // FP64; n_a is at most a few hundred).
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -157,11 +158,31 @@ static void axis_pass(Ctx &c, int axis, const double *in, double *out, int ncols
     RPA_LAUNCH("coulomb axis transform");
 }
 
-void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s) {
-    if (ncols <= 0) return;
-    const size_t blk = sizeof(double) * (size_t)ncols * c.nd;
-    char *base = (char *)c.coul_tmp.ensure(2 * blk + sizeof(double) * c.nd);
-    double *t1 = (double *)base, *t2 = (double *)(base + blk), *sc = (double *)(base + 2 * blk);
+// Fixed scratch for rpa_coulomb_apply_noalloc.  Every device that loads the library holds
+// RPA_STATIC_SCRATCH_BYTES of it until the process exits.  In host code the symbol is only a
+// stand-in: the device address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[RPA_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up on first use).
+void *static_scratch(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) fail(RPA_ERR_INVALID, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        RPA_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_scratch_addr[dev] = ptr;
+    }
+    return g_scratch_addr[dev];
+}
+}  // namespace
+
+static void coulomb_passes(Ctx &c, double power, const double *in, double *out, int ncols, double *t1, double *t2,
+                           double *sc, cudaStream_t s) {
     k_scale_grid<<<(unsigned)((c.nd + 255) / 256), 256, 0, s>>>(c.lam, sc, c.nd, power);
     RPA_LAUNCH("coulomb scale");
     axis_pass(c, 0, in, t1, ncols, 1, nullptr, s);
@@ -170,6 +191,30 @@ void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncol
     axis_pass(c, 2, t1, t2, ncols, 0, nullptr, s);
     axis_pass(c, 1, t2, t1, ncols, 0, nullptr, s);
     axis_pass(c, 0, t1, out, ncols, 0, nullptr, s);
+}
+
+void coulomb_apply_noalloc(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s) {
+    if (ncols <= 0) return;
+    const size_t blk = (sizeof(double) * (size_t)ncols * c.nd + 255) / 256 * 256;
+    const size_t need = 2 * blk + sizeof(double) * (size_t)c.nd;
+    if (need > (size_t)RPA_STATIC_SCRATCH_BYTES)
+        fail(RPA_ERR_INVALID, "rpa_coulomb_apply_noalloc: %d columns of %lld points need %zu bytes of scratch, "
+                              "more than the fixed %zu", ncols, c.nd, need, (size_t)RPA_STATIC_SCRATCH_BYTES);
+    int dev = 0;
+    RPA_CUDA(cudaGetDevice(&dev));
+    if (dev != c.device) fail(RPA_ERR_INVALID, "the current device is not the context's device");
+    char *base = (char *)static_scratch(dev);
+    double *t1 = (double *)base, *t2 = (double *)(base + blk), *sc = (double *)(base + 2 * blk);
+    // every scratch word is written before it is read: nothing needs clearing
+    coulomb_passes(c, power, in, out, ncols, t1, t2, sc, s);
+}
+
+void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s) {
+    if (ncols <= 0) return;
+    const size_t blk = sizeof(double) * (size_t)ncols * c.nd;
+    char *base = (char *)c.coul_tmp.ensure(2 * blk + sizeof(double) * c.nd);
+    double *t1 = (double *)base, *t2 = (double *)(base + blk), *sc = (double *)(base + 2 * blk);
+    coulomb_passes(c, power, in, out, ncols, t1, t2, sc, s);
 }
 
 }  // namespace rpa

@@ -122,6 +122,8 @@ struct Ctx {
 // Kronecker Coulomb operator nu^power on ncols columns.
 void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s);
 void coulomb_setup(Ctx &c);
+// Same operator with its scratch in the library's fixed device array (no allocation).
+void coulomb_apply_noalloc(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s);
 
 // Sternheimer solves for the systems given by (n, j) pairs with real right-hand sides b
 // (nsys x nd, row per system) -> complex solutions x (nsys x nd interleaved, FP64).

@@ -29,7 +29,7 @@ RPA_FP64, RPA_MIXED = 0, 1
 STATUS_NAMES = {0: "RPA_OK", 1: "RPA_ERR_INVALID", 2: "RPA_ERR_CUDA", 3: "RPA_ERR_OOM",
                 4: "RPA_ERR_NOT_CONVERGED", 5: "RPA_ERR_BREAKDOWN", 6: "RPA_ERR_NOT_SPD"}
 
-EXPORTED = ("rpa_default_options", "rpa_setup", "rpa_set_options", "rpa_coulomb_apply",
+EXPORTED = ("rpa_default_options", "rpa_setup", "rpa_set_options", "rpa_coulomb_apply", "rpa_coulomb_apply_noalloc",
             "rpa_sternheimer_solve", "rpa_apply_nuchi0", "rpa_ec", "rpa_destroy", "rpa_last_error",
             "rpa_version")
 
@@ -84,6 +84,8 @@ def _load():
     lib.rpa_set_options.restype = i
     lib.rpa_coulomb_apply.argtypes = [vp, d, dp, dp, i, vp]
     lib.rpa_coulomb_apply.restype = i
+    lib.rpa_coulomb_apply_noalloc.argtypes = [vp, d, dp, dp, i, vp]
+    lib.rpa_coulomb_apply_noalloc.restype = i
     lib.rpa_sternheimer_solve.argtypes = [vp, d, ctypes.POINTER(ctypes.c_int), i, dp, i, dp, ip, ip, vp]
     lib.rpa_sternheimer_solve.restype = i
     lib.rpa_apply_nuchi0.argtypes = [vp, d, dp, dp, i, i, vp]
@@ -291,6 +293,17 @@ def rpa_set_options(ctx: Context, options: Options):
 
 def rpa_coulomb_apply(ctx: Context, power, X, out=None, stream=None):
     return ctx.coulomb_apply(power, X, out, stream)
+
+
+def rpa_coulomb_apply_noalloc(ctx: Context, power, X, out=None, stream=None):
+    """Same result as rpa_coulomb_apply, with the scratch in the library's fixed device array
+    (the call itself allocates no device memory; ``out`` must then be given by the caller)."""
+    import torch
+    k = X.shape[0]
+    _dev64(X, (k, ctx.n_d))
+    out = torch.empty_like(X) if out is None else _dev64(out, (k, ctx.n_d))
+    _check(_lib.rpa_coulomb_apply_noalloc(ctx._h, float(power), _ptr(X), _ptr(out), k, _stream(stream)))
+    return out
 
 
 def rpa_sternheimer_solve(ctx: Context, omega, orbitals, rhs, project=True, stream=None):
