@@ -118,6 +118,37 @@ __device__ __forceinline__ void block_sum(double (&v)[N]) {
     }
 }
 
+// Block sum in the working precision T (256 threads), converted to double once at the end;
+// result valid in thread 0.  Fixed order.
+template <typename T, int N>
+__device__ __forceinline__ void block_sum_t(const T (&in)[N], double (&out)[N]) {
+    __shared__ T sh[N][kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        v[c] = in[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < N; ++c) sh[c][warp] = v[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < N; ++c) out[c] = 0.0;
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            T t = lane < kWarpsPerBlock ? sh[c][lane] : (T)0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            out[c] = (double)t;
+        }
+    }
+}
+
 // Sum one slot's per-item partials with one warp (fixed order); result in every lane.
 template <int N, int STRIDE>
 __device__ __forceinline__ void warp_slot_sum(const double *part, int nblk, double (&out)[N]) {
@@ -256,7 +287,7 @@ __global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename
         const T ar = (T)sl.alpha_re, ai = (T)sl.alpha_im;
         const long long off = (long long)s * P.g.nd;
         const C *p = pbuf + (long long)(sl.iters & 1) * pstride;   // the new direction (iters counted in k_alpha)
-        double v[3] = {0.0, 0.0, 0.0};
+        T a0 = 0, a1 = 0, a2 = 0;          // per-thread sums in the working precision (FP64 is slow)
 #pragma unroll 4
         for (int t = 0; t < kPPT; ++t) {
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
@@ -269,12 +300,14 @@ __global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename
                 rv.y -= ar * qv.y + ai * qv.x;
                 x[off + idx] = xv;
                 r[off + idx] = rv;
-                v[0] += (double)(rv.x * rv.x - rv.y * rv.y);
-                v[1] += (double)(2 * rv.x * rv.y);
-                v[2] += (double)(rv.x * rv.x + rv.y * rv.y);
+                a0 += rv.x * rv.x - rv.y * rv.y;
+                a1 += 2 * rv.x * rv.y;
+                a2 += rv.x * rv.x + rv.y * rv.y;
             }
         }
-        block_sum<3>(v);
+        const T a[3] = {a0, a1, a2};
+        double v[3];
+        block_sum_t<T, 3>(a, v);
         if (threadIdx.x == 0) {
             double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
             o[0] = v[0];
@@ -317,28 +350,37 @@ struct Tiles {
 // Fused direction update and stencil (one COCG half-step), for the slots of the active list:
 //   p_new = r + beta p_old          (p is double-buffered per slot by iteration parity)
 //   q     = (H - eps_n + i omega) p_new ,  partial sums of p_new^T q
-// Work item = (slot, xy tile).  The block marches along z; each thread keeps the 13 values of
-// p_new on its own column (z-6 .. z+6) in registers, and the centre plane of the tile plus a
-// 6-point halo (computed from r and p_old, never read back from p_new) is staged in shared
-// memory for the x and y neighbours.  Values outside the box are zero.
-template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_cocg_pa(Params P, int par, Tiles tl, const typename Cx<T>::t *__restrict__ r,
-                                                    typename Cx<T>::t *__restrict__ pbuf, long long pstride,
-                                                    typename Cx<T>::t *__restrict__ q, const T *__restrict__ vloc,
-                                                    Coef<T> cf) {
+// Work item = (slot, xy tile).  The block marches along z.  Each thread keeps the 13 values of
+// p_new on its own column (z-6 .. z+6) in registers; the centre plane of the tile and its
+// 6-point halo (computed from r and p_old, never read back from p_new) go to one of two shared
+// frames, so one barrier per plane suffices.  Loads are issued ahead of use: the halo of plane
+// z+1 and the column front two planes ahead are in flight while plane z is computed.  Values
+// outside the box are zero.
+template <typename T> struct PaBounds;
+template <> struct PaBounds<float> { static constexpr int threads = 640; };
+template <> struct PaBounds<double> { static constexpr int threads = 448; };
+// MAXH: halo elements per thread that are prefetched into registers; any rest loads in place.
+template <typename T, int MAXH>
+__global__ void __launch_bounds__(PaBounds<T>::threads, 1)
+    k_cocg_pa(Params P, int par, Tiles tl, const typename Cx<T>::t *__restrict__ r, typename Cx<T>::t *__restrict__ pbuf,
+              long long pstride, typename Cx<T>::t *__restrict__ q, const T *__restrict__ vloc, Coef<T> cf) {
     using C = typename Cx<T>::t;
     extern __shared__ unsigned char smraw[];
-    C *sm = reinterpret_cast<C *>(smraw);
     constexpr int R = kRadius;
-    const int W = tl.tx + 2 * R;
+    const int W = tl.tx + 2 * R, H = tl.ty + 2 * R, frame = W * H;
+    C *const fr0 = reinterpret_cast<C *>(smraw);
+    C *const fr1 = fr0 + frame;
     // the block is rounded up to whole warps; threads past tx * ty only help with the halo
     const bool in_tile = threadIdx.x < tl.tx * tl.ty;
     const int lx = threadIdx.x % tl.tx, ly = in_tile ? threadIdx.x / tl.tx : 0;
     const int ntiles = tl.ntx * tl.nty;
     const long long items = (long long)P.cnt[par] * ntiles;
     const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz;
-    const int plane = nx * ny;                 // grid functions have < 2^31 points
-    const int nhalo = 2 * R * (tl.tx + tl.ty); // top/bottom (tx x R) and left/right (R x ty) strips
+    const int plane = nx * ny;                    // grid functions have < 2^31 points
+    // with one tile across x the left/right strips lie outside the box: zero, never loaded
+    const bool sides = tl.ntx > 1;
+    const int nhalo = sides ? 2 * R * (tl.tx + tl.ty) : 2 * R * tl.tx;
+    const C zero = {(T)0, (T)0};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int s = P.list[par * P.S + (int)(it / ntiles)], tile = (int)(it % ntiles);
         const Slot &sl = P.slots[s];
@@ -354,85 +396,127 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_cocg_pa(Params 
         const int gx = x0 + lx, gy = y0 + ly;
         const bool own = in_tile && gx < nx && gy < ny;
         const int col = gy * nx + gx;
+        auto pnew = [&](const C a, const C b) -> C {
+            C o;
+            o.x = a.x + br * b.x - bi * b.y;
+            o.y = a.y + br * b.y + bi * b.x;
+            return o;
+        };
+        // halo element e -> frame offset and in-plane grid offset (-1: outside the box)
+        auto halo_of = [&](int e, int &foff, int &goff) {
+            int hx, hy;
+            if (e < 2 * R * tl.tx) {                  // top / bottom strips
+                const int rr = e / tl.tx;
+                hx = e - rr * tl.tx + R;
+                hy = rr < R ? rr : tl.ty + rr;
+            } else {                                  // left / right strips
+                const int e2 = e - 2 * R * tl.tx;
+                const int cc = e2 / tl.ty;
+                hy = e2 - cc * tl.ty + R;
+                hx = cc < R ? cc : tl.tx + cc;
+            }
+            const int ax = x0 + hx - R, ay = y0 + hy - R;
+            foff = hy * W + hx;
+            goff = (ax >= 0 && ax < nx && ay >= 0 && ay < ny) ? ay * nx + ax : -1;
+        };
+        __syncthreads();                              // the previous item's readers are done
+        if (!sides) {                                 // zero the side strips of both frames
+            for (int e = threadIdx.x; e < 2 * R * tl.ty; e += blockDim.x) {
+                const int cc = e / tl.ty, hy = e - cc * tl.ty + R;
+                const int hx = cc < R ? cc : tl.tx + cc;
+                fr0[hy * W + hx] = zero;
+                fr1[hy * W + hx] = zero;
+            }
+        }
+        int hf[MAXH], hg[MAXH];
+        C hr[MAXH], hp[MAXH];
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h) {
+            const int e = threadIdx.x + h * blockDim.x;
+            hf[h] = -1;
+            hg[h] = -1;
+            if (e < nhalo) halo_of(e, hf[h], hg[h]);
+            hr[h] = zero;
+            hp[h] = zero;
+            if (hg[h] >= 0) {                         // plane 0
+                hr[h] = rs[hg[h]];
+                hp[h] = po[hg[h]];
+            }
+        }
+        // column window z = -6 .. 6 and the front planes 7, 8 (raw r, p_old)
         C qv[2 * R + 1];
 #pragma unroll
         for (int m = 0; m < 2 * R + 1; ++m) {
             const int z = m - R;
-            C v;
-            v.x = 0;
-            v.y = 0;
-            if (own && z >= 0 && z < nz) {
-                const C a = rs[col + z * plane], b = po[col + z * plane];
-                v.x = a.x + br * b.x - bi * b.y;
-                v.y = a.y + br * b.y + bi * b.x;
-            }
-            qv[m] = v;
+            qv[m] = (own && z >= 0 && z < nz) ? pnew(rs[col + z * plane], po[col + z * plane]) : zero;
         }
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int z = 0; z < nz; ++z) {
-            __syncthreads();                                   // previous plane's readers are done
-            if (in_tile) sm[(ly + R) * W + lx + R] = qv[R];
-            for (int e = threadIdx.x; e < nhalo; e += blockDim.x) {
-                int hx, hy;                                    // frame coordinates
-                if (e < 2 * R * tl.tx) {                       // top / bottom strips
-                    const int rr = e / tl.tx;
-                    hx = e - rr * tl.tx + R;
-                    hy = rr < R ? rr : tl.ty + rr;
-                } else {                                       // left / right strips
-                    const int e2 = e - 2 * R * tl.tx;
-                    const int cc = e2 / tl.ty;
-                    hy = e2 - cc * tl.ty + R;
-                    hx = cc < R ? cc : tl.tx + cc;
-                }
-                const int ax = x0 + hx - R, ay = y0 + hy - R;
-                C v;
-                v.x = 0;
-                v.y = 0;
-                if (ax >= 0 && ax < nx && ay >= 0 && ay < ny) {
-                    const int idx = z * plane + ay * nx + ax;
-                    const C a = rs[idx], b = po[idx];
-                    v.x = a.x + br * b.x - bi * b.y;
-                    v.y = a.y + br * b.y + bi * b.x;
-                }
-                sm[hy * W + hx] = v;
-            }
-            __syncthreads();
-            if (own) {
-                const int idx = col + z * plane;
-                const C c = qv[R];
-                const T dre = (T)3 * cf.a[0] + vloc[idx] + sre;
-                T re = dre * c.x - sim * c.y;
-                T im = dre * c.y + sim * c.x;
-                const C *cs = sm + (ly + R) * W + lx + R;
-#pragma unroll
-                for (int d = 1; d <= R; ++d) {
-                    const C a1 = cs[-d], a2 = cs[d], a3 = cs[-d * W], a4 = cs[d * W], a5 = qv[R - d], a6 = qv[R + d];
-                    re += cf.a[d] * (((a1.x + a2.x) + (a3.x + a4.x)) + (a5.x + a6.x));
-                    im += cf.a[d] * (((a1.y + a2.y) + (a3.y + a4.y)) + (a5.y + a6.y));
-                }
-                C y;
-                y.x = re;
-                y.y = im;
-                qs[idx] = y;
-                pn[idx] = c;
-                acc0 += (double)(c.x * y.x - c.y * y.y);
-                acc1 += (double)(c.x * y.y + c.y * y.x);
-            }
-            // advance the column window
-#pragma unroll
-            for (int m = 0; m < 2 * R; ++m) qv[m] = qv[m + 1];
-            C v;
-            v.x = 0;
-            v.y = 0;
-            const int zn = z + R + 1;
-            if (own && zn < nz) {
-                const C a = rs[col + zn * plane], b = po[col + zn * plane];
-                v.x = a.x + br * b.x - bi * b.y;
-                v.y = a.y + br * b.y + bi * b.x;
-            }
-            qv[2 * R] = v;
+        C f1r = zero, f1p = zero;          // raw front of plane z+R+1, consumed at the end of step z
+        if (own && R + 1 < nz) {
+            f1r = rs[col + (R + 1) * plane];
+            f1p = po[col + (R + 1) * plane];
         }
-        double acc[2] = {acc0, acc1};
+        T acc0 = 0, acc1 = 0;              // per-thread sums in the working precision (FP64 is slow)
+        // The z loop is unrolled by the window length: slot (u + m) % 13 of qv holds plane z-6+m,
+        // so the window turns without moving registers.
+        for (int z0 = 0; z0 < nz; z0 += 2 * R + 1) {
+#pragma unroll
+            for (int u = 0; u < 2 * R + 1; ++u) {
+                const int z = z0 + u;
+                if (z >= nz) break;
+                C *const fb = (z & 1) ? fr1 : fr0;
+                if (in_tile) fb[(ly + R) * W + lx + R] = qv[(u + R) % (2 * R + 1)];
+#pragma unroll
+                for (int h = 0; h < MAXH; ++h)
+                    if (hf[h] >= 0) fb[hf[h]] = hg[h] >= 0 ? pnew(hr[h], hp[h]) : zero;
+                for (int e = threadIdx.x + MAXH * blockDim.x; e < nhalo; e += blockDim.x) {   // rare: small blocks
+                    int foff, goff;
+                    halo_of(e, foff, goff);
+                    fb[foff] = goff >= 0 ? pnew(rs[z * plane + goff], po[z * plane + goff]) : zero;
+                }
+                // loads for later planes: halo of z+1, column front z+R+2
+                if (z + 1 < nz) {
+#pragma unroll
+                    for (int h = 0; h < MAXH; ++h)
+                        if (hg[h] >= 0) {
+                            hr[h] = rs[(z + 1) * plane + hg[h]];
+                            hp[h] = po[(z + 1) * plane + hg[h]];
+                        }
+                }
+                C f2r = zero, f2p = zero;
+                if (own && z + R + 2 < nz) {
+                    f2r = rs[col + (z + R + 2) * plane];
+                    f2p = po[col + (z + R + 2) * plane];
+                }
+                __syncthreads();
+                if (own) {
+                    const int idx = col + z * plane;
+                    const C c = qv[(u + R) % (2 * R + 1)];
+                    const T dre = (T)3 * cf.a[0] + vloc[idx] + sre;
+                    T re = dre * c.x - sim * c.y;
+                    T im = dre * c.y + sim * c.x;
+                    const C *cs = fb + (ly + R) * W + lx + R;
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        const C a1 = cs[-d], a2 = cs[d], a3 = cs[-d * W], a4 = cs[d * W];
+                        const C a5 = qv[(u + R - d) % (2 * R + 1)], a6 = qv[(u + R + d) % (2 * R + 1)];
+                        re += cf.a[d] * (((a1.x + a2.x) + (a3.x + a4.x)) + (a5.x + a6.x));
+                        im += cf.a[d] * (((a1.y + a2.y) + (a3.y + a4.y)) + (a5.y + a6.y));
+                    }
+                    C y;
+                    y.x = re;
+                    y.y = im;
+                    qs[idx] = y;
+                    pn[idx] = c;
+                    acc0 += c.x * y.x - c.y * y.y;
+                    acc1 += c.x * y.y + c.y * y.x;
+                }
+                // the front loaded one plane ago takes the slot of plane z-6
+                qv[u] = (own && z + R + 1 < nz) ? pnew(f1r, f1p) : zero;
+                f1r = f2r;
+                f1p = f2p;
+            }
+        }
+        double acc[2] = {(double)acc0, (double)acc1};
         block_sum_any<2>(acc);
         if (threadIdx.x == 0) {
             double *o = P.partA + ((long long)s * P.nparta + tile) * 2;
@@ -745,13 +829,15 @@ struct SolveSpec {
     std::vector<int> n, j;
 };
 
-// xy tiles of the stencil kernel: at most 64 columns wide, about 512 threads per block.
-Tiles pick_tiles(int nx, int ny) {
+// xy tiles of the stencil kernel: at most 64 columns wide and at most max_threads grid columns
+// (one thread each) per block.
+Tiles pick_tiles(int nx, int ny, int max_threads) {
     Tiles t;
     t.ntx = (nx + 63) / 64;
     t.tx = (nx + t.ntx - 1) / t.ntx;
-    int nty = (int)std::max(1LL, ((long long)ny * t.tx + 511) / 512);
-    t.ty = std::max(1, std::min((ny + nty - 1) / nty, 480 / t.tx));
+    const int ty_max = std::max(1, (max_threads - 31) / t.tx);
+    const int nty = (ny + ty_max - 1) / ty_max;
+    t.ty = (ny + nty - 1) / nty;
     t.nty = (ny + t.ty - 1) / t.ty;
     return t;
 }
@@ -808,7 +894,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         q = cv.take<double2>(n);
     }
     const long long pstride = (long long)n;
-    const Tiles tl = pick_tiles(c.nx, c.ny);
+    const Tiles tl = pick_tiles(c.nx, c.ny, mixed ? PaBounds<float>::threads : PaBounds<double>::threads);
     const int ntiles = tl.ntx * tl.nty;
     double *partA = (double *)c.cocg_partials.ensure(sizeof(double) * (size_t)S * (2 * ntiles + 3 * nblk));
     double *partB = partA + (size_t)S * ntiles * 2;
@@ -853,12 +939,20 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, (long long)dev_sms * 8));
     const unsigned wgrid = cdiv(S, kWarpsPerBlock);      // one warp per slot
     const int pa_threads = (tl.tx * tl.ty + 31) / 32 * 32;
-    const size_t pa_smem = (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);
+    const int pa_halo = tl.ntx > 1 ? 2 * kRadius * (tl.tx + tl.ty) : 2 * kRadius * tl.tx;
+    const bool pa_h1 = pa_halo <= pa_threads;
+    auto pa32 = pa_h1 ? k_cocg_pa<float, 1> : k_cocg_pa<float, 2>;
+    auto pa64 = pa_h1 ? k_cocg_pa<double, 1> : k_cocg_pa<double, 2>;
+    const size_t pa_smem = 2 * (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);
+    if (pa_smem > 48 * 1024) {
+        if (mixed) RPA_CUDA(cudaFuncSetAttribute(pa32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
+        else RPA_CUDA(cudaFuncSetAttribute(pa64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
+    }
     int pa_per_sm = 1;
     if (mixed)
-        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, k_cocg_pa<float>, pa_threads, pa_smem));
+        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, pa32, pa_threads, pa_smem));
     else
-        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, k_cocg_pa<double>, pa_threads, pa_smem));
+        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, pa64, pa_threads, pa_smem));
     const unsigned pa_grid = (unsigned)std::max<long long>(
         1, std::min<long long>((long long)S * ntiles, (long long)dev_sms * std::max(1, pa_per_sm)));
     const Coef<float> cf32 = cast_coef<float>(c.coef);
@@ -930,7 +1024,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             k_beta<<<wgrid, kThreads, 0, ss>>>(P, par);
             if (mixed) {
                 rec(t0 + 0);
-                k_cocg_pa<float><<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const float2 *)r, (float2 *)p,
+                pa32<<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const float2 *)r, (float2 *)p,
                                                                       pstride, (float2 *)q, c.vloc32, cf32);
                 rec(t0 + 1);
                 k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
@@ -940,7 +1034,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
                 rec(t0 + 3);
             } else {
                 rec(t0 + 0);
-                k_cocg_pa<double><<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const double2 *)r, (double2 *)p,
+                pa64<<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const double2 *)r, (double2 *)p,
                                                                         pstride, (double2 *)q, c.vloc64, cf64);
                 rec(t0 + 1);
                 k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
