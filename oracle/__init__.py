@@ -15,8 +15,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   frequency_quadrature  closed-form integrals of rational functions on [0, inf)
   rpa_ec                dense eigenvalues of nu^1/2 chi0 nu^1/2 at full rank; adaptive
                         quadrature of the dense integrand; convergence in N_omega
+  rpa_ec_gradient       central finite differences of a dense sum-over-states E_c built
+                        from the unoccupied eigenpairs of the projected Hamiltonian
 """
 from .rpa_oracle import *  # noqa: F401,F403
 from .rpa_oracle import (Oracle, Grid, Coulomb, SolveStats, EcResult, fd_weights, apply_h, cocg,  # noqa: F401
                          frequency_quadrature, g_rpa, orthonormalize_cholesky, rpa_ec, num_threads,
-                         set_threads, second_difference_1d, NotSPD)
+                         set_threads, second_difference_1d, NotSPD, rpa_ec_gradient)

@@ -237,12 +237,15 @@ class Oracle:
 
     def chi0(self, dv: np.ndarray, omega: float, tol: float, maxit: int = 100000, sign: int = +1,
              stats: Optional[SolveStats] = None, max_chunk_bytes: float = 2.5e8,
-             galerkin: bool = False, return_x: bool = False):
+             galerkin: bool = False, return_x: bool = False, project_solution: bool = False):
         """drho = chi0(i omega) dV for every row of dv (Eqs. 7-9).
 
         For each occupied n and each dV: solve (H - eps_n + sign*i*omega) x = b by COCG, then
         drho = (4/h^3) Re sum_n u_n (.) x_n.  galerkin=True takes the paper's Galerkin
         initial guess instead of projecting the right-hand side (Section "Implementation").
+        project_solution=True also removes the occupied components of x (x <- P_c x): the same
+        operator when the orbitals are exact eigenvectors of H, and the first-order-consistent
+        response of the fixed occupied space when V_loc moves away from them.
         """
         g = self.grid
         dv = np.atleast_2d(np.asarray(dv, dtype=np.float64))
@@ -263,6 +266,8 @@ class Oracle:
                     if stats is not None:
                         stats.iterations.append(it)
                         stats.status.append(st)
+                if project_solution:
+                    x = x - (x @ self.psi.T) @ self.psi
                 drho[j0:j0 + chunk] += (4.0 / g.h ** 3) * np.real(self.psi[n][None, :] * x)
                 if return_x:
                     xs.append((n, j0, x))
@@ -288,12 +293,29 @@ class Oracle:
         return x0 + d
 
     def chi_tilde(self, V: np.ndarray, omega: float, tol: float, maxit: int = 100000,
-                  stats: Optional[SolveStats] = None) -> np.ndarray:
+                  stats: Optional[SolveStats] = None, project_solution: bool = False) -> np.ndarray:
         """R = nu^1/2 chi0(i omega) nu^1/2 V for every row of V (Algorithm 1: V_j = N V_j,
         Sternheimer loop over n, R_j = N R_j)."""
         vt = self.coulomb.apply(V, 0.5)
-        drho = self.chi0(vt, omega, tol, maxit, stats=stats)
+        drho = self.chi0(vt, omega, tol, maxit, stats=stats, project_solution=project_solution)
         return self.coulomb.apply(drho, 0.5)
+
+    def response_square(self, Y: np.ndarray, omega: float, coef: np.ndarray, tol: float,
+                        maxit: int = 100000) -> np.ndarray:
+        """sum_i coef_i (4/h^3) Re sum_n x_{n,i}(r)^2 with x_{n,i} the projected Sternheimer
+        solutions for dV = nu^1/2 y_i (rows of Y): the derivative of y_i^T chi~0 y_i with respect to
+        V_loc(r) at fixed orbitals (the adjoint solve is the forward solve, A being complex
+        symmetric)."""
+        g = self.grid
+        vt = self.coulomb.apply(Y, 0.5)
+        out = np.zeros(g.n_d)
+        for n in range(self.n_s):
+            sigma = -self.eps[n] + 1j * omega
+            b = self.sternheimer_rhs(n, vt).astype(np.complex128)
+            x, it, st = cocg(g, self.vloc, np.full(len(vt), sigma), b, tol, maxit)
+            x = x - (x @ self.psi.T) @ self.psi
+            out += (4.0 / g.h ** 3) * (coef[:, None] * np.real(x * x)).sum(axis=0)
+        return out
 
     def nu_chi0(self, V: np.ndarray, omega: float, tol: float, maxit: int = 100000,
                 stats: Optional[SolveStats] = None) -> np.ndarray:
@@ -344,11 +366,13 @@ class EcResult:
     sternheimer_solves: int = 0
     cocg_iterations: int = 0
     V_final: Optional[np.ndarray] = None
+    ritz_vectors: Optional[List[np.ndarray]] = None   # per frequency (ascending omega), rows y_i
 
 
 def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, omega0: float = 1.0,
            max_subspace_iters: int = 100, fixed_iters: Optional[int] = None, maxit: int = 100000,
-           verbose: bool = False) -> EcResult:
+           verbose: bool = False, project_solution: bool = False, keep_ritz: bool = False,
+           independent_frequencies: bool = False) -> EcResult:
     """E_c by Algorithm 1 with Rayleigh-Ritz: frequencies from highest to lowest, the subspace
     carried over from each frequency to the next; at each frequency iterate
     R = chi~0 V, C = V^T R, lambda = eig(C), E_cm = (w_m/2pi) sum g(lambda), M = R^T R = L L^T,
@@ -362,15 +386,21 @@ def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, om
     iters = np.zeros(n_omega, dtype=np.int64)
     stats = SolveStats()
     thr = eps_c * o.n_atoms / n_omega
+    ritz = [None] * n_omega
+    V_start = V
     for m in range(n_omega - 1, -1, -1):
+        if independent_frequencies:
+            V = V_start
         ecm = 0.0
         it = 0
         while True:
             ecm_old = ecm
-            R = o.chi_tilde(V, omegas[m], tol, maxit, stats=stats)
+            R = o.chi_tilde(V, omegas[m], tol, maxit, stats=stats, project_solution=project_solution)
             C = V @ R.T
             C = 0.5 * (C + C.T)
-            lam = np.linalg.eigvalsh(C)
+            lam, Qc = np.linalg.eigh(C)
+            if keep_ritz:
+                ritz[m] = Qc.T @ V
             ecm = weights[m] / (2.0 * math.pi) * float(np.sum(g_rpa(lam)))
             V = orthonormalize_cholesky(R)
             it += 1
@@ -386,4 +416,23 @@ def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, om
         iters[m] = it
     e_c = float(np.sum(e_m))
     return EcResult(e_c, e_c / o.n_atoms, e_m, lambdas, omegas, weights, iters,
-                    stats.n_solves(), stats.total_iterations(), V)
+                    stats.n_solves(), stats.total_iterations(), V, ritz if keep_ritz else None)
+
+
+def rpa_ec_gradient(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, omega0: float = 1.0,
+                    max_subspace_iters: int = 100, fixed_iters: Optional[int] = None, maxit: int = 100000,
+                    independent_frequencies: bool = False):
+    """dE_c/dV_loc(r) at fixed occupied orbitals and eigenvalues, by Hellmann-Feynman on the Ritz
+    pairs of the last subspace iteration at each frequency:
+        dE_c/dV(r) = (1/2pi) sum_m w_m sum_i g'(lambda_i) d lambda_i/dV(r),  g'(x) = -x/(1-x),
+        d lambda_i/dV(r) = (4/h^3) Re sum_n x_{n,i}(r)^2
+    where x_{n,i} solves the projected Sternheimer system for dV = nu^1/2 y_i.  E_c is evaluated
+    with the projected response (project_solution).  Returns (EcResult, gradient)."""
+    res = rpa_ec(o, V0, n_omega, tol, eps_c, omega0, max_subspace_iters, fixed_iters, maxit,
+                 project_solution=True, keep_ritz=True, independent_frequencies=independent_frequencies)
+    grad = np.zeros(o.grid.n_d)
+    for m in range(n_omega):
+        lam = res.lambdas[m]
+        coef = res.weights[m] / (2.0 * math.pi) * (-lam / (1.0 - lam))
+        grad += o.response_square(res.ritz_vectors[m], res.omegas[m], coef, tol, maxit)
+    return res, grad

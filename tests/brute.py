@@ -51,3 +51,36 @@ def nu_power_dense(nx, ny, nz, h, power):
 def chi_tilde_dense(system, omega):
     nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5)
     return nh @ chi0_sum_over_states(system, omega) @ nh
+
+
+def chi0_projected_sos(system, vloc, omega):
+    """chi0(i omega) at fixed occupied orbitals u_i and eigenvalues eps_i for the potential vloc:
+    the unoccupied states are the eigenpairs (phi_a, e_a) of the Hamiltonian H(vloc) restricted
+    to the orthogonal complement of span{u_i}; then
+        chi0 = (4/h^3) sum_{i,a} (u_i phi_a)(u_i phi_a)^T (eps_i - e_a) / ((eps_i - e_a)^2 + omega^2).
+    At the potential the orbitals belong to, this is the sum over states of Eq. 2."""
+    import scipy.linalg as sla
+    s2 = synth.System(system.name, system.nx, system.ny, system.nz, system.h, np.asarray(vloc),
+                      system.psi, system.eps, system.n_atoms)
+    H = dense_h(s2)
+    Q = sla.null_space(system.psi)
+    e, Z = np.linalg.eigh(Q.T @ H @ Q)
+    Phi = (Q @ Z).T
+    X = np.zeros((system.n_d, system.n_d))
+    for i in range(system.n_s):
+        d = system.eps[i] - e
+        f = d / (d * d + omega * omega)
+        P = system.psi[i][None, :] * Phi
+        X += (P.T * f) @ P
+    return (4.0 / system.h ** 3) * X
+
+
+def ec_projected_dense(system, vloc, n_r, omegas, weights):
+    """E_c = (1/2pi) sum_m w_m sum_{i < n_r} g(lambda_i) over the n_r lowest eigenvalues of
+    nu^1/2 chi0 nu^1/2, chi0 from chi0_projected_sos."""
+    nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5)
+    e = 0.0
+    for om, w in zip(omegas, weights):
+        lam = np.linalg.eigvalsh(nh @ chi0_projected_sos(system, vloc, om) @ nh)[:n_r]
+        e += w / (2.0 * math.pi) * float(np.sum(np.log1p(-lam) + lam))
+    return e

@@ -241,3 +241,54 @@ def test_ec_quadrature_against_adaptive_integral():
     x8, w8 = oracle.frequency_quadrature(8)
     val8 = sum(wi * F(xi) for xi, wi in zip(x8, w8)) / (2 * math.pi)
     assert abs(val8 - ref) < 1e-2 * abs(ref)
+
+
+# ------------------------------------------------------------------ adjoint dE_c/dV_loc
+def test_projected_sos_reduces_to_sum_over_states(cube):
+    """At the potential the orbitals belong to, the fixed-orbital response equals Eq. 2."""
+    a = brute.chi0_projected_sos(cube, cube.vloc, 0.6)
+    b = brute.chi0_sum_over_states(cube, 0.6)
+    assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
+
+
+def test_ec_gradient_matches_finite_differences_of_dense_sos():
+    s = synth.small_system((6, 5, 5), h=0.6, n_s=2, n_wells=2, seed=23)
+    o = oracle.Oracle.from_system(s)
+    n_r, n_omega = 3, 2
+    V0 = synth.trial_vectors(23, n_r, s.n_d)
+    res, grad = oracle.rpa_ec_gradient(o, V0, n_omega, tol=1e-13, eps_c=1e-15, max_subspace_iters=600)
+    # the oracle's E_c is the dense projected-SOS E_c of the same n_r eigenvalues
+    ref = brute.ec_projected_dense(s, s.vloc, n_r, res.omegas, res.weights)
+    assert abs(res.e_c - ref) < 1e-10 * abs(ref)
+    rng = np.random.default_rng(0)
+    pts = rng.choice(s.n_d, 6, replace=False)
+    d = 1e-4
+    for r in pts:
+        vp, vm = s.vloc.copy(), s.vloc.copy()
+        vp[r] += d
+        vm[r] -= d
+        fd = (brute.ec_projected_dense(s, vp, n_r, res.omegas, res.weights)
+              - brute.ec_projected_dense(s, vm, n_r, res.omegas, res.weights)) / (2 * d)
+        assert abs(grad[r] - fd) < 1e-6 * np.max(np.abs(grad)), (r, grad[r], fd)
+
+
+def test_frozen_subspace_gradient_is_exact_derivative():
+    """With every frequency starting from the same fixed subspace and one Rayleigh-Ritz step
+    (independent_frequencies), E_c is a smooth function of V_loc whose derivative is exactly the
+    Hellmann-Feynman gradient; finite differences of the oracle's own E_c must agree."""
+    s = synth.small_system((7, 6, 6), h=0.55, n_s=2, n_wells=2, seed=29)
+    o = oracle.Oracle.from_system(s)
+    V0 = synth.trial_vectors(29, 4, s.n_d)
+    kw = dict(n_omega=2, tol=1e-13, eps_c=0.0, fixed_iters=1, independent_frequencies=True)
+    res, grad = oracle.rpa_ec_gradient(o, V0, **kw)
+    d = 1e-4
+    for r in np.random.default_rng(1).choice(s.n_d, 4, replace=False):
+        e = []
+        for sgn in (1, -1):
+            v = s.vloc.copy()
+            v[r] += sgn * d
+            o2 = oracle.Oracle(s.nx, s.ny, s.nz, s.h, v, s.psi, s.eps, s.n_atoms)
+            e.append(oracle.rpa_ec(o2, V0, 2, 1e-13, 0.0, fixed_iters=1, project_solution=True,
+                                   independent_frequencies=True).e_c)
+        fd = (e[0] - e[1]) / (2 * d)
+        assert abs(grad[r] - fd) < 1e-6 * np.max(np.abs(grad)), (r, grad[r], fd)
