@@ -42,8 +42,8 @@ def parse():
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tts", action="store_true", help="also time E_c to convergence (eps_c 1e-5 Ha/atom)")
-    ap.add_argument("--fp64-compare", action="store_true", help="also time one step of the plain FP64 form")
+    ap.add_argument("--no-tts", action="store_true", help="skip the E_c time-to-solution run (eps_c 1e-5 Ha/atom)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the step of the plain FP64 form")
     return ap.parse_args()
 
 
@@ -100,6 +100,30 @@ class Clocks:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic(kernel_name, points_per_launch):
+    """DRAM bytes per launch of a COCG kernel from the committed ncu summary, scaled from the
+    captured launch to this launch size by grid points.  None when the summary is missing or the
+    kernel source changed since the counters were taken."""
+    import hashlib
+    fname = {"k_cocg_pa<c64>": "k_cocg_pa_mixed40.txt", "k_cocg_b<c64>": "k_cocg_b_mixed40.txt"}.get(kernel_name)
+    if not fname:
+        return None
+    path = os.path.join(ROOT, "profiles", fname)
+    src = os.path.join(ROOT, "paper_2504_01816_gb300", "csrc", "cocg.cu")
+    try:
+        info = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info[k.strip()] = v.strip()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if info.get("source_sha1") != sha:
+            return None
+        return float(info["dram_bytes_per_point"]) * points_per_launch
+    except Exception:
+        return None
 
 
 def measured_peaks():
@@ -261,18 +285,23 @@ def run_ours(args):
         agg = {}
         for st in kstats:
             for k in st.get("kernels", []):
-                a = agg.setdefault(k["name"], {"ms": 0.0, "launches": 0, "bytes": 0.0})
+                a = agg.setdefault(k["name"], {"ms": 0.0, "launches": 0, "bytes": 0.0, "points": 0.0})
                 a["ms"] += k["ms"]
                 a["launches"] += k["launches"]
                 a["bytes"] += k["bytes"]
+                a["points"] += k["points"]
         roofline = None
         if agg:
             name, a = max(agg.items(), key=lambda kv: kv[1]["ms"])
             per_launch_s = a["ms"] / 1e3 / max(a["launches"], 1)
             bytes_per_launch = a["bytes"] / max(a["launches"], 1)
             achieved = bytes_per_launch / per_launch_s / 1e9
+            pts_per_launch = a.get("points", 0.0) / max(a["launches"], 1)
+            tr = kernel_traffic(name, pts_per_launch)
             roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved / hbm, "traffic": None,
+                        "frac": achieved / hbm, "traffic": tr,
+                        "algorithmic_bytes_per_launch": bytes_per_launch,
+                        "points_per_launch": pts_per_launch,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
                         "share_of_step": a["ms"] / total_ms, "avg_launch_us": 1e6 * per_launch_s}
         mean_iters = sum(st["cocg_iterations"] for st in kstats) / max(sum(st["sternheimer_solves"] for st in kstats), 1)
@@ -288,9 +317,11 @@ def run_ours(args):
                            "mean_cocg_iterations_per_solve": mean_iters,
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": int(sum(st.get("launches", 0) for st in kstats)),
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "share_of_step": v["ms"] / total_ms,
+                                "achieved_gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6} for k, v in agg.items()},
                 "clocks": clk, "e2e": e2e, "roofline": roofline,
                 "e_c_per_atom_last_step": res.e_c_per_atom}
-    if args.fp64_compare and rank == 0:
+    if not args.no_fp64 and rank == 0:
         o64 = rpa.default_options()
         for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "profile"):
             setattr(o64, k, getattr(opts, k))
@@ -303,19 +334,23 @@ def run_ours(args):
         e1.synchronize()
         line["fp64_form"] = {"value": r64.stats["sternheimer_solves"] / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
                              "ms_per_step": e0.elapsed_time(e1),
+                             "mixed_speedup": e0.elapsed_time(e1) / (total_ms / args.steps),
+                             "mean_cocg_iterations_per_solve": r64.stats["cocg_iterations"] / max(r64.stats["sternheimer_solves"], 1),
                              "max_abs_dlambda_vs_mixed": float(np.max(np.abs(r64.lambdas - res.lambdas))),
                              "de_c_per_atom_vs_mixed": float(r64.e_c_per_atom - res.e_c_per_atom)}
         ctx.set_options(opts)
-    if args.tts and rank == 0:
+    if not args.no_tts and rank == 0:
         ot = rpa.default_options()
         for k in ("prec", "tol", "n_omega", "n_atoms", "profile"):
             setattr(ot, k, getattr(opts, k))
         ot.eps_c = 1e-5
         ot.fixed_subspace_iters = 0
         ctx.set_options(ot)
+        torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         rt = ctx.ec(V0)
         line["time_to_solution"] = {"seconds": time.perf_counter() - t0, "e_c_per_atom": rt.e_c_per_atom,
+                                    "prec": args.prec,
                                     "eps_c_ha_per_atom": 1e-5,
                                     "subspace_iterations": rt.stats["subspace_iterations"],
                                     "sternheimer_solves": rt.stats["sternheimer_solves"]}

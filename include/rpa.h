@@ -64,7 +64,7 @@ typedef struct {
     int prec;                  /* rpa_precision */
     double tol;                /* COCG: stop when ||b - A x||_2 <= tol ||b||_2 (Hermitian norm) */
     int maxit;                 /* COCG: iteration limit per system (FP64) or per inner solve (mixed) */
-    int max_refine;            /* mixed: limit on FP64 refinement cycles per system */
+    int max_refine;            /* mixed: limit on FP64 residual evaluations per system */
     double inner_tol;          /* mixed: relative residual reduction asked of each FP32 inner solve */
     double eps_c;              /* subspace iteration: stop when |dE_c,m| <= eps_c * n_atoms / n_omega (Ha/atom) */
     int n_omega;               /* Gauss-Legendre frequency count (<= 64) */
@@ -75,6 +75,15 @@ typedef struct {
     int batch_systems;         /* Sternheimer systems in flight at once (0 = automatic) */
     int profile;               /* != 0: time every launch of the COCG kernels with CUDA events and
                                   count the grid points they process (filled into rpa_stats.prof_*) */
+    int project_solution;      /* != 0: also remove the occupied components of every Sternheimer
+                                  solution (x <- P_c x).  The same chi0 when the orbitals are exact
+                                  eigenvectors of H; when V_loc differs from the potential the
+                                  orbitals belong to, it is the response of the fixed occupied space
+                                  (the function rpa_ec_gradient differentiates) */
+    int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
+                                  the next higher frequency (no warm start, Algorithm 1 carries it);
+                                  with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
+                                  of the fixed subspace span(V0) at every frequency */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8
@@ -107,7 +116,7 @@ typedef struct {
 
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
- * profile 0. */
+ * profile 0, project_solution 0, independent_frequencies 0. */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).
@@ -153,6 +162,22 @@ rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, dou
  * ec_per_omega_host n_omega weighted contributions (w_m/2pi) sum_i g(lambda_i); stats. */
 rpa_status rpa_ec(rpa_ctx *ctx, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host,
                   double *ec_per_omega_host, rpa_stats *stats, void *stream);
+
+/* dE_c/dV_loc(r) at fixed occupied orbitals and eigenvalues (the adjoint of rpa_ec).
+ *
+ * Runs rpa_ec with project_solution on, then at every frequency takes the Ritz pairs
+ * (lambda_i, y_i) of the last subspace iteration and, by Hellmann-Feynman,
+ *     dE_c/dV(r) = (1/2pi) sum_m w_m sum_i g'(lambda_i) d lambda_i/dV(r),  g'(x) = -x/(1-x),
+ *     d lambda_i/dV(r) = (4/h^3) Re sum_n x_{n,i}(r)^2,
+ * where x_{n,i} is the projected Sternheimer solution for dV = nu^1/2 y_i.  The Sternheimer
+ * operator is complex symmetric, so the adjoint solve is the forward solve; the solutions are
+ * recomputed (one extra Sternheimer pass per frequency), never stored.  This derivative is not
+ * in the paper; it differentiates the method's E_c (Eq. 10).
+ * grad_dev: N_d doubles (written).  V_out_dev: N_d x n_r, the final subspace (may be NULL).
+ * The other arguments and outputs are those of rpa_ec. */
+rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *grad_dev, double *V_out_dev,
+                           double *lambdas_host, double *ec_host, double *ec_per_omega_host, rpa_stats *stats,
+                           void *stream);
 
 /* Size of the fixed device scratch array used by rpa_coulomb_apply_noalloc (64 MiB).  Every
  * GPU on which the library is loaded keeps this much memory reserved until the process exits. */

@@ -12,6 +12,7 @@
 namespace rpa {
 
 static thread_local std::string g_last_error;
+thread_local long long g_launches = 0;
 
 void fail(rpa_status st, const char *fmt, ...) {
     char buf[512];
@@ -57,7 +58,7 @@ Ctx::~Ctx() {
     for (double *q : Q) cudaFree(q);
     cudaFree(lam);
     for (DevBuf *b : {&cocg_state, &cocg_partials, &sys_state, &rhs, &pc_coef, &coul_tmp, &blockA, &blockB,
-                      &blockC, &blockD, &small, &slot_idx, &dense_scratch})
+                      &blockC, &blockD, &small, &slot_idx, &dense_scratch, &proj_buf, &coef_buf, &blockE})
         b->release();
     if (h_state) cudaFreeHost(h_state);
     if (h_count) cudaFreeHost(h_count);
@@ -213,6 +214,8 @@ void rpa_default_options(rpa_options *o) {
     o->n_atoms = 1;
     o->batch_systems = 0;
     o->profile = 0;
+    o->project_solution = 0;
+    o->independent_frequencies = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }
@@ -359,110 +362,178 @@ rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, dou
     return (rpa_status)worst;
 }
 
+}  // extern "C"
+
+namespace rpa {
+namespace {
+
+// Algorithm 1 with Rayleigh-Ritz; with grad != nullptr also dE_c/dV_loc (see rpa_ec_gradient).
+int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host, double *ec_per_omega_host,
+            rpa_stats *stats, cudaStream_t s, double *grad, double *V_out) {
+    int worst = 0;
+    if (n_r < 1 || n_r > c.nd) fail(RPA_ERR_INVALID, "n_r must be in [1, N_d]");
+    if (n_r > 1024) fail(RPA_ERR_INVALID, "n_r above 1024 is not supported");
+    std::memset(&c.stats, 0, sizeof c.stats);
+    g_launches = 0;
+    const rpa_options &o = c.opt;
+    const int nw = o.n_omega;
+    double om[kMaxOmega], wt[kMaxOmega];
+    frequency_rule(nw, o.omega0, om, wt);
+    for (int m = 0; m < nw; ++m) {
+        c.stats.omegas[m] = om[m];
+        c.stats.weights[m] = wt[m];
+    }
+    const size_t blk = sizeof(double) * (size_t)n_r * c.nd;
+    double *V = (double *)c.blockA.ensure(blk);
+    double *R = (double *)c.blockB.ensure(blk);
+    double *T1 = (double *)c.blockC.ensure(blk);
+    double *T2 = (double *)c.blockD.ensure(blk);
+    double *Vprev = grad ? (double *)c.blockE.ensure(blk) : nullptr;
+    const size_t nn = (size_t)n_r * n_r;
+    char *sm = (char *)c.small.ensure(sizeof(double) * (5 * nn + 4 * (size_t)n_r + 8) + 64);
+    double *Cm = (double *)sm;            // projection / overlap
+    double *Lm = Cm + nn;                 // inverse factor
+    double *Wm = Lm + nn;                 // copy for the eigen solve
+    double *Cprev = Wm + nn;              // projected matrix of the last iteration (gradient)
+    double *Sm = Cprev + nn;              // rotation to Ritz vectors (gradient)
+    double *lam = Sm + nn;
+    double *work = lam + n_r;             // 3 n_r
+    double *ecm_dev = work + 3 * (size_t)n_r;
+    int *info = (int *)(ecm_dev + 2);
+    std::vector<double> h_lam(n_r), h_scal(2);
+    int h_info = 0;
+    if (grad) RPA_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * c.nd, s));
+
+    cudaEvent_t t0, t1;
+    RPA_CUDA(cudaEventCreate(&t0));
+    RPA_CUDA(cudaEventCreate(&t1));
+    RPA_CUDA(cudaEventRecord(t0, s));
+
+    // Y = X L^{-T}, L L^T = X^T X (rows: Y = L^{-1} X)
+    auto orthonormalize = [&](const double *X, double *Y) {
+        gram(X, n_r, X, n_r, c.nd, Cm, s, c.dense_scratch);
+        symmetrize(Cm, n_r, s);
+        cholesky(Cm, n_r, info, s);
+        RPA_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RPA_CUDA(cudaStreamSynchronize(s));
+        if (h_info != 0) fail(RPA_ERR_NOT_SPD, "overlap matrix not positive definite (pivot %d)", h_info - 1);
+        tri_inverse(Cm, n_r, Lm, s);
+        combine_rows(Lm, n_r, n_r, X, c.nd, Y, s);
+    };
+    orthonormalize(V0_dev, V);
+
+    double ec = 0.0;
+    std::vector<double> ecm_all(nw, 0.0);
+    const double thr = o.eps_c * o.n_atoms / nw;
+    for (int m = nw - 1; m >= 0; --m) {
+        if (o.independent_frequencies && m != nw - 1) orthonormalize(V0_dev, V);
+        double ecm = 0.0;
+        int it = 0;
+        for (;;) {
+            const double ecm_old = ecm;
+            const int w = apply_nuchi0_impl(c, om[m], V, R, n_r, 1, T1, T2, s);
+            worst = std::max(worst, w);
+            cudaEvent_t a, b;
+            RPA_CUDA(cudaEventCreate(&a));
+            RPA_CUDA(cudaEventCreate(&b));
+            RPA_CUDA(cudaEventRecord(a, s));
+            // Rayleigh-Ritz: C = V^T R, eigenvalues, E_cm = (w_m / 2 pi) sum g(lambda)
+            gram(V, n_r, R, n_r, c.nd, Wm, s, c.dense_scratch);
+            symmetrize(Wm, n_r, s);
+            if (grad) {
+                RPA_CUDA(cudaMemcpyAsync(Cprev, Wm, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+                RPA_CUDA(cudaMemcpyAsync(Vprev, V, blk, cudaMemcpyDeviceToDevice, s));
+            }
+            sym_eigvals(Wm, n_r, lam, work, wt[m] / (2.0 * M_PI), ecm_dev, s);
+            // orthonormalisation: M = R^T R = L L^T, V = R L^{-T}
+            orthonormalize(R, V);
+            RPA_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * n_r, cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaMemcpyAsync(h_scal.data(), ecm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaEventRecord(b, s));
+            RPA_CUDA(cudaEventSynchronize(b));
+            c.stats.ms_subspace += ms_between(a, b);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            ecm = h_scal[0];
+            ++it;
+            if (o.fixed_subspace_iters > 0) {
+                if (it >= o.fixed_subspace_iters) break;
+            } else if (std::fabs(ecm - ecm_old) <= thr || it >= o.max_subspace_iters) {
+                break;
+            }
+        }
+        c.stats.subspace_iterations[m] = it;
+        ecm_all[m] = ecm;
+        ec += ecm;
+        if (lambdas_host) std::memcpy(lambdas_host + (size_t)m * n_r, h_lam.data(), sizeof(double) * n_r);
+        if (grad) {
+            // Ritz pairs of the last iteration: C = Q diag(lambda) Q^T, y_i = sum_k Q[k][i] v_k
+            std::vector<double> Ch(nn), wv, Q;
+            RPA_CUDA(cudaMemcpyAsync(Ch.data(), Cprev, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaStreamSynchronize(s));
+            jacobi_eigh(Ch, n_r, wv, Q);
+            std::vector<double> S(nn), coef(n_r);
+            for (int i = 0; i < n_r; ++i) {
+                coef[i] = wt[m] / (2.0 * M_PI) * (-wv[i] / (1.0 - wv[i]));   // (w_m / 2pi) g'(lambda_i)
+                for (int k = 0; k < n_r; ++k) S[(size_t)i * n_r + k] = Q[(size_t)k * n_r + i];
+            }
+            RPA_CUDA(cudaMemcpyAsync(Sm, S.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+            combine_rows(Sm, n_r, n_r, Vprev, c.nd, T1, s);           // Ritz vectors
+            coulomb_apply(c, 0.5, T1, T2, n_r, s);                    // nu^1/2 y_i
+            worst = std::max(worst, response_square(c, om[m], T2, coef.data(), grad, n_r, s));
+        }
+    }
+    if (V_out) RPA_CUDA(cudaMemcpyAsync(V_out, V, blk, cudaMemcpyDeviceToDevice, s));
+    RPA_CUDA(cudaEventRecord(t1, s));
+    RPA_CUDA(cudaEventSynchronize(t1));
+    c.stats.ms_total = ms_between(t0, t1);
+    c.stats.launches = g_launches;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (ec_host) {
+        ec_host[0] = ec;
+        ec_host[1] = ec / o.n_atoms;
+    }
+    if (ec_per_omega_host) std::memcpy(ec_per_omega_host, ecm_all.data(), sizeof(double) * nw);
+    if (stats) *stats = c.stats;
+    return worst;
+}
+
+}  // namespace
+}  // namespace rpa
+
+extern "C" {
+
 rpa_status rpa_ec(rpa_ctx *ctx, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host,
                   double *ec_per_omega_host, rpa_stats *stats, void *stream) {
     int worst = 0;
     rpa_status st = guarded([&] {
         if (!ctx || !V0_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        worst = ec_impl(ctx->impl, n_r, V0_dev, lambdas_host, ec_host, ec_per_omega_host, stats, as_stream(stream),
+                        nullptr, nullptr);
+    });
+    if (st != RPA_OK) return st;
+    if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
+    return (rpa_status)worst;
+}
+
+rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *grad_dev, double *V_out_dev,
+                           double *lambdas_host, double *ec_host, double *ec_per_omega_host, rpa_stats *stats,
+                           void *stream) {
+    int worst = 0;
+    rpa_status st = guarded([&] {
+        if (!ctx || !V0_dev || !grad_dev) fail(RPA_ERR_INVALID, "NULL argument");
         Ctx &c = ctx->impl;
-        if (n_r < 1 || n_r > c.nd) fail(RPA_ERR_INVALID, "n_r must be in [1, N_d]");
-        if (n_r > 1024) fail(RPA_ERR_INVALID, "n_r above 1024 is not supported");
-        cudaStream_t s = as_stream(stream);
-        std::memset(&c.stats, 0, sizeof c.stats);
-        const rpa_options &o = c.opt;
-        const int nw = o.n_omega;
-        double om[kMaxOmega], wt[kMaxOmega];
-        frequency_rule(nw, o.omega0, om, wt);
-        for (int m = 0; m < nw; ++m) {
-            c.stats.omegas[m] = om[m];
-            c.stats.weights[m] = wt[m];
+        const int saved = c.opt.project_solution;
+        c.opt.project_solution = 1;
+        try {
+            worst = ec_impl(c, n_r, V0_dev, lambdas_host, ec_host, ec_per_omega_host, stats, as_stream(stream),
+                            grad_dev, V_out_dev);
+        } catch (...) {
+            c.opt.project_solution = saved;
+            throw;
         }
-        const size_t blk = sizeof(double) * (size_t)n_r * c.nd;
-        double *V = (double *)c.blockA.ensure(blk);
-        double *R = (double *)c.blockB.ensure(blk);
-        double *T1 = (double *)c.blockC.ensure(blk);
-        double *T2 = (double *)c.blockD.ensure(blk);
-        const size_t nn = (size_t)n_r * n_r;
-        char *sm = (char *)c.small.ensure(sizeof(double) * (3 * nn + 4 * (size_t)n_r + 8) + 64);
-        double *Cm = (double *)sm;            // projection / overlap
-        double *Lm = Cm + nn;                 // inverse factor
-        double *Wm = Lm + nn;                 // copy for the eigen solve
-        double *lam = Wm + nn;
-        double *work = lam + n_r;             // 3 n_r
-        double *ecm_dev = work + 3 * (size_t)n_r;
-        int *info = (int *)(ecm_dev + 2);
-        std::vector<double> h_lam(n_r), h_scal(2);
-        int h_info = 0;
-
-        cudaEvent_t t0, t1;
-        RPA_CUDA(cudaEventCreate(&t0));
-        RPA_CUDA(cudaEventCreate(&t1));
-        RPA_CUDA(cudaEventRecord(t0, s));
-
-        // V = V0 L^{-T}, L L^T = V0^T V0 (rows: V = L^{-1} V0)
-        auto orthonormalize = [&](const double *X, double *Y) {
-            gram(X, n_r, X, n_r, c.nd, Cm, s, c.dense_scratch);
-            symmetrize(Cm, n_r, s);
-            cholesky(Cm, n_r, info, s);
-            RPA_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s));
-            RPA_CUDA(cudaStreamSynchronize(s));
-            if (h_info != 0) fail(RPA_ERR_NOT_SPD, "overlap matrix not positive definite (pivot %d)", h_info - 1);
-            tri_inverse(Cm, n_r, Lm, s);
-            combine_rows(Lm, n_r, n_r, X, c.nd, Y, s);
-        };
-        orthonormalize(V0_dev, V);
-
-        double ec = 0.0;
-        std::vector<double> ecm_all(nw, 0.0);
-        const double thr = o.eps_c * o.n_atoms / nw;
-        for (int m = nw - 1; m >= 0; --m) {
-            double ecm = 0.0;
-            int it = 0;
-            for (;;) {
-                const double ecm_old = ecm;
-                const int w = apply_nuchi0_impl(c, om[m], V, R, n_r, 1, T1, T2, s);
-                worst = std::max(worst, w);
-                cudaEvent_t a, b;
-                RPA_CUDA(cudaEventCreate(&a));
-                RPA_CUDA(cudaEventCreate(&b));
-                RPA_CUDA(cudaEventRecord(a, s));
-                // Rayleigh-Ritz: C = V^T R, eigenvalues, E_cm = (w_m / 2 pi) sum g(lambda)
-                gram(V, n_r, R, n_r, c.nd, Wm, s, c.dense_scratch);
-                symmetrize(Wm, n_r, s);
-                sym_eigvals(Wm, n_r, lam, work, wt[m] / (2.0 * M_PI), ecm_dev, s);
-                // orthonormalisation: M = R^T R = L L^T, V = R L^{-T}
-                orthonormalize(R, V);
-                RPA_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * n_r, cudaMemcpyDeviceToHost, s));
-                RPA_CUDA(cudaMemcpyAsync(h_scal.data(), ecm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
-                RPA_CUDA(cudaEventRecord(b, s));
-                RPA_CUDA(cudaEventSynchronize(b));
-                c.stats.ms_subspace += ms_between(a, b);
-                cudaEventDestroy(a);
-                cudaEventDestroy(b);
-                ecm = h_scal[0];
-                ++it;
-                if (o.fixed_subspace_iters > 0) {
-                    if (it >= o.fixed_subspace_iters) break;
-                } else if (std::fabs(ecm - ecm_old) <= thr || it >= o.max_subspace_iters) {
-                    break;
-                }
-            }
-            c.stats.subspace_iterations[m] = it;
-            ecm_all[m] = ecm;
-            ec += ecm;
-            if (lambdas_host) std::memcpy(lambdas_host + (size_t)m * n_r, h_lam.data(), sizeof(double) * n_r);
-        }
-        RPA_CUDA(cudaEventRecord(t1, s));
-        RPA_CUDA(cudaEventSynchronize(t1));
-        c.stats.ms_total = ms_between(t0, t1);
-        cudaEventDestroy(t0);
-        cudaEventDestroy(t1);
-        if (ec_host) {
-            ec_host[0] = ec;
-            ec_host[1] = ec / o.n_atoms;
-        }
-        if (ec_per_omega_host) std::memcpy(ec_per_omega_host, ecm_all.data(), sizeof(double) * nw);
-        if (stats) *stats = c.stats;
+        c.opt.project_solution = saved;
     });
     if (st != RPA_OK) return st;
     if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";

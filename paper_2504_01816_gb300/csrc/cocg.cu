@@ -85,6 +85,11 @@ struct Params {
     int *count;        // slots busy + systems waiting (for the host)
     int *sys_iters, *sys_status, *sys_refines;
     unsigned long long *prof;   // grid points processed by k_cocg_p/_a/_b (nullptr = off)
+    // occupied-space projection of finished solutions (x <- x - sum_k (u_k . x) u_k)
+    int project, ns;
+    const double *psi;          // ns x nd orbitals
+    double *partP;              // [S][nblk][ns][2] partial u_k . x
+    double *Tp;                 // [S][ns][2]       u_k . x
 };
 
 __device__ __forceinline__ void prof_add(const Params &P, int which, int chunk) {
@@ -455,6 +460,7 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
             f1r = rs[col + (R + 1) * plane];
             f1p = po[col + (R + 1) * plane];
         }
+        T vnext = own ? vloc[col] : (T)0;  // potential of the next plane
         T acc0 = 0, acc1 = 0;              // per-thread sums in the working precision (FP64 is slow)
         // The z loop is unrolled by the window length: slot (u + m) % 13 of qv holds plane z-6+m,
         // so the window turns without moving registers.
@@ -487,11 +493,13 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
                     f2r = rs[col + (z + R + 2) * plane];
                     f2p = po[col + (z + R + 2) * plane];
                 }
+                const T vz = vnext;                          // potential of plane z (loaded one plane ago)
+                if (own && z + 1 < nz) vnext = vloc[col + (z + 1) * plane];
                 __syncthreads();
                 if (own) {
                     const int idx = col + z * plane;
                     const C c = qv[(u + R) % (2 * R + 1)];
-                    const T dre = (T)3 * cf.a[0] + vloc[idx] + sre;
+                    const T dre = (T)3 * cf.a[0] + vz + sre;
                     T re = dre * c.x - sim * c.y;
                     T im = dre * c.y + sim * c.x;
                     const C *cs = fb + (ly + R) * W + lx + R;
@@ -554,8 +562,10 @@ __global__ void __launch_bounds__(kThreads) k_refine_x(Params P, double2 *__rest
     }
 }
 
-// Mixed form: r64 = b - (H + sigma) x64 in FP64; the next inner solve starts from d = 0,
-// r32 = r64, p = 0.  Partials (into partB): r32^T r32 and ||r64||^2.
+// Mixed form: r64 = b - (H + sigma) x64 in FP64 (x64 has absorbed the FP32 correction d); the
+// next inner solve starts from d = 0, r32 = r64, p = 0.  Partials (into partB): r32^T r32 and
+// ||r64||^2.  (Continuing the FP32 recurrence with the replaced residual instead of restarting
+// was measured to lose convergence: the FP32 recursive residual can be far below the true one.)
 __global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double *__restrict__ b,
                                                          const double2 *__restrict__ x64, float2 *__restrict__ d,
                                                          float2 *__restrict__ r32, float2 *__restrict__ p32,
@@ -636,6 +646,90 @@ __global__ void k_state(Params P) {
     }
 }
 
+// Partial sums of u_k . x64 (complex) over each item of the finished slots, for k < ns.
+__global__ void __launch_bounds__(kThreads) k_proj_dots(Params P, const double2 *__restrict__ x64) {
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        if (P.slots[s].phase != kFinished) continue;
+        const long long off = (long long)s * P.g.nd;
+        for (int k = 0; k < P.ns; ++k) {
+            double v[2] = {0.0, 0.0};
+            for (int t = 0; t < kPPT; ++t) {
+                const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+                if (idx < P.g.nd) {
+                    const double u = P.psi[(long long)k * P.g.nd + idx];
+                    const double2 xv = x64[off + idx];
+                    v[0] += u * xv.x;
+                    v[1] += u * xv.y;
+                }
+            }
+            block_sum<2>(v);
+            if (threadIdx.x == 0) {
+                double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k) * 2;
+                o[0] = v[0];
+                o[1] = v[1];
+            }
+        }
+    }
+}
+
+// Tp[s][k] = sum over items of the partial dots (fixed order); one warp per finished slot.
+__global__ void k_proj_sum(Params P) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= P.S || P.slots[w].phase != kFinished) return;
+    for (int k = 0; k < P.ns; ++k) {
+        double v[2];
+        const double *base = P.partP + ((long long)w * P.nblk * P.ns + k) * 2;
+        v[0] = v[1] = 0.0;
+        for (int b = lane; b < P.nblk; b += 32) {
+            v[0] += base[(long long)b * P.ns * 2 + 0];
+            v[1] += base[(long long)b * P.ns * 2 + 1];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+            v[1] += __shfl_xor_sync(0xffffffffu, v[1], o);
+        }
+        if (lane == 0) {
+            P.Tp[((long long)w * P.ns + k) * 2 + 0] = v[0];
+            P.Tp[((long long)w * P.ns + k) * 2 + 1] = v[1];
+        }
+    }
+}
+
+// The finished solution of slot s at one point, with its occupied components removed when
+// P.project is set.
+__device__ __forceinline__ double2 solution_at(const Params &P, const double2 *__restrict__ x64, int s, long long idx) {
+    double2 x = x64[(long long)s * P.g.nd + idx];
+    if (P.project) {
+        const double *t = P.Tp + (long long)s * P.ns * 2;
+        for (int k = 0; k < P.ns; ++k) {
+            const double u = P.psi[(long long)k * P.g.nd + idx];
+            x.x -= t[2 * k] * u;
+            x.y -= t[2 * k + 1] * u;
+        }
+    }
+    return x;
+}
+
+// grad += scale * coef[j] * Re(x^2) for every finished slot, slots added in slot order.
+__global__ void k_retire_grad(Params P, const double2 *__restrict__ x64, const double *__restrict__ coef,
+                              double *__restrict__ grad, double scale) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P.g.nd;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int s = 0; s < P.S; ++s) {
+            const Slot &sl = P.slots[s];
+            if (sl.phase != kFinished) continue;
+            const double2 x = solution_at(P, x64, s, idx);
+            acc += coef[sl.j] * (x.x * x.x - x.y * x.y);
+        }
+        grad[idx] += scale * acc;
+    }
+}
+
 // drho_j += (4/h^3) u_n (.) Re x64 for every finished slot, slots added in slot order.
 __global__ void k_retire_drho(Params P, const double2 *__restrict__ x64, const double *__restrict__ psi,
                               double *__restrict__ drho, double scale) {
@@ -645,7 +739,7 @@ __global__ void k_retire_drho(Params P, const double2 *__restrict__ x64, const d
             const Slot &sl = P.slots[s];
             if (sl.phase != kFinished) continue;
             drho[(long long)sl.j * P.g.nd + idx] +=
-                scale * psi[(long long)sl.n * P.g.nd + idx] * x64[(long long)s * P.g.nd + idx].x;
+                scale * psi[(long long)sl.n * P.g.nd + idx] * solution_at(P, x64, s, idx).x;
         }
 }
 
@@ -658,7 +752,7 @@ __global__ void k_retire_copy(Params P, const double2 *__restrict__ x64, double2
         if (sl.phase != kFinished) continue;
         for (int t = 0; t < kPPT; ++t) {
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
-            if (idx < P.g.nd) xout[(long long)sl.sys * P.g.nd + idx] = x64[(long long)s * P.g.nd + idx];
+            if (idx < P.g.nd) xout[(long long)sl.sys * P.g.nd + idx] = solution_at(P, x64, s, idx);
         }
     }
 }
@@ -824,6 +918,8 @@ struct SolveSpec {
     const double *rhs = nullptr;    // solve mode: right-hand side per system; x copied out
     double2 *xout = nullptr;
     const double *Tc = nullptr;     // P_c coefficients per system (nullptr = no projection)
+    double *grad = nullptr;         // response-square mode: gradient accumulated with coef[j]
+    const double *coef = nullptr;   // device, one per column j
     double sign = 1.0;
     double omega = 0.0;
     std::vector<int> n, j;
@@ -932,6 +1028,14 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     P.sys_iters = sys_it;
     P.sys_status = sys_st;
     P.sys_refines = sys_rf;
+    P.project = c.opt.project_solution != 0 || sp.grad != nullptr;
+    P.ns = c.ns;
+    P.psi = c.psi64;
+    if (P.project) {
+        double *pp = (double *)c.proj_buf.ensure(sizeof(double) * 2 * (size_t)S * c.ns * (nblk + 1));
+        P.Tp = pp;
+        P.partP = pp + (size_t)S * c.ns * 2;
+    }
 
     int dev_sms = 0;
     RPA_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
@@ -996,7 +1100,13 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
                                                     cf64);   // p = direction buffer 0
             k_state<<<wgrid, kThreads, 0, ss>>>(P);
         }
-        if (sp.drho)
+        if (P.project) {
+            k_proj_dots<<<grid, kThreads, 0, ss>>>(P, x64);
+            k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P);
+        }
+        if (sp.grad)
+            k_retire_grad<<<std::min<unsigned>(cdiv(nd, 256), 2048u), 256, 0, ss>>>(P, x64, sp.coef, sp.grad, scale);
+        else if (sp.drho)
             k_retire_drho<<<std::min<unsigned>(cdiv(nd, 256), 2048u), 256, 0, ss>>>(P, x64, c.psi64, sp.drho, scale);
         else
             k_retire_copy<<<grid, kThreads, 0, ss>>>(P, x64, sp.xout);
@@ -1047,7 +1157,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         RPA_LAUNCH("cocg iterations");
         maintenance(ss);
     };
-    const int per_epoch = 4 * kEpoch + (mixed ? 7 : 4);
+    const int per_epoch = 4 * kEpoch + (mixed ? 7 : 4) + (P.project ? 2 : 0);
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     if (use_graph) {
@@ -1107,7 +1217,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     for (int g = 0; g < 2; ++g)
         if (gexec[g] && (g == 0 || gexec[1] != gexec[0])) cudaGraphExecDestroy(gexec[g]);
     for (auto &e : evs) cudaEventDestroy(e);
-    c.stats.launches += launches + 1;
+    count_launches(launches + 1);
     if (prof) {
         unsigned long long pts[3];
         RPA_CUDA(cudaMemcpy(pts, c.d_prof_points, sizeof pts, cudaMemcpyDeviceToHost));
@@ -1182,22 +1292,52 @@ int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, 
     return run_queue(c, sp, s, iters, status);
 }
 
-int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
-    RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
+// P_c coefficients of the pair right-hand sides u_n (.) dv_j for all (n, j), system n*ncols + j.
+static double *pair_coefficients(Ctx &c, const double *dv, int ncols, cudaStream_t s) {
     const int nsys = c.ns * ncols;
-    // P_c coefficients T[(n, j)][k] = u_k . (u_n (.) dv_j), one Gram per orbital n
     double *T = (double *)c.pc_coef.ensure(sizeof(double) * (size_t)nsys * c.ns);
     double *rows = (double *)c.rhs.ensure(sizeof(double) * (size_t)ncols * c.nd);
     for (int n = 0; n < c.ns; ++n) {
         k_pair_rows<<<dim3(std::min<unsigned>(cdiv(c.nd, 256), 1024u), ncols), 256, 0, s>>>(c.psi64, dv, n, c.nd,
                                                                                              rows);
         RPA_LAUNCH("pair rows");
+        count_launches(1);
         pc_coefficients(c, rows, ncols, T + (size_t)n * ncols * c.ns, s);
     }
+    return T;
+}
+
+int response_square(Ctx &c, double omega, const double *dv, const double *coef, double *grad, int ncols,
+                    cudaStream_t s) {
+    const int nsys = c.ns * ncols;
+    double *cd = (double *)c.coef_buf.ensure(sizeof(double) * (size_t)ncols);
+    RPA_CUDA(cudaMemcpyAsync(cd, coef, sizeof(double) * ncols, cudaMemcpyHostToDevice, s));
+    SolveSpec sp;
+    sp.vt = dv;
+    sp.grad = grad;
+    sp.coef = cd;
+    sp.Tc = pair_coefficients(c, dv, ncols, s);
+    sp.sign = -1.0;
+    sp.omega = omega;
+    sp.n.resize(nsys);
+    sp.j.resize(nsys);
+    for (int n = 0; n < c.ns; ++n)
+        for (int j = 0; j < ncols; ++j) {
+            sp.n[n * ncols + j] = n;
+            sp.j[n * ncols + j] = j;
+        }
+    const int w = run_queue(c, sp, s, nullptr, nullptr);
+    RPA_CUDA(cudaStreamSynchronize(s));   // coef (host) must outlive the copy
+    return w;
+}
+
+int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
+    const int nsys = c.ns * ncols;
     SolveSpec sp;
     sp.vt = dv;
     sp.drho = drho;
-    sp.Tc = T;
+    sp.Tc = pair_coefficients(c, dv, ncols, s);   // T[(n, j)][k] = u_k . (u_n (.) dv_j)
     sp.sign = -1.0;
     sp.omega = omega;
     sp.n.resize(nsys);

@@ -16,8 +16,6 @@
 
 namespace rpa {
 
-namespace {
-
 // Symmetric eigendecomposition A = Q diag(w) Q^T (row-major n x n, Q[i*n+a] = component i of
 // eigenvector a) by cyclic Jacobi rotations.
 void jacobi_eigh(std::vector<double> A, int n, std::vector<double> &w, std::vector<double> &Q) {
@@ -60,6 +58,8 @@ void jacobi_eigh(std::vector<double> A, int n, std::vector<double> &w, std::vect
     w.resize(n);
     for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
 }
+
+namespace {
 
 // out[o][a][i] = sum_b M[a][b] in[o][b][i]; M = Q^T (forward) or Q (back).  The data are viewed
 // as [outer][n][inner].  Each block takes one outer index and 32 consecutive inner indices
@@ -185,6 +185,7 @@ static void coulomb_passes(Ctx &c, double power, const double *in, double *out, 
                            double *sc, cudaStream_t s) {
     k_scale_grid<<<(unsigned)((c.nd + 255) / 256), 256, 0, s>>>(c.lam, sc, c.nd, power);
     RPA_LAUNCH("coulomb scale");
+    count_launches(7);   // scale + six axis passes
     axis_pass(c, 0, in, t1, ncols, 1, nullptr, s);
     axis_pass(c, 1, t1, t2, ncols, 1, nullptr, s);
     axis_pass(c, 2, t2, t1, ncols, 1, sc, s);

@@ -281,6 +281,7 @@ void gram(const double *A, int na, const double *B, int nb, long long len, doubl
     const long long n = (long long)na * nb;
     k_sum_splits<<<std::min<unsigned>(cdiv(n, 256), 4096u), 256, 0, s>>>(part, (int)splits, n, G);
     RPA_LAUNCH("gram");
+    count_launches(2);
 }
 
 void combine_rows(const double *S, int nc, int nk, const double *X, long long len, double *Y, cudaStream_t s) {
@@ -288,26 +289,31 @@ void combine_rows(const double *S, int nc, int nk, const double *X, long long le
     if (sh > 48 * 1024) RPA_CUDA(cudaFuncSetAttribute(k_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     k_combine<<<dim3(std::min<unsigned>(cdiv(len, 256), 2048u), cdiv(nc, 16)), 256, sh, s>>>(S, nc, nk, X, len, Y);
     RPA_LAUNCH("combine_rows");
+    count_launches(1);
 }
 
 void cholesky(double *M, int n, int *dev_info, cudaStream_t s) {
     k_cholesky<<<1, 1024, 0, s>>>(M, n, dev_info);
     RPA_LAUNCH("cholesky");
+    count_launches(1);
 }
 
 void tri_inverse(const double *L, int n, double *Linv, cudaStream_t s) {
     k_tri_inverse<<<cdiv(n, 64), 64, 0, s>>>(L, n, Linv);
     RPA_LAUNCH("tri_inverse");
+    count_launches(1);
 }
 
 void symmetrize(double *C, int n, cudaStream_t s) {
     k_symmetrize<<<cdiv((long long)n * n, 256), 256, 0, s>>>(C, n);
     RPA_LAUNCH("symmetrize");
+    count_launches(1);
 }
 
 void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out, cudaStream_t s) {
     k_sym_eigvals<<<1, 1024, 0, s>>>(C, n, lam, work, weight, e_out);
     RPA_LAUNCH("sym_eigvals");
+    count_launches(1);
 }
 
 }  // namespace rpa

@@ -25,6 +25,10 @@ struct Error {
 };
 
 [[noreturn]] void fail(rpa_status st, const char *fmt, ...);
+
+// Kernel launches issued by the library on this thread (reported in rpa_stats.launches).
+extern thread_local long long g_launches;
+inline void count_launches(long long n) { g_launches += n; }
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 #define RPA_CUDA(call) ::rpa::check_cuda((call), #call, __FILE__, __LINE__)
 #define RPA_LAUNCH(what) ::rpa::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
@@ -97,6 +101,9 @@ struct Ctx {
     DevBuf blockA, blockB, blockC, blockD;   // N_d x N_r blocks for rpa_ec / apply
     DevBuf small;                 // N_r x N_r matrices and scalars
     DevBuf slot_idx;              // (n, j) of the slots
+    DevBuf proj_buf;              // occupied-space projection of finished solutions
+    DevBuf coef_buf;              // per-column coefficients of the gradient pass
+    DevBuf blockE;                // subspace of the previous iteration (gradient)
     DevBuf dense_scratch;         // split-K partial sums
     SysState *h_state = nullptr;  // pinned host mirror of the slot states
     size_t h_state_cap = 0;
@@ -134,6 +141,15 @@ int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const doub
 // chi0 on ncols real columns: drho = (4/h^3) Re sum_n u_n x_n with the projected right-hand
 // sides -P_c(u_n dV_j).  Returns the worst status.
 int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s);
+
+// grad += sum_j coef[j] (4/h^3) Re sum_n (P_c x_{n,j})^2 for the projected Sternheimer solutions of
+// dV_j (ncols rows of dv); coef: ncols doubles on the host.  Returns the worst status.
+int response_square(Ctx &c, double omega, const double *dv, const double *coef, double *grad, int ncols,
+                    cudaStream_t s);
+
+// Host symmetric eigendecomposition (cyclic Jacobi): A = Q diag(w) Q^T, Q[i*n+a] = component i of
+// eigenvector a; w ascending is not guaranteed.
+void jacobi_eigh(std::vector<double> A, int n, std::vector<double> &w, std::vector<double> &Q);
 
 // Same as sternheimer_batch, with b replaced by P_c b first.
 int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

@@ -30,8 +30,8 @@ STATUS_NAMES = {0: "RPA_OK", 1: "RPA_ERR_INVALID", 2: "RPA_ERR_CUDA", 3: "RPA_ER
                 4: "RPA_ERR_NOT_CONVERGED", 5: "RPA_ERR_BREAKDOWN", 6: "RPA_ERR_NOT_SPD"}
 
 EXPORTED = ("rpa_default_options", "rpa_setup", "rpa_set_options", "rpa_coulomb_apply", "rpa_coulomb_apply_noalloc",
-            "rpa_sternheimer_solve", "rpa_apply_nuchi0", "rpa_ec", "rpa_destroy", "rpa_last_error",
-            "rpa_version")
+            "rpa_sternheimer_solve", "rpa_apply_nuchi0", "rpa_ec", "rpa_ec_gradient", "rpa_destroy",
+            "rpa_last_error", "rpa_version")
 
 
 class rpa_options(ctypes.Structure):
@@ -39,7 +39,8 @@ class rpa_options(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double), ("eps_c", ctypes.c_double),
                 ("n_omega", ctypes.c_int), ("omega0", ctypes.c_double), ("max_subspace_iters", ctypes.c_int),
                 ("fixed_subspace_iters", ctypes.c_int), ("n_atoms", ctypes.c_int),
-                ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int), ("project_solution", ctypes.c_int),
+                ("independent_frequencies", ctypes.c_int)]
 
 
 PROF_SLOTS = 8
@@ -93,6 +94,10 @@ def _load():
     lib.rpa_ec.argtypes = [vp, i, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(rpa_stats), vp]
     lib.rpa_ec.restype = i
+    lib.rpa_ec_gradient.argtypes = [vp, i, dp, dp, dp, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(rpa_stats), vp]
+    lib.rpa_ec_gradient.restype = i
     lib.rpa_destroy.argtypes = [vp]
     lib.rpa_destroy.restype = None
     lib.rpa_last_error.restype = ctypes.c_char_p
@@ -158,6 +163,8 @@ class Options:
     n_atoms: int = 1
     batch_systems: int = 0
     profile: int = 0
+    project_solution: int = 0
+    independent_frequencies: int = 0
 
     def to_c(self) -> rpa_options:
         o = rpa_options()
@@ -275,6 +282,26 @@ class Context:
         _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
         return EcResult(float(ec[0]), float(ec[1]), ecm, lam, st, stats_dict(stats, nw))
 
+    def ec_gradient(self, V0, want_subspace: bool = False, stream=None):
+        """E_c and dE_c/dV_loc (N_d, float64 CUDA tensor) at fixed orbitals (rpa_ec_gradient);
+        with want_subspace also the final subspace (n_r x N_d)."""
+        import torch
+        n_r = V0.shape[0]
+        _dev64(V0, (n_r, self.n_d))
+        nw = self.options.n_omega
+        lam = np.zeros((nw, n_r))
+        ec = np.zeros(2)
+        ecm = np.zeros(nw)
+        stats = rpa_stats()
+        grad = torch.empty(self.n_d, dtype=torch.float64, device=V0.device)
+        vout = torch.empty_like(V0) if want_subspace else None
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        st = _lib.rpa_ec_gradient(self._h, n_r, _ptr(V0), grad.data_ptr(), _ptr(vout), dptr(lam), dptr(ec),
+                                  dptr(ecm), ctypes.byref(stats), _stream(stream))
+        _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
+        res = EcResult(float(ec[0]), float(ec[1]), ecm, lam, st, stats_dict(stats, nw))
+        return (res, grad, vout) if want_subspace else (res, grad)
+
 
 # ----------------------------------------------------------------------------------------
 # The C entry points under their own names (raw marshalling, returning the status code).
@@ -316,6 +343,42 @@ def rpa_apply_nuchi0(ctx: Context, omega, V, symmetric=True, out=None, stream=No
 
 def rpa_ec(ctx: Context, V0, stream=None) -> EcResult:
     return ctx.ec(V0, stream)
+
+
+def rpa_ec_gradient(ctx: Context, V0, stream=None):
+    return ctx.ec_gradient(V0, stream=stream)
+
+
+def _autograd_function():
+    import torch
+
+    class EcFunction(torch.autograd.Function):
+        """E_c as a differentiable function of V_loc at fixed occupied orbitals and eigenvalues.
+
+        forward(vloc, psi, eps, V0, nx, ny, nz, h, options) -> E_c (Ha, 0-d tensor); backward gives
+        dE_c/dV_loc from rpa_ec_gradient (the hand-written adjoint; no graph is recorded through
+        the library)."""
+
+        @staticmethod
+        def forward(ctx, vloc, psi, eps, V0, nx, ny, nz, h, options):
+            with Context(nx, ny, nz, h, vloc.detach().contiguous(), psi.detach().contiguous(),
+                         np.asarray(eps, dtype=np.float64), options) as c:
+                res, grad = c.ec_gradient(V0.detach().contiguous())
+            ctx.save_for_backward(grad)
+            return torch.tensor(res.e_c, dtype=torch.float64, device=vloc.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad, None, None, None, None, None, None, None, None
+
+    return EcFunction
+
+
+def ec_autograd(vloc, psi, eps, V0, nx, ny, nz, h, options: Optional[Options] = None):
+    """Differentiable E_c(V_loc): torch.autograd sees dE_c/dV_loc from the library's adjoint."""
+    opts = options or default_options()
+    return _autograd_function().apply(vloc, psi, eps, V0, nx, ny, nz, h, opts)
 
 
 def rpa_destroy(ctx: Context):

@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(rpa, tmp_path):
 #include "rpa.h"
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
-         offsetof(rpa_options, profile), offsetof(rpa_stats, ms_coulomb),
+         offsetof(rpa_options, independent_frequencies), offsetof(rpa_stats, ms_coulomb),
          offsetof(rpa_stats, worst_status), offsetof(rpa_stats, prof_bytes), offsetof(rpa_stats, launches));
   return 0;
 }
@@ -60,7 +60,7 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     O, S = rpa.rpa.rpa_options, rpa.rpa.rpa_stats
-    assert got == [ctypes.sizeof(O), ctypes.sizeof(S), O.profile.offset, S.ms_coulomb.offset,
+    assert got == [ctypes.sizeof(O), ctypes.sizeof(S), O.independent_frequencies.offset, S.ms_coulomb.offset,
                    S.worst_status.offset, S.prof_bytes.offset, S.launches.offset]
 
 
