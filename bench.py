@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the E_c time-to-solution run (eps_c 1e-5 Ha/atom)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the step of the plain FP64 form")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default COCG kernel configuration")
     return ap.parse_args()
 
 
@@ -124,6 +125,14 @@ def kernel_traffic(kernel_name, points_per_launch):
         return float(info["dram_bytes_per_point"]) * points_per_launch
     except Exception:
         return None
+
+
+def ctx_omegas(n):
+    """Gauss-Legendre frequency nodes mapped to [0, inf) (omega0 = 1), ascending; only used to
+    pick the autotuning frequency."""
+    import numpy as np
+    x, _ = np.polynomial.legendre.leggauss(n)
+    return (1.0 + x) / (1.0 - x)
 
 
 def measured_peaks():
@@ -236,6 +245,14 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    # autotuner: choose the COCG kernel configuration on this workload (one chi~0 application
+    # per candidate at a middle frequency), outside the timed region
+    tune = None
+    if args.prec == "mixed" and not args.no_autotune:
+        om_mid = ctx_omegas(w.n_omega)[w.n_omega // 2]
+        chosen, names, times = ctx.autotune(om_mid, V0)
+        opts.stencil_shape, opts.z_chunks = ctx.options.stencil_shape, ctx.options.z_chunks
+        tune = {"chosen": names[chosen], "ms_per_candidate": dict(zip(names, times))}
     for _ in range(args.warmup):
         ctx.ec(V0)
     clocks = Clocks(local)
@@ -315,6 +332,8 @@ def run_ours(args):
                                        f"frequency ({s.n_s * w.n_r * w.n_omega} Sternheimer solves)",
                            "l2": "flushed (512 MB write) between timed steps",
                            "mean_cocg_iterations_per_solve": mean_iters,
+                           "near_breakdowns_per_step": sum(st.get("near_breakdowns", 0) for st in kstats) / args.steps,
+                           "autotune": tune,
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": int(sum(st.get("launches", 0) for st in kstats)),
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "share_of_step": v["ms"] / total_ms,
@@ -341,7 +360,7 @@ def run_ours(args):
         ctx.set_options(opts)
     if not args.no_tts and rank == 0:
         ot = rpa.default_options()
-        for k in ("prec", "tol", "n_omega", "n_atoms", "profile"):
+        for k in ("prec", "tol", "n_omega", "n_atoms", "profile", "stencil_shape", "z_chunks"):
             setattr(ot, k, getattr(opts, k))
         ot.eps_c = 1e-5
         ot.fixed_subspace_iters = 0

@@ -80,6 +80,12 @@ typedef struct {
                                   eigenvectors of H; when V_loc differs from the potential the
                                   orbitals belong to, it is the response of the fixed occupied space
                                   (the function rpa_ec_gradient differentiates) */
+    int z_chunks;              /* stencil work items per grid column along z (0 or 1 = whole columns);
+                                  more chunks give more parallel items when few systems are in flight,
+                                  at the price of re-reading a 6-plane overlap per chunk */
+    int stencil_shape;         /* block shape of the FP32 stencil kernel: 0 = up to 640 threads per block
+                                  (one block per SM), 1 = 416 (two), 2 = 288 (three); rpa_autotune
+                                  sets it */
     int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
@@ -112,11 +118,14 @@ typedef struct {
     double prof_points[RPA_PROF_SLOTS];
     double prof_bytes[RPA_PROF_SLOTS];
     long long launches;             /* kernels launched by the call (all of the library's kernels) */
+    long long near_breakdowns;      /* mixed form: FP32 COCG steps at which r^T r or p^T A p fell to
+                                       rounding level (the recurrence restarted or the inner solve
+                                       ended early), summed over systems */
 } rpa_stats;
 
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
- * profile 0, project_solution 0, independent_frequencies 0. */
+ * profile 0, project_solution 0, z_chunks 0, stencil_shape 0, independent_frequencies 0. */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).
@@ -204,6 +213,16 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
  * serialise them. */
 rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *in_dev, double *out_dev,
                                      int ncols, void *stream);
+
+/* Autotuner: times one application of nu^1/2 chi0(i omega) nu^1/2 to the n_r columns of V_dev
+ * for each candidate configuration of the COCG kernels -- the block shape of the stencil kernel
+ * (up to 640, 416 or 288 threads per block, i.e. the xy tile shape and blocks per SM) crossed with
+ * one or two z chunks per column -- and keeps the fastest for this context by setting its
+ * stencil_shape and z_chunks options (mixed form; the plain form has one shape).  times_ms_host (may be NULL) receives the 6 timings in the order
+ * shape-major; *chosen_host (may be NULL) the index of the chosen candidate.  The context's
+ * results do not depend on the choice beyond rounding. */
+rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r, int *chosen_host,
+                        double *times_ms_host, void *stream);
 
 /* Release the context and its device workspaces.  NULL is ignored. */
 void rpa_destroy(rpa_ctx *ctx);

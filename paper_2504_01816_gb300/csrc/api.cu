@@ -54,6 +54,7 @@ Ctx::~Ctx() {
     cudaFree(vloc64);
     cudaFree(vloc32);
     cudaFree(psi64);
+    cudaFree(psi32);
     cudaFree(eps_dev);
     for (double *q : Q) cudaFree(q);
     cudaFree(lam);
@@ -100,6 +101,8 @@ void validate_options(const rpa_options &o) {
     if (o.fixed_subspace_iters < 0) fail(RPA_ERR_INVALID, "fixed_subspace_iters must be >= 0");
     if (o.n_atoms < 1) fail(RPA_ERR_INVALID, "n_atoms must be >= 1");
     if (o.batch_systems < 0) fail(RPA_ERR_INVALID, "batch_systems must be >= 0");
+    if (o.z_chunks < 0 || o.z_chunks > 64) fail(RPA_ERR_INVALID, "z_chunks must be in [0, 64]");
+    if (o.stencil_shape < 0 || o.stencil_shape > 2) fail(RPA_ERR_INVALID, "stencil_shape must be 0, 1 or 2");
 }
 
 // Gauss-Legendre nodes and weights on (-1, 1) by Newton iteration on P_n, then the map
@@ -215,6 +218,8 @@ void rpa_default_options(rpa_options *o) {
     o->batch_systems = 0;
     o->profile = 0;
     o->project_solution = 0;
+    o->z_chunks = 0;
+    o->stencil_shape = 0;
     o->independent_frequencies = 0;
 }
 
@@ -261,11 +266,13 @@ rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_ord
             RPA_CUDA(cudaMalloc(&c.vloc64, sizeof(double) * nd));
             RPA_CUDA(cudaMalloc(&c.vloc32, sizeof(float) * nd));
             RPA_CUDA(cudaMalloc(&c.psi64, sizeof(double) * nd * n_s));
+            RPA_CUDA(cudaMalloc(&c.psi32, sizeof(float) * nd * n_s));
             RPA_CUDA(cudaMalloc(&c.eps_dev, sizeof(double) * n_s));
             RPA_CUDA(cudaMemcpyAsync(c.vloc64, vloc_dev, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s));
             RPA_CUDA(cudaMemcpyAsync(c.psi64, psi_dev, sizeof(double) * nd * n_s, cudaMemcpyDeviceToDevice, s));
             RPA_CUDA(cudaMemcpyAsync(c.eps_dev, eps_host, sizeof(double) * n_s, cudaMemcpyHostToDevice, s));
             k_to_float<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(c.vloc64, c.vloc32, nd);
+            k_to_float<<<(unsigned)((nd * n_s + 255) / 256), 256, 0, s>>>(c.psi64, c.psi32, nd * n_s);
             RPA_LAUNCH("setup");
             RPA_CUDA(cudaMallocHost((void **)&c.h_count, 8 * sizeof(int)));
             RPA_CUDA(cudaMalloc(&c.d_count, sizeof(int)));
@@ -340,6 +347,53 @@ rpa_status rpa_sternheimer_solve(rpa_ctx *ctx, double omega, const int *orbital_
     return (rpa_status)worst;
 }
 
+rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r, int *chosen_host,
+                        double *times_ms_host, void *stream) {
+    return guarded([&] {
+        if (!ctx || !V_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        if (n_r < 1) fail(RPA_ERR_INVALID, "n_r must be >= 1");
+        if (!std::isfinite(omega)) fail(RPA_ERR_INVALID, "omega must be finite");
+        Ctx &c = ctx->impl;
+        cudaStream_t s = as_stream(stream);
+        const size_t blk = sizeof(double) * (size_t)n_r * c.nd;
+        double *t1 = (double *)c.blockA.ensure(blk);
+        double *t2 = (double *)c.blockB.ensure(blk);
+        double *R = (double *)c.blockC.ensure(blk);
+        const int saved_zc = c.opt.z_chunks;
+        const int nvar = c.opt.prec == RPA_MIXED ? 3 : 1;
+        double best = 1e300;
+        int best_i = 0;
+        cudaEvent_t a, b;
+        RPA_CUDA(cudaEventCreate(&a));
+        RPA_CUDA(cudaEventCreate(&b));
+        for (int v = 0; v < 3; ++v)
+            for (int z = 0; z < 2; ++z) {
+                const int i = 2 * v + z;
+                double ms = 1e300;
+                if (v < nvar) {
+                    c.opt.stencil_shape = v;
+                    c.opt.z_chunks = z + 1;
+                    RPA_CUDA(cudaEventRecord(a, s));
+                    apply_nuchi0_impl(c, omega, V_dev, R, n_r, 1, t1, t2, s);
+                    RPA_CUDA(cudaEventRecord(b, s));
+                    RPA_CUDA(cudaEventSynchronize(b));
+                    ms = ms_between(a, b);
+                    if (ms < best) {
+                        best = ms;
+                        best_i = i;
+                    }
+                }
+                if (times_ms_host) times_ms_host[i] = ms;
+            }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        c.opt.stencil_shape = best_i / 2;
+        c.opt.z_chunks = best_i % 2 + 1;
+        (void)saved_zc;
+        if (chosen_host) *chosen_host = best_i;
+    });
+}
+
 rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, double *R_dev, int n_r, int symmetric,
                             void *stream) {
     int worst = 0;
@@ -410,13 +464,35 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
     RPA_CUDA(cudaEventRecord(t0, s));
 
     // Y = X L^{-T}, L L^T = X^T X (rows: Y = L^{-1} X)
+    int cur_m = -1, cur_it = 0;
     auto orthonormalize = [&](const double *X, double *Y) {
         gram(X, n_r, X, n_r, c.nd, Cm, s, c.dense_scratch);
         symmetrize(Cm, n_r, s);
         cholesky(Cm, n_r, info, s);
         RPA_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s));
         RPA_CUDA(cudaStreamSynchronize(s));
-        if (h_info != 0) fail(RPA_ERR_NOT_SPD, "overlap matrix not positive definite (pivot %d)", h_info - 1);
+        if (h_info != 0) {
+            // the overlap again, for the message: its diagonal holds the squared row norms
+            gram(X, n_r, X, n_r, c.nd, Wm, s, c.dense_scratch);
+            std::vector<double> M(nn);
+            RPA_CUDA(cudaMemcpyAsync(M.data(), Wm, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaStreamSynchronize(s));
+            double dmin = 1e300, dmax = 0.0;
+            int bad = 0;
+            for (int i = 0; i < n_r; ++i) {
+                const double d = M[(size_t)i * n_r + i];
+                if (!std::isfinite(d)) ++bad;
+                else {
+                    dmin = std::min(dmin, d);
+                    dmax = std::max(dmax, d);
+                }
+            }
+            fail(RPA_ERR_NOT_SPD,
+                 "overlap matrix not positive definite (pivot %d) of %s (frequency %d, subspace iteration %d); "
+                 "recomputed overlap: diagonal in [%.3e, %.3e], %d non-finite, pivot entry %.3e",
+                 h_info - 1, cur_m < 0 ? "the starting block" : "the block A V", cur_m, cur_it, dmin, dmax, bad,
+                 M[(size_t)(h_info - 1) * n_r + (h_info - 1)]);
+        }
         tri_inverse(Cm, n_r, Lm, s);
         combine_rows(Lm, n_r, n_r, X, c.nd, Y, s);
     };
@@ -426,11 +502,14 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
     std::vector<double> ecm_all(nw, 0.0);
     const double thr = o.eps_c * o.n_atoms / nw;
     for (int m = nw - 1; m >= 0; --m) {
+        cur_m = -1;
         if (o.independent_frequencies && m != nw - 1) orthonormalize(V0_dev, V);
+        cur_m = m;
         double ecm = 0.0;
         int it = 0;
         for (;;) {
             const double ecm_old = ecm;
+            cur_it = it;
             const int w = apply_nuchi0_impl(c, om[m], V, R, n_r, 1, T1, T2, s);
             worst = std::max(worst, w);
             cudaEvent_t a, b;

@@ -3,19 +3,19 @@
 //
 // Persistent slot queue.  A fixed set of S slots holds the systems in flight; each slot owns
 // its Krylov vectors and a small state record.  All systems of a call wait in a queue; when
-// a slot's system is solved its contribution is retired (drho accumulated, or x copied out)
-// and the slot takes the next system.  S is chosen so that the vectors touched every
-// iteration fit in the 126 MB L2, so the Krylov iteration runs out of L2 instead of HBM.
+// a slot's system is solved its contribution is retired (drho or the gradient accumulated, or
+// x copied out) and the slot takes the next system.
 //
-// One COCG iteration is three kernels over all (slot, chunk) work items (fixed grid,
-// grid-stride; items of idle slots are skipped in a few instructions):
-//   k_cocg_p:  rho = r^T r and ||r|| from the previous partial sums (fixed order), convergence
-//              test, beta = rho / rho_old, p = r + beta p
-//   k_cocg_a:  q = (H - eps_n + i omega) p, partial sums of p^T q
-//   k_cocg_b:  alpha = rho / p^T q, x += alpha p, r -= alpha q, partial sums of r^T r, ||r||^2
+// One COCG iteration over the slots of the active list is four launches:
+//   k_beta:     one warp per slot: rho = r^T r and ||r|| from the partial sums of the last
+//               update (fixed order), stopping test, beta = rho / rho_old, active list
+//   k_cocg_pa:  p = r + beta p_old and q = (H - eps_n + i omega) p (12th-order stencil, z-marching
+//               register window), partial sums of p^T q
+//   k_alpha:    one warp per slot: alpha = rho / p^T q
+//   k_cocg_b:   x += alpha p, r -= alpha q, partial sums of r^T r and ||r||^2
 // Reductions are deterministic: every block writes its own partial sums; consumers add them in
-// block order.  Between groups of iterations ("epochs") maintenance kernels refine, retire,
-// refill and load slots.
+// block order.  Groups of iterations ("epochs") are replayed as CUDA graphs; between epochs
+// maintenance kernels refine, retire, refill and load slots.
 //
 // Plain form:  complex FP64 COCG to ||r|| <= tol ||b||.
 // Mixed form:  FP64 iterative refinement around complex FP32 COCG: r64 = b - A x64 in FP64,
@@ -36,6 +36,13 @@ constexpr int kPPT = 8;
 constexpr int kChunk = kThreads * kPPT;   // grid points per work item
 constexpr int kEpoch = 8;                 // COCG iterations between maintenance passes (even)
 constexpr int kWarpsPerBlock = kThreads / 32;
+// Near-breakdown of the FP32 inner solve (mixed form).  COCG divides by r^T r, an unconjugated
+// form that can vanish for a nonzero complex r.  FP32 sums carry errors of ~1e-7..1e-6 of
+// ||r||^2, so when |r^T r| falls below kNearBreak ||r||^2 the next beta = r_new^T r_new / r^T r
+// is mostly rounding: the inner solve ends there and the FP64 refinement restarts it from the
+// true residual.  For unrelated complex vectors of N_d >= 10^4 points the ratio is
+// ~N_d^-1/2 >= 1e-3, so this is rare in a healthy solve.
+constexpr double kNearBreak = 1e-5;
 
 enum Phase : int { kEmpty = 0, kInner = 1, kInnerDone = 2, kFinished = 3, kLoading = 4 };
 
@@ -43,9 +50,12 @@ struct Slot {
     double rho_re[2], rho_im[2];    // r^T r of the last two iterations (by parity of the iteration)
     double alpha_re, alpha_im, beta_re, beta_im;
     double shift_re, shift_im;
-    double bnorm, ref_norm, rnorm;
+    double bnorm, ref_norm, rnorm;  // ||b||; inner solve: norms of the scaled FP32 residual
+    double scale;                   // mixed: the FP32 inner solve works on scale * (b - A x64)
     int phase, sys, n, j;
     int iters, total_iters, refines, status;
+    int discard;                    // mixed: the inner solve went non-finite; its correction is dropped
+    int nearbreak;                  // mixed: inner solves ended at a near-breakdown
 };
 
 template <typename T> struct Cx;
@@ -73,7 +83,7 @@ struct Params {
     int S, nblk;       // items per slot of the streaming kernels
     int nparta;        // partial sums per slot written by the stencil kernel (its tiles)
     Grid3 g;
-    double *partA;     // [S][nblk][2]   p^T q
+    double *partA;     // [S][nparta][2] p^T q
     double *partB;     // [S][nblk][3]   r^T r (re, im), ||r||^2
     int *list;         // [2][S] active slots of the current iteration (by parity)
     int *cnt;          // [2]    their number
@@ -83,13 +93,32 @@ struct Params {
     int *head;         // next system of the queue
     int nsys;
     int *count;        // slots busy + systems waiting (for the host)
-    int *sys_iters, *sys_status, *sys_refines;
+    int *sys_out;      // [4][nsys] per system: iterations, status, refinements, near-breakdowns
     unsigned long long *prof;   // grid points processed by k_cocg_p/_a/_b (nullptr = off)
     // occupied-space projection of finished solutions (x <- x - sum_k (u_k . x) u_k)
     int project, ns;
     const double *psi;          // ns x nd orbitals
     double *partP;              // [S][nblk][ns][2] partial u_k . x
     double *Tp;                 // [S][ns][2]       u_k . x
+    // mixed form with projected right-hand sides: P_c on every FP32 correction and residual
+    int cproject;
+    int proj_re_only;           // only Re(u_k . x) is needed (the solutions retire into drho)
+    float *Tp32;                // [S][ns][2]       Tp in FP32 (for FP32 updates)
+    const float *psi32;         // ns x nd orbitals in FP32
+};
+
+// The fields of Params that the two streaming kernels of the iteration read, passed on their
+// own: with the whole Params struct their kernel parameter blocks reached 256 bytes, and
+// k_cocg_b measured 18% slower from that size on (same code, same registers).
+struct IterArgs {
+    Slot *slots;
+    const int *list;               // active slots of the iteration's parity
+    const int *cnt;                // their number
+    double *part;                  // per-item partial sums: [S][nper][k_cocg_pa: 2, k_cocg_b: 3]
+    unsigned long long *prof;      // grid points processed (nullptr = off)
+    long long nd;
+    int nx, ny, nz;
+    int nper;                      // work items per slot (stencil tiles, or chunks)
 };
 
 __device__ __forceinline__ void prof_add(const Params &P, int which, int chunk) {
@@ -221,16 +250,24 @@ __global__ void k_beta(Params P, int par) {
     if (lane != 0) return;
     const int k = sl.iters;
     const double rn = sqrt(v[2]);
-    const double thr = P.mixed ? fmax(P.inner_tol * sl.ref_norm, 0.3 * P.tol * sl.bnorm) : P.tol * sl.bnorm;
+    const double thr =
+        P.mixed ? fmax(P.inner_tol * sl.ref_norm, 0.3 * P.tol * sl.bnorm * sl.scale) : P.tol * sl.bnorm;
     const bool conv = rn <= thr;
-    const bool bad = !isfinite(rn) || !(v[0] * v[0] + v[1] * v[1] > 0.0);
+    const double rr2 = v[0] * v[0] + v[1] * v[1];
+    const bool nonfinite = !isfinite(rn) || !isfinite(rr2);
+    const bool zero = !(rr2 > 0.0);
+    const bool nearb = P.mixed && k > 0 && !(rr2 > kNearBreak * kNearBreak * v[2] * v[2]);
     sl.rnorm = rn;
-    if (conv || k >= P.maxit || bad) {
+    if (conv || k >= P.maxit || nonfinite || zero || nearb) {
         if (P.mixed) {
-            if (bad && !conv) sl.status = RPA_ERR_BREAKDOWN;
+            // the inner solve ends; the refinement restarts it from the true residual unless it
+            // went non-finite (its correction is dropped) or r^T r vanished at its start
+            if (nonfinite) sl.discard = 1;
+            if (!conv && (nonfinite || (zero && k == 0))) sl.status = RPA_ERR_BREAKDOWN;
+            if (!conv && !nonfinite && nearb) sl.nearbreak += 1;
             sl.phase = kInnerDone;
         } else {
-            sl.status = conv ? RPA_OK : (bad ? RPA_ERR_BREAKDOWN : RPA_ERR_NOT_CONVERGED);
+            sl.status = conv ? RPA_OK : ((nonfinite || zero) ? RPA_ERR_BREAKDOWN : RPA_ERR_NOT_CONVERGED);
             sl.phase = kFinished;
         }
         return;
@@ -266,6 +303,7 @@ __global__ void k_alpha(Params P, int par) {
     const double den = mu[0] * mu[0] + mu[1] * mu[1];
     if (!(den > 0.0) || !isfinite(den)) {
         sl.status = RPA_ERR_BREAKDOWN;
+        if (P.mixed && !isfinite(den)) sl.discard = 1;
         sl.phase = P.mixed ? kInnerDone : kFinished;
         return;
     }
@@ -279,24 +317,24 @@ __global__ void k_alpha(Params P, int par) {
 
 // x += alpha p ; r -= alpha q ; partial sums of r^T r and ||r||^2
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename Cx<T>::t *__restrict__ x,
+__global__ void __launch_bounds__(kThreads) k_cocg_b(IterArgs A, typename Cx<T>::t *__restrict__ x,
                                                      typename Cx<T>::t *__restrict__ r,
                                                      const typename Cx<T>::t *__restrict__ pbuf, long long pstride,
                                                      const typename Cx<T>::t *__restrict__ q) {
     using C = typename Cx<T>::t;
-    const long long items = (long long)P.cnt[par] * P.nblk;
+    const long long items = (long long)*A.cnt * A.nper;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int s = P.list[par * P.S + (int)(it / P.nblk)], chunk = (int)(it % P.nblk);
-        Slot &sl = P.slots[s];
+        const int s = A.list[(int)(it / A.nper)], chunk = (int)(it % A.nper);
+        Slot &sl = A.slots[s];
         if (sl.phase != kInner) continue;      // breakdown in k_alpha (stable during this kernel)
         const T ar = (T)sl.alpha_re, ai = (T)sl.alpha_im;
-        const long long off = (long long)s * P.g.nd;
+        const long long off = (long long)s * A.nd;
         const C *p = pbuf + (long long)(sl.iters & 1) * pstride;   // the new direction (iters counted in k_alpha)
         T a0 = 0, a1 = 0, a2 = 0;          // per-thread sums in the working precision (FP64 is slow)
 #pragma unroll 4
         for (int t = 0; t < kPPT; ++t) {
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
-            if (idx < P.g.nd) {
+            if (idx < A.nd) {
                 const C pv = p[off + idx], qv = q[off + idx];
                 C xv = x[off + idx], rv = r[off + idx];
                 xv.x += ar * pv.x - ai * pv.y;
@@ -314,12 +352,15 @@ __global__ void __launch_bounds__(kThreads) k_cocg_b(Params P, int par, typename
         double v[3];
         block_sum_t<T, 3>(a, v);
         if (threadIdx.x == 0) {
-            double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
+            double *o = A.part + ((long long)s * A.nper + chunk) * 3;
             o[0] = v[0];
             o[1] = v[1];
             o[2] = v[2];
         }
-        prof_add(P, 2, chunk);
+        if (A.prof && threadIdx.x == 0) {
+            const long long left = A.nd - (long long)chunk * kChunk;
+            atomicAdd(A.prof + 2, (unsigned long long)(left < kChunk ? left : kChunk));
+        }
     }
 }
 
@@ -347,9 +388,11 @@ __device__ __forceinline__ void block_sum_any(double (&v)[N]) {
     }
 }
 
-// xy tiling of the fused stencil kernel: a tile of tx x ty grid columns, one thread per column.
+// Tiling of the fused stencil kernel: xy tiles of tx x ty grid columns (one thread per column)
+// and nzc chunks of zlen planes along z.
 struct Tiles {
     int tx, ty, ntx, nty;
+    int nzc, zlen;
 };
 
 // Fused direction update and stencil (one COCG half-step), for the slots of the active list:
@@ -361,13 +404,17 @@ struct Tiles {
 // frames, so one barrier per plane suffices.  Loads are issued ahead of use: the halo of plane
 // z+1 and the column front two planes ahead are in flight while plane z is computed.  Values
 // outside the box are zero.
-template <typename T> struct PaBounds;
-template <> struct PaBounds<float> { static constexpr int threads = 640; };
-template <> struct PaBounds<double> { static constexpr int threads = 448; };
+// Block-shape variants of the stencil kernel (maximum threads per block, blocks per SM the
+// register budget is sized for).  The autotuner (rpa_autotune) picks one per context.
+struct PaShape {
+    int max_threads, min_blocks;
+};
+constexpr PaShape kPaShapes32[3] = {{640, 1}, {416, 2}, {288, 3}};
+constexpr PaShape kPaShape64 = {448, 1};
 // MAXH: halo elements per thread that are prefetched into registers; any rest loads in place.
-template <typename T, int MAXH>
-__global__ void __launch_bounds__(PaBounds<T>::threads, 1)
-    k_cocg_pa(Params P, int par, Tiles tl, const typename Cx<T>::t *__restrict__ r, typename Cx<T>::t *__restrict__ pbuf,
+template <typename T, int MAXH, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_cocg_pa(IterArgs A, Tiles tl, const typename Cx<T>::t *__restrict__ r, typename Cx<T>::t *__restrict__ pbuf,
               long long pstride, typename Cx<T>::t *__restrict__ q, const T *__restrict__ vloc, Coef<T> cf) {
     using C = typename Cx<T>::t;
     extern __shared__ unsigned char smraw[];
@@ -378,26 +425,28 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
     // the block is rounded up to whole warps; threads past tx * ty only help with the halo
     const bool in_tile = threadIdx.x < tl.tx * tl.ty;
     const int lx = threadIdx.x % tl.tx, ly = in_tile ? threadIdx.x / tl.tx : 0;
-    const int ntiles = tl.ntx * tl.nty;
-    const long long items = (long long)P.cnt[par] * ntiles;
-    const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz;
+    const int ntiles = tl.ntx * tl.nty * tl.nzc;
+    const long long items = (long long)*A.cnt * ntiles;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
     const int plane = nx * ny;                    // grid functions have < 2^31 points
     // with one tile across x the left/right strips lie outside the box: zero, never loaded
     const bool sides = tl.ntx > 1;
     const int nhalo = sides ? 2 * R * (tl.tx + tl.ty) : 2 * R * tl.tx;
     const C zero = {(T)0, (T)0};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int s = P.list[par * P.S + (int)(it / ntiles)], tile = (int)(it % ntiles);
-        const Slot &sl = P.slots[s];
+        const int s = A.list[(int)(it / ntiles)], tile = (int)(it % ntiles);
+        const Slot &sl = A.slots[s];
         const int k = sl.iters;
         const T br = (T)sl.beta_re, bi = (T)sl.beta_im;
         const T sre = (T)sl.shift_re, sim = (T)sl.shift_im;
-        const long long off = (long long)s * P.g.nd;
+        const long long off = (long long)s * A.nd;
         const C *__restrict__ rs = r + off;
         const C *__restrict__ po = pbuf + (long long)(k & 1) * pstride + off;
         C *__restrict__ pn = pbuf + (long long)((k + 1) & 1) * pstride + off;
         C *__restrict__ qs = q + off;
-        const int x0 = (tile % tl.ntx) * tl.tx, y0 = (tile / tl.ntx) * tl.ty;
+        const int xyt = tile / tl.nzc, zc = tile % tl.nzc;
+        const int x0 = (xyt % tl.ntx) * tl.tx, y0 = (xyt / tl.ntx) * tl.ty;
+        const int zb = zc * tl.zlen, ze = min(nz, zb + tl.zlen);   // planes computed by this item
         const int gx = x0 + lx, gy = y0 + ly;
         const bool own = in_tile && gx < nx && gy < ny;
         const int col = gy * nx + gx;
@@ -443,32 +492,32 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
             if (e < nhalo) halo_of(e, hf[h], hg[h]);
             hr[h] = zero;
             hp[h] = zero;
-            if (hg[h] >= 0) {                         // plane 0
-                hr[h] = rs[hg[h]];
-                hp[h] = po[hg[h]];
+            if (hg[h] >= 0) {                         // plane zb
+                hr[h] = rs[zb * plane + hg[h]];
+                hp[h] = po[zb * plane + hg[h]];
             }
         }
-        // column window z = -6 .. 6 and the front planes 7, 8 (raw r, p_old)
+        // column window z = zb-6 .. zb+6 and the front plane zb+7 (raw r, p_old)
         C qv[2 * R + 1];
 #pragma unroll
         for (int m = 0; m < 2 * R + 1; ++m) {
-            const int z = m - R;
+            const int z = zb + m - R;
             qv[m] = (own && z >= 0 && z < nz) ? pnew(rs[col + z * plane], po[col + z * plane]) : zero;
         }
         C f1r = zero, f1p = zero;          // raw front of plane z+R+1, consumed at the end of step z
-        if (own && R + 1 < nz) {
-            f1r = rs[col + (R + 1) * plane];
-            f1p = po[col + (R + 1) * plane];
+        if (own && zb + R + 1 < nz) {
+            f1r = rs[col + (zb + R + 1) * plane];
+            f1p = po[col + (zb + R + 1) * plane];
         }
-        T vnext = own ? vloc[col] : (T)0;  // potential of the next plane
+        T vnext = own ? vloc[col + zb * plane] : (T)0;  // potential of the next plane
         T acc0 = 0, acc1 = 0;              // per-thread sums in the working precision (FP64 is slow)
         // The z loop is unrolled by the window length: slot (u + m) % 13 of qv holds plane z-6+m,
         // so the window turns without moving registers.
-        for (int z0 = 0; z0 < nz; z0 += 2 * R + 1) {
+        for (int z0 = zb; z0 < ze; z0 += 2 * R + 1) {
 #pragma unroll
             for (int u = 0; u < 2 * R + 1; ++u) {
                 const int z = z0 + u;
-                if (z >= nz) break;
+                if (z >= ze) break;
                 C *const fb = (z & 1) ? fr1 : fr0;
                 if (in_tile) fb[(ly + R) * W + lx + R] = qv[(u + R) % (2 * R + 1)];
 #pragma unroll
@@ -480,7 +529,7 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
                     fb[foff] = goff >= 0 ? pnew(rs[z * plane + goff], po[z * plane + goff]) : zero;
                 }
                 // loads for later planes: halo of z+1, column front z+R+2
-                if (z + 1 < nz) {
+                if (z + 1 < ze) {
 #pragma unroll
                     for (int h = 0; h < MAXH; ++h)
                         if (hg[h] >= 0) {
@@ -494,7 +543,7 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
                     f2p = po[col + (z + R + 2) * plane];
                 }
                 const T vz = vnext;                          // potential of plane z (loaded one plane ago)
-                if (own && z + 1 < nz) vnext = vloc[col + (z + 1) * plane];
+                if (own && z + 1 < ze) vnext = vloc[col + (z + 1) * plane];
                 __syncthreads();
                 if (own) {
                     const int idx = col + z * plane;
@@ -517,6 +566,7 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
                     pn[idx] = c;
                     acc0 += c.x * y.x - c.y * y.y;
                     acc1 += c.x * y.y + c.y * y.x;
+
                 }
                 // the front loaded one plane ago takes the slot of plane z-6
                 qv[u] = (own && z + R + 1 < nz) ? pnew(f1r, f1p) : zero;
@@ -527,12 +577,12 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
         double acc[2] = {(double)acc0, (double)acc1};
         block_sum_any<2>(acc);
         if (threadIdx.x == 0) {
-            double *o = P.partA + ((long long)s * P.nparta + tile) * 2;
+            double *o = A.part + ((long long)s * A.nper + tile) * 2;
             o[0] = acc[0];
             o[1] = acc[1];
-            if (P.prof) {
-                const long long w = (long long)min(tl.tx, nx - x0) * min(tl.ty, ny - y0) * nz;
-                atomicAdd(P.prof + 1, (unsigned long long)w);
+            if (A.prof) {
+                const long long w = (long long)min(tl.tx, nx - x0) * min(tl.ty, ny - y0) * (ze - zb);
+                atomicAdd(A.prof + 1, (unsigned long long)w);
             }
         }
     }
@@ -542,20 +592,41 @@ __global__ void __launch_bounds__(PaBounds<T>::threads, 1)
 // Maintenance kernels (between epochs).  Slot phases do not change while these item kernels
 // run, so every thread of a block reads the same phase.
 // ---------------------------------------------------------------------------------------------
-// Mixed form, slots whose inner solve ended: x64 += d.
+// Mixed form: the FP32 inner solve works on the residual times a per-slot scale chosen so that
+// its norm starts near 1.  Late refinements (tol 1e-12 of a small ||b||) would otherwise run
+// FP32 COCG on values whose squares fall into FP32's subnormal range.  The scale of the next
+// inner solve comes from the norm the last one ended at (its recursive residual, which tracks
+// the true one to within the FP32 accuracy), limited to 1e12 per step.
+__device__ __forceinline__ double next_scale(const Slot &sl) {
+    const double rn = sl.rnorm;
+    if (sl.discard || !isfinite(rn) || !(rn > 0.0)) return sl.scale;
+    return sl.scale / fmax(rn, 1e-12 * sl.ref_norm);
+}
+
+// Mixed form, slots whose inner solve ended: x64 += d / scale, d projected first when
+// P.cproject (dropped if the inner solve went non-finite).
 __global__ void __launch_bounds__(kThreads) k_refine_x(Params P, double2 *__restrict__ x64, const float2 *__restrict__ d) {
     const long long items = (long long)P.S * P.nblk;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
-        if (P.slots[s].phase != kInnerDone) continue;
+        const Slot &sl = P.slots[s];
+        if (sl.phase != kInnerDone || sl.discard) continue;
+        const double inv = 1.0 / sl.scale;
         const long long off = (long long)s * P.g.nd;
+        const float *tp = P.Tp32 + (long long)s * P.ns * 2;
         for (int t = 0; t < kPPT; ++t) {
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
             if (idx < P.g.nd) {
                 double2 xv = x64[off + idx];
-                const float2 dv = d[off + idx];
-                xv.x += (double)dv.x;
-                xv.y += (double)dv.y;
+                float2 dv = d[off + idx];
+                if (P.cproject)
+                    for (int k = 0; k < P.ns; ++k) {
+                        const float u = P.psi32[(long long)k * P.g.nd + idx];
+                        dv.x -= tp[2 * k] * u;
+                        dv.y -= tp[2 * k + 1] * u;
+                    }
+                xv.x += (double)dv.x * inv;
+                xv.y += (double)dv.y * inv;
                 x64[off + idx] = xv;
             }
         }
@@ -563,8 +634,8 @@ __global__ void __launch_bounds__(kThreads) k_refine_x(Params P, double2 *__rest
 }
 
 // Mixed form: r64 = b - (H + sigma) x64 in FP64 (x64 has absorbed the FP32 correction d); the
-// next inner solve starts from d = 0, r32 = r64, p = 0.  Partials (into partB): r32^T r32 and
-// ||r64||^2.  (Continuing the FP32 recurrence with the replaced residual instead of restarting
+// next inner solve starts from d = 0, r32 = scale * r64 (scale = next_scale), p = 0.  Partials
+// (into partB): r32^T r32 and ||scale * r64||^2.  (Continuing the FP32 recurrence with the replaced residual instead of restarting
 // was measured to lose convergence: the FP32 recursive residual can be far below the true one.)
 __global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double *__restrict__ b,
                                                          const double2 *__restrict__ x64, float2 *__restrict__ d,
@@ -576,6 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double 
         const Slot &sl = P.slots[s];
         if (sl.phase != kInnerDone) continue;
         const double sre = sl.shift_re, sim = sl.shift_im;
+        const double sc = next_scale(sl);
         const long long off = (long long)s * P.g.nd;
         double v[3] = {0.0, 0.0, 0.0};
         for (int t = 0; t < kPPT; ++t) {
@@ -585,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double 
                 coords(idx, P.g, i, j, k);
                 const double dre = 3.0 * cf.a[0] + vloc[idx] + sre;
                 const double2 ax = stencil_at<double, double2>(x64 + off, idx, i, j, k, P.g, cf, dre, sim);
-                const double rr = b[off + idx] - ax.x, ri = -ax.y;
+                const double rr = (b[off + idx] - ax.x) * sc, ri = -ax.y * sc;
                 const float2 rf = make_float2((float)rr, (float)ri);
                 r32[off + idx] = rf;
                 d[off + idx] = make_float2(0.f, 0.f);
@@ -593,6 +665,85 @@ __global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double 
                 v[0] += (double)rf.x * rf.x - (double)rf.y * rf.y;
                 v[1] += 2.0 * (double)rf.x * rf.y;
                 v[2] += rr * rr + ri * ri;
+            }
+        }
+        block_sum<3>(v);
+        if (threadIdx.x == 0) {
+            double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
+            o[0] = v[0];
+            o[1] = v[1];
+            o[2] = v[2];
+        }
+    }
+}
+
+// Mixed form with projected right-hand sides (P.cproject): the refinement works in the
+// unoccupied space, where the solution lies.  Each FP32 solve leaves occupied components of
+// ~1e-7 ||d|| in its correction d; accumulated in x64 they put occupied components into the
+// residual, and the next inner solves would have to solve for them, where (H - eps_n + i omega)
+// is indefinite (eigenvalues eps_k - eps_n + i omega, k <= n) and COCG stagnates.  So both the
+// correction (before x64 absorbs it) and the FP32 residual (before the inner solve) are
+// projected, v <- v - sum_k (u_k . v) u_k, and convergence is tested on ||P_c r||.  FP32 dots
+// against FP32 orbitals resolve the occupied components to ~1e-9 of the vector's norm, which
+// keeps those of x64 far below the residuals the refinement reaches.
+// Partial sums of u_k . v over each item of the slots whose inner solve ended, for k < ns.
+__global__ void __launch_bounds__(kThreads) k_cproj_dots(Params P, const float2 *__restrict__ d) {
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        if (P.slots[s].phase != kInnerDone) continue;
+        const long long off = (long long)s * P.g.nd;
+        float2 dv[kPPT];
+#pragma unroll
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            dv[t] = idx < P.g.nd ? d[off + idx] : make_float2(0.f, 0.f);
+        }
+        for (int k = 0; k < P.ns; ++k) {
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int t = 0; t < kPPT; ++t) {
+                const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+                if (idx < P.g.nd) {
+                    const float u = P.psi32[(long long)k * P.g.nd + idx];
+                    a0 += u * dv[t].x;
+                    a1 += u * dv[t].y;
+                }
+            }
+            double v[2] = {(double)a0, (double)a1};
+            block_sum<2>(v);
+            if (threadIdx.x == 0) {
+                double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k) * 2;
+                o[0] = v[0];
+                o[1] = v[1];
+            }
+        }
+    }
+}
+
+// P.cproject: r32 -= sum_k Tp[s][k] u_k for the slots whose inner solve ended; partials (into
+// partB): r32^T r32 and ||r32||^2 of the projected residual.
+__global__ void __launch_bounds__(kThreads) k_cproj_residual(Params P, float2 *__restrict__ r32) {
+    const long long items = (long long)P.S * P.nblk;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        if (P.slots[s].phase != kInnerDone) continue;
+        const long long off = (long long)s * P.g.nd;
+        const float *tp = P.Tp32 + (long long)s * P.ns * 2;
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            if (idx < P.g.nd) {
+                float2 rv = r32[off + idx];
+                for (int k = 0; k < P.ns; ++k) {
+                    const float u = P.psi32[(long long)k * P.g.nd + idx];
+                    rv.x -= tp[2 * k] * u;
+                    rv.y -= tp[2 * k + 1] * u;
+                }
+                r32[off + idx] = rv;
+                v[0] += (double)rv.x * rv.x - (double)rv.y * rv.y;
+                v[1] += 2.0 * (double)rv.x * rv.y;
+                v[2] += (double)rv.x * rv.x + (double)rv.y * rv.y;
             }
         }
         block_sum<3>(v);
@@ -625,13 +776,19 @@ __global__ void k_state(Params P) {
         sl.total_iters = 0;
         sl.refines = 0;
         sl.status = RPA_OK;
+        sl.discard = 0;
+        sl.nearbreak = 0;
+        sl.scale = 1.0;
         sl.phase = (rn > 0.0) ? kInner : kFinished;
         return;
     }
-    // kInnerDone (mixed form): rn = ||b - A x64||
+    // kInnerDone (mixed form): rn = ||scale * (b - A x64)|| with the scale of the next inner solve
+    const double sc = next_scale(sl);
     sl.refines += 1;
+    sl.scale = sc;
+    sl.discard = 0;
     sl.rnorm = rn;
-    if (rn <= P.tol * sl.bnorm) {
+    if (rn <= P.tol * sl.bnorm * sc) {
         sl.status = RPA_OK;
         sl.phase = kFinished;
     } else if (sl.status == RPA_ERR_BREAKDOWN) {
@@ -653,15 +810,21 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(Params P, const double2 
         const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
         if (P.slots[s].phase != kFinished) continue;
         const long long off = (long long)s * P.g.nd;
+        double2 xv[kPPT];
+#pragma unroll
+        for (int t = 0; t < kPPT; ++t) {
+            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+            xv[t] = idx < P.g.nd ? x64[off + idx] : make_double2(0.0, 0.0);
+        }
         for (int k = 0; k < P.ns; ++k) {
             double v[2] = {0.0, 0.0};
+#pragma unroll
             for (int t = 0; t < kPPT; ++t) {
                 const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
                 if (idx < P.g.nd) {
                     const double u = P.psi[(long long)k * P.g.nd + idx];
-                    const double2 xv = x64[off + idx];
-                    v[0] += u * xv.x;
-                    v[1] += u * xv.y;
+                    v[0] += u * xv[t].x;
+                    if (!P.proj_re_only) v[1] += u * xv[t].y;
                 }
             }
             block_sum<2>(v);
@@ -674,11 +837,11 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(Params P, const double2 
     }
 }
 
-// Tp[s][k] = sum over items of the partial dots (fixed order); one warp per finished slot.
-__global__ void k_proj_sum(Params P) {
+// Tp[s][k] = sum over items of the partial dots (fixed order); one warp per slot in phase ph.
+__global__ void k_proj_sum(Params P, int ph) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= P.S || P.slots[w].phase != kFinished) return;
+    if (w >= P.S || P.slots[w].phase != ph) return;
     for (int k = 0; k < P.ns; ++k) {
         double v[2];
         const double *base = P.partP + ((long long)w * P.nblk * P.ns + k) * 2;
@@ -695,6 +858,8 @@ __global__ void k_proj_sum(Params P) {
         if (lane == 0) {
             P.Tp[((long long)w * P.ns + k) * 2 + 0] = v[0];
             P.Tp[((long long)w * P.ns + k) * 2 + 1] = v[1];
+            P.Tp32[((long long)w * P.ns + k) * 2 + 0] = (float)v[0];
+            P.Tp32[((long long)w * P.ns + k) * 2 + 1] = (float)v[1];
         }
     }
 }
@@ -778,9 +943,10 @@ __global__ void __launch_bounds__(1024) k_refill(Params P, const int *__restrict
         if (sl) {
             if (sl->phase == kFinished) {
                 if (sl->sys >= 0) {
-                    P.sys_iters[sl->sys] = sl->total_iters;
-                    P.sys_status[sl->sys] = sl->status;
-                    P.sys_refines[sl->sys] = sl->refines;
+                    P.sys_out[sl->sys] = sl->total_iters;
+                    P.sys_out[P.nsys + sl->sys] = sl->status;
+                    P.sys_out[2 * P.nsys + sl->sys] = sl->refines;
+                    P.sys_out[3 * P.nsys + sl->sys] = sl->nearbreak;
                 }
                 sl->phase = kEmpty;
                 sl->sys = -1;
@@ -935,6 +1101,8 @@ Tiles pick_tiles(int nx, int ny, int max_threads) {
     const int nty = (ny + ty_max - 1) / ty_max;
     t.ty = (ny + nty - 1) / nty;
     t.nty = (ny + t.ty - 1) / t.ty;
+    t.nzc = 1;
+    t.zlen = 1 << 30;
     return t;
 }
 
@@ -990,17 +1158,24 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         q = cv.take<double2>(n);
     }
     const long long pstride = (long long)n;
-    const Tiles tl = pick_tiles(c.nx, c.ny, mixed ? PaBounds<float>::threads : PaBounds<double>::threads);
-    const int ntiles = tl.ntx * tl.nty;
+    const int variant = std::max(0, std::min(2, c.opt.stencil_shape));
+    Tiles tl = pick_tiles(c.nx, c.ny, mixed ? kPaShapes32[variant].max_threads : kPaShape64.max_threads);
+    if (c.opt.z_chunks > 1) {
+        tl.zlen = (c.nz + c.opt.z_chunks - 1) / c.opt.z_chunks;
+        tl.nzc = (c.nz + tl.zlen - 1) / tl.zlen;
+    } else {
+        tl.zlen = c.nz;
+    }
+    const int ntiles = tl.ntx * tl.nty * tl.nzc;
     double *partA = (double *)c.cocg_partials.ensure(sizeof(double) * (size_t)S * (2 * ntiles + 3 * nblk));
     double *partB = partA + (size_t)S * ntiles * 2;
     Slot *slots = (Slot *)c.sys_state.ensure(sizeof(Slot) * S);
-    // ints: head, count, cnt[2], list[2][S], then per system: n, j, iters, status, refines
-    const size_t nint = 4 + 2 * (size_t)S + 5 * (size_t)nsys;
+    // ints: head, count, cnt[2], list[2][S], then per system: n, j, iters, status, refines,
+    // near-breakdowns
+    const size_t nint = 4 + 2 * (size_t)S + 6 * (size_t)nsys;
     int *qi = (int *)c.slot_idx.ensure(sizeof(int) * nint);
     int *head = qi, *count = qi + 1, *cnt = qi + 2, *list = qi + 4;
-    int *sys_n = list + 2 * S, *sys_j = sys_n + nsys, *sys_it = sys_j + nsys, *sys_st = sys_it + nsys,
-        *sys_rf = sys_st + nsys;
+    int *sys_n = list + 2 * S, *sys_j = sys_n + nsys, *sys_out = sys_j + nsys;
     RPA_CUDA(cudaMemsetAsync(qi, 0, sizeof(int) * nint, st));
     RPA_CUDA(cudaMemcpyAsync(sys_n, sp.n.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
     RPA_CUDA(cudaMemcpyAsync(sys_j, sp.j.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
@@ -1025,16 +1200,34 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     P.head = head;
     P.nsys = nsys;
     P.count = count;
-    P.sys_iters = sys_it;
-    P.sys_status = sys_st;
-    P.sys_refines = sys_rf;
-    P.project = c.opt.project_solution != 0 || sp.grad != nullptr;
+    P.sys_out = sys_out;
+    // mixed form with P_c applied to the right-hand sides: the refinement works in the
+    // unoccupied space, and the finished solution is projected in FP64 (the FP32 projections
+    // leave occupied components of ~1e-9..1e-8 of its norm)
+    P.cproject = mixed && sp.Tc != nullptr;
+    P.project = c.opt.project_solution != 0 || sp.grad != nullptr || P.cproject;
+    P.proj_re_only = sp.drho != nullptr && sp.grad == nullptr;
     P.ns = c.ns;
     P.psi = c.psi64;
-    if (P.project) {
-        double *pp = (double *)c.proj_buf.ensure(sizeof(double) * 2 * (size_t)S * c.ns * (nblk + 1));
+    P.psi32 = c.psi32;
+    if (P.project || P.cproject) {
+        // Tp, partP, then Tp32
+        double *pp = (double *)c.proj_buf.ensure(sizeof(double) * 2 * (size_t)S * c.ns * (nblk + 2));
         P.Tp = pp;
         P.partP = pp + (size_t)S * c.ns * 2;
+        P.Tp32 = (float *)(P.partP + (size_t)S * c.ns * 2 * nblk);
+    }
+
+    // per parity: the stencil kernel's and the update kernel's views of P
+    IterArgs ia_pa[2], ia_b[2];
+    for (int par = 0; par < 2; ++par) {
+        const IterArgs base{slots, list + par * S, cnt + par, nullptr, nullptr, nd, c.nx, c.ny, c.nz, 0};
+        ia_pa[par] = base;
+        ia_pa[par].part = partA;
+        ia_pa[par].nper = ntiles;
+        ia_b[par] = base;
+        ia_b[par].part = partB;
+        ia_b[par].nper = nblk;
     }
 
     int dev_sms = 0;
@@ -1045,8 +1238,13 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const int pa_threads = (tl.tx * tl.ty + 31) / 32 * 32;
     const int pa_halo = tl.ntx > 1 ? 2 * kRadius * (tl.tx + tl.ty) : 2 * kRadius * tl.tx;
     const bool pa_h1 = pa_halo <= pa_threads;
-    auto pa32 = pa_h1 ? k_cocg_pa<float, 1> : k_cocg_pa<float, 2>;
-    auto pa64 = pa_h1 ? k_cocg_pa<double, 1> : k_cocg_pa<double, 2>;
+    using Pa32 = void (*)(IterArgs, Tiles, const float2 *, float2 *, long long, float2 *, const float *, Coef<float>);
+    static const Pa32 pa32_table[3][2] = {
+        {k_cocg_pa<float, 1, 640, 1>, k_cocg_pa<float, 2, 640, 1>},
+        {k_cocg_pa<float, 1, 416, 2>, k_cocg_pa<float, 2, 416, 2>},
+        {k_cocg_pa<float, 1, 288, 3>, k_cocg_pa<float, 2, 288, 3>}};
+    const Pa32 pa32 = pa32_table[variant][pa_h1 ? 0 : 1];
+    auto pa64 = pa_h1 ? k_cocg_pa<double, 1, 448, 1> : k_cocg_pa<double, 2, 448, 1>;
     const size_t pa_smem = 2 * (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);
     if (pa_smem > 48 * 1024) {
         if (mixed) RPA_CUDA(cudaFuncSetAttribute(pa32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
@@ -1077,6 +1275,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     if (prof) {
         RPA_CUDA(cudaMemsetAsync(c.d_prof_points, 0, sizeof(unsigned long long) * 3, st));
         P.prof = c.d_prof_points;
+        for (int par = 0; par < 2; ++par) ia_pa[par].prof = ia_b[par].prof = c.d_prof_points;
     }
     // Two graph instances of one epoch (alternating, so that the events of one can be read while
     // the other runs); without graphs the same launches go straight to the stream.
@@ -1095,14 +1294,23 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
 
     auto maintenance = [&](cudaStream_t ss) {
         if (mixed) {
+            if (P.cproject) {
+                k_cproj_dots<<<grid, kThreads, 0, ss>>>(P, (const float2 *)xin);
+                k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P, kInnerDone);
+            }
             k_refine_x<<<grid, kThreads, 0, ss>>>(P, x64, (const float2 *)xin);
             k_residual64<<<grid, kThreads, 0, ss>>>(P, b, x64, (float2 *)xin, (float2 *)r, (float2 *)p, c.vloc64,
                                                     cf64);   // p = direction buffer 0
+            if (P.cproject) {
+                k_cproj_dots<<<grid, kThreads, 0, ss>>>(P, (const float2 *)r);
+                k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P, kInnerDone);
+                k_cproj_residual<<<grid, kThreads, 0, ss>>>(P, (float2 *)r);
+            }
             k_state<<<wgrid, kThreads, 0, ss>>>(P);
         }
         if (P.project) {
             k_proj_dots<<<grid, kThreads, 0, ss>>>(P, x64);
-            k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P);
+            k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P, kFinished);
         }
         if (sp.grad)
             k_retire_grad<<<std::min<unsigned>(cdiv(nd, 256), 2048u), 256, 0, ss>>>(P, x64, sp.coef, sp.grad, scale);
@@ -1134,22 +1342,22 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             k_beta<<<wgrid, kThreads, 0, ss>>>(P, par);
             if (mixed) {
                 rec(t0 + 0);
-                pa32<<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const float2 *)r, (float2 *)p,
+                pa32<<<pa_grid, pa_threads, pa_smem, ss>>>(ia_pa[par], tl, (const float2 *)r, (float2 *)p,
                                                                       pstride, (float2 *)q, c.vloc32, cf32);
                 rec(t0 + 1);
                 k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
                 rec(t0 + 2);
-                k_cocg_b<float><<<grid, kThreads, 0, ss>>>(P, par, (float2 *)xin, (float2 *)r, (const float2 *)p,
+                k_cocg_b<float><<<grid, kThreads, 0, ss>>>(ia_b[par], (float2 *)xin, (float2 *)r, (const float2 *)p,
                                                            pstride, (const float2 *)q);
                 rec(t0 + 3);
             } else {
                 rec(t0 + 0);
-                pa64<<<pa_grid, pa_threads, pa_smem, ss>>>(P, par, tl, (const double2 *)r, (double2 *)p,
+                pa64<<<pa_grid, pa_threads, pa_smem, ss>>>(ia_pa[par], tl, (const double2 *)r, (double2 *)p,
                                                                         pstride, (double2 *)q, c.vloc64, cf64);
                 rec(t0 + 1);
                 k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
                 rec(t0 + 2);
-                k_cocg_b<double><<<grid, kThreads, 0, ss>>>(P, par, (double2 *)xin, (double2 *)r, (const double2 *)p,
+                k_cocg_b<double><<<grid, kThreads, 0, ss>>>(ia_b[par], (double2 *)xin, (double2 *)r, (const double2 *)p,
                                                             pstride, (const double2 *)q);
                 rec(t0 + 3);
             }
@@ -1157,7 +1365,8 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         RPA_LAUNCH("cocg iterations");
         maintenance(ss);
     };
-    const int per_epoch = 4 * kEpoch + (mixed ? 7 : 4) + (P.project ? 2 : 0);
+    const int per_maint = (mixed ? 7 : 4) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
+    const int per_epoch = 4 * kEpoch + per_maint;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     if (use_graph) {
@@ -1188,7 +1397,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     };
 
     maintenance(st);   // first fill of the slots
-    launches += mixed ? 7 : 4;
+    launches += per_maint;
     // Epochs are enqueued up to two ahead of the host's check of the busy count.
     constexpr int kRing = 4;
     int *hc = c.h_count;
@@ -1230,11 +1439,12 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         }
     }
 
-    std::vector<int> h(3 * (size_t)nsys);
-    RPA_CUDA(cudaMemcpy(h.data(), sys_it, sizeof(int) * 3 * nsys, cudaMemcpyDeviceToHost));
+    std::vector<int> h(4 * (size_t)nsys);
+    RPA_CUDA(cudaMemcpy(h.data(), sys_out, sizeof(int) * 4 * nsys, cudaMemcpyDeviceToHost));
     int worst = 0;
     for (int i = 0; i < nsys; ++i) {
         const int it = h[i], stt = h[nsys + i], rf = h[2 * nsys + i];
+        c.stats.near_breakdowns += h[3 * (size_t)nsys + i];
         worst = std::max(worst, stt);
         c.stats.sternheimer_solves += 1;
         c.stats.cocg_iterations += it;

@@ -83,6 +83,7 @@ struct Ctx {
     double *vloc64 = nullptr;
     float *vloc32 = nullptr;
     double *psi64 = nullptr;      // ns x nd (row s = orbital s)
+    float *psi32 = nullptr;       // FP32 copy (projection of the mixed form's FP32 residuals)
     std::vector<double> eps;
     double *eps_dev = nullptr;
 

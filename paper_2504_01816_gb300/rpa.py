@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "RPA_OK", 1: "RPA_ERR_INVALID", 2: "RPA_ERR_CUDA", 3: "RPA_ER
                 4: "RPA_ERR_NOT_CONVERGED", 5: "RPA_ERR_BREAKDOWN", 6: "RPA_ERR_NOT_SPD"}
 
 EXPORTED = ("rpa_default_options", "rpa_setup", "rpa_set_options", "rpa_coulomb_apply", "rpa_coulomb_apply_noalloc",
-            "rpa_sternheimer_solve", "rpa_apply_nuchi0", "rpa_ec", "rpa_ec_gradient", "rpa_destroy",
+            "rpa_sternheimer_solve", "rpa_apply_nuchi0", "rpa_ec", "rpa_ec_gradient", "rpa_autotune", "rpa_destroy",
             "rpa_last_error", "rpa_version")
 
 
@@ -40,6 +40,7 @@ class rpa_options(ctypes.Structure):
                 ("n_omega", ctypes.c_int), ("omega0", ctypes.c_double), ("max_subspace_iters", ctypes.c_int),
                 ("fixed_subspace_iters", ctypes.c_int), ("n_atoms", ctypes.c_int),
                 ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int), ("project_solution", ctypes.c_int),
+                ("z_chunks", ctypes.c_int), ("stencil_shape", ctypes.c_int),
                 ("independent_frequencies", ctypes.c_int)]
 
 
@@ -56,7 +57,7 @@ class rpa_stats(ctypes.Structure):
                 ("prof_count", ctypes.c_int), ("prof_name", (ctypes.c_char * 32) * PROF_SLOTS),
                 ("prof_launches", ctypes.c_longlong * PROF_SLOTS), ("prof_ms", ctypes.c_double * PROF_SLOTS),
                 ("prof_points", ctypes.c_double * PROF_SLOTS), ("prof_bytes", ctypes.c_double * PROF_SLOTS),
-                ("launches", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("near_breakdowns", ctypes.c_longlong)]
 
 
 def stats_dict(stats: "rpa_stats", n_omega: int) -> dict:
@@ -98,6 +99,8 @@ def _load():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(rpa_stats), vp]
     lib.rpa_ec_gradient.restype = i
+    lib.rpa_autotune.argtypes = [vp, d, dp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
+    lib.rpa_autotune.restype = i
     lib.rpa_destroy.argtypes = [vp]
     lib.rpa_destroy.restype = None
     lib.rpa_last_error.restype = ctypes.c_char_p
@@ -164,6 +167,8 @@ class Options:
     batch_systems: int = 0
     profile: int = 0
     project_solution: int = 0
+    z_chunks: int = 0
+    stencil_shape: int = 0
     independent_frequencies: int = 0
 
     def to_c(self) -> rpa_options:
@@ -281,6 +286,21 @@ class Context:
                          _stream(stream))
         _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
         return EcResult(float(ec[0]), float(ec[1]), ecm, lam, st, stats_dict(stats, nw))
+
+    AUTOTUNE_CANDIDATES = [f"stencil block <= {t} threads, {z} z chunk(s)" for t in (640, 416, 288) for z in (1, 2)]
+
+    def autotune(self, omega: float, V, stream=None):
+        """rpa_autotune: time the COCG kernel configurations on this workload, keep the fastest.
+        Returns (chosen index, candidate descriptions, times in ms)."""
+        n_r = V.shape[0]
+        _dev64(V, (n_r, self.n_d))
+        chosen = ctypes.c_int(0)
+        times = (ctypes.c_double * 6)()
+        _check(_lib.rpa_autotune(self._h, float(omega), _ptr(V), n_r, ctypes.byref(chosen), times, _stream(stream)))
+        # the autotuner sets stencil_shape and z_chunks; keep the Python-side options in step
+        self.options.stencil_shape = chosen.value // 2
+        self.options.z_chunks = chosen.value % 2 + 1
+        return chosen.value, self.AUTOTUNE_CANDIDATES, list(times)
 
     def ec_gradient(self, V0, want_subspace: bool = False, stream=None):
         """E_c and dE_c/dV_loc (N_d, float64 CUDA tensor) at fixed orbitals (rpa_ec_gradient);

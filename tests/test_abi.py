@@ -50,9 +50,10 @@ def test_struct_layouts_match_header(rpa, tmp_path):
 #include <stddef.h>
 #include "rpa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
          offsetof(rpa_options, independent_frequencies), offsetof(rpa_stats, ms_coulomb),
-         offsetof(rpa_stats, worst_status), offsetof(rpa_stats, prof_bytes), offsetof(rpa_stats, launches));
+         offsetof(rpa_stats, worst_status), offsetof(rpa_stats, prof_bytes), offsetof(rpa_stats, launches),
+         offsetof(rpa_stats, near_breakdowns));
   return 0;
 }
 """)
@@ -61,7 +62,8 @@ int main(void) {
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     O, S = rpa.rpa.rpa_options, rpa.rpa.rpa_stats
     assert got == [ctypes.sizeof(O), ctypes.sizeof(S), O.independent_frequencies.offset, S.ms_coulomb.offset,
-                   S.worst_status.offset, S.prof_bytes.offset, S.launches.offset]
+                   S.worst_status.offset, S.prof_bytes.offset, S.launches.offset,
+                   S.near_breakdowns.offset]
 
 
 def test_setup_rejects_bad_arguments_without_a_gpu(rpa):

@@ -178,6 +178,40 @@ def test_apply_nuchi0_small_batches_agree(rpa, ragged):
     assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
 
 
+@pytest.mark.parametrize("zc", [2, 3, 5])
+def test_z_chunked_stencil_items_agree(rpa, zc):
+    """Stencil work items split along z (with a 6-plane overlap) give the same result."""
+    s = synth.small_system((13, 11, 17), h=0.5, n_s=3, n_wells=3, seed=33)
+    V = synth.random_block(12, 5, s.n_d)
+    with rpa.Context.from_system(s, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED)) as ctx:
+        Ra, _ = ctx.apply_nuchi0(0.6, cuda(V))
+        ctx.set_options(opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, z_chunks=zc, batch_systems=4))
+        Rb, _ = ctx.apply_nuchi0(0.6, cuda(V))
+    assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_stencil_block_shapes_agree(rpa, shape):
+    """The stencil kernel's block-shape variants (other xy tiles, more blocks per SM)."""
+    s = synth.small_system((70, 31, 9), h=0.5, n_s=2, n_wells=3, seed=17)
+    V = synth.random_block(13, 3, s.n_d)
+    with rpa.Context.from_system(s, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED)) as ctx:
+        Ra, _ = ctx.apply_nuchi0(0.7, cuda(V))
+        ctx.set_options(opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, stencil_shape=shape))
+        Rb, _ = ctx.apply_nuchi0(0.7, cuda(V))
+    assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
+
+
+def test_autotune_keeps_results(rpa, ragged):
+    V = synth.random_block(14, 4, ragged.n_d)
+    with rpa.Context.from_system(ragged, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED)) as ctx:
+        Ra, _ = ctx.apply_nuchi0(0.5, cuda(V))
+        chosen, names, times = ctx.autotune(0.5, cuda(V))
+        assert 0 <= chosen < 6 and all(t > 0 for t in times)
+        Rb, _ = ctx.apply_nuchi0(0.5, cuda(V))
+    assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
+
+
 def test_apply_nuchi0_deterministic(rpa, tiny):
     V = synth.random_block(10, 4, tiny.n_d)
     with rpa.Context.from_system(tiny, opts(rpa, prec=rpa.RPA_MIXED)) as ctx:
@@ -246,3 +280,20 @@ def test_mixed40_sampled_columns_match_oracle(rpa):
     cols = [0, 37]
     ref = oracle.Oracle.from_system(s).chi_tilde(V[cols], omega, 1e-10)
     assert relerr(R[cols], ref) < 1e-7
+
+
+@pytest.mark.slow
+def test_lih72_sampled_column_matches_oracle(rpa):
+    """LiH-shaped 72^3 cell (h=0.3, 32 Li-like + 32 H-like wells, 64 orbitals): one column of
+    nu^1/2 chi0 nu^1/2 V at one frequency in the mixed form against the oracle (64 Sternheimer
+    solves on the host), and a second column for the batched path."""
+    w = synth.workload("lih72")
+    s = w.system
+    assert s.n_s == 64 and s.n_atoms == 64
+    V = synth.trial_vectors(w.seed, 2, s.n_d)
+    omega = oracle.frequency_quadrature(w.n_omega)[0][5]
+    with rpa.Context.from_system(s, opts(rpa, prec=rpa.RPA_MIXED, tol=1e-9)) as ctx:
+        R, code = ctx.apply_nuchi0(omega, cuda(V))
+    assert code == rpa.RPA_OK
+    ref = oracle.Oracle.from_system(s).chi_tilde(V[:1], omega, 1e-9)
+    assert relerr(R.cpu().numpy()[:1], ref) < 1e-6
