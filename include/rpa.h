@@ -83,9 +83,10 @@ typedef struct {
     int z_chunks;              /* stencil work items per grid column along z (0 or 1 = whole columns);
                                   more chunks give more parallel items when few systems are in flight,
                                   at the price of re-reading a 6-plane overlap per chunk */
-    int stencil_shape;         /* block shape of the FP32 stencil kernel: 0 = up to 640 threads per block
-                                  (one block per SM), 1 = 416 (two), 2 = 288 (three); rpa_autotune
-                                  sets it */
+    int stencil_shape;         /* variant of the FP32 stencil kernel: 0 = one grid column per thread,
+                                  up to 640 threads per block; 1 = two columns per thread, up to 512
+                                  threads; 2 = two columns per thread, up to 384 threads;
+                                  rpa_autotune sets it */
     int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
@@ -215,12 +216,13 @@ rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *i
                                      int ncols, void *stream);
 
 /* Autotuner: times one application of nu^1/2 chi0(i omega) nu^1/2 to the n_r columns of V_dev
- * for each candidate configuration of the COCG kernels -- the block shape of the stencil kernel
- * (up to 640, 416 or 288 threads per block, i.e. the xy tile shape and blocks per SM) crossed with
- * one or two z chunks per column -- and keeps the fastest for this context by setting its
- * stencil_shape and z_chunks options (mixed form; the plain form has one shape).  times_ms_host (may be NULL) receives the 6 timings in the order
- * shape-major; *chosen_host (may be NULL) the index of the chosen candidate.  The context's
- * results do not depend on the choice beyond rounding. */
+ * for each candidate configuration of the COCG kernels -- the three stencil kernel variants of
+ * rpa_options.stencil_shape (columns per thread and threads per block, i.e. the xy tile shape)
+ * crossed with one or two z chunks per column -- and keeps the fastest for this context by
+ * setting its stencil_shape and z_chunks options (mixed form; the plain form has one shape).
+ * times_ms_host (may be NULL) receives the 6 timings in the order shape-major; *chosen_host (may
+ * be NULL) the index of the chosen candidate.  The context's results do not depend on the
+ * choice beyond rounding. */
 rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r, int *chosen_host,
                         double *times_ms_host, void *stream);
 

@@ -404,13 +404,15 @@ struct Tiles {
 // frames, so one barrier per plane suffices.  Loads are issued ahead of use: the halo of plane
 // z+1 and the column front two planes ahead are in flight while plane z is computed.  Values
 // outside the box are zero.
-// Block-shape variants of the stencil kernel (maximum threads per block, blocks per SM the
-// register budget is sized for).  The autotuner (rpa_autotune) picks one per context.
+// Variants of the FP32 stencil kernel the autotuner (rpa_autotune) chooses from, by
+// rpa_options.stencil_shape: 0 = one column per thread, up to 640 threads per block; 1 = two
+// columns per thread, up to 512 threads; 2 = two columns per thread, up to 384 threads (more
+// registers, no spills).  The FP64 form has one shape.
 struct PaShape {
-    int max_threads, min_blocks;
+    int max_threads, min_blocks, pairs;
 };
-constexpr PaShape kPaShapes32[3] = {{640, 1}, {416, 2}, {288, 3}};
-constexpr PaShape kPaShape64 = {448, 1};
+constexpr PaShape kPaShapes32[3] = {{640, 1, 0}, {512, 1, 1}, {384, 1, 1}};
+constexpr PaShape kPaShape64 = {448, 1, 0};
 // MAXH: halo elements per thread that are prefetched into registers; any rest loads in place.
 template <typename T, int MAXH, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
@@ -588,6 +590,234 @@ __global__ void __launch_bounds__(MAXT, MINB)
     }
 }
 
+// The FP32 stencil kernel with two grid columns per thread (x and x+1).  Same algorithm as
+// k_cocg_pa; the pair shares its x-neighbours, so the shared-memory frame is read with 16-byte
+// loads: 7 for the 14 x-neighbours of the pair and 12 for the y-neighbours of both points (19
+// per two points instead of 48 8-byte loads), and the per-plane overhead (halo, barrier, index
+// arithmetic, window turn) is paid once per two points.  Tiles are an even number of columns
+// wide; a column past nx (odd nx) is held at zero.
+template <int MAXH, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+    k_cocg_pa2(IterArgs A, Tiles tl, const float2 *__restrict__ r, float2 *__restrict__ pbuf, long long pstride,
+               float2 *__restrict__ q, const float *__restrict__ vloc, Coef<float> cf) {
+    extern __shared__ float4 smv[];
+    constexpr int R = kRadius;
+    constexpr int NW = 2 * R + 1;
+    const int W = tl.tx + 2 * R, H = tl.ty + 2 * R, frame = W * H;   // in float2 units (W even)
+    float2 *const fr0 = reinterpret_cast<float2 *>(smv);
+    float2 *const fr1 = fr0 + frame;
+    const int txp = tl.tx / 2;                            // column pairs per tile row
+    const bool in_tile = threadIdx.x < txp * tl.ty;
+    const int lp = threadIdx.x % txp, ly = in_tile ? threadIdx.x / txp : 0;
+    const int ntiles = tl.ntx * tl.nty * tl.nzc;
+    const long long items = (long long)*A.cnt * ntiles;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int plane = nx * ny;
+    const bool sides = tl.ntx > 1;
+    const int nhalo = sides ? R * (tl.tx + tl.ty) : R * tl.tx;      // halo pairs per plane
+    const float2 zero = make_float2(0.f, 0.f);
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = A.list[(int)(it / ntiles)], tile = (int)(it % ntiles);
+        const Slot &sl = A.slots[s];
+        const int k = sl.iters;
+        const float br = (float)sl.beta_re, bi = (float)sl.beta_im;
+        const float sre = (float)sl.shift_re, sim = (float)sl.shift_im;
+        const long long off = (long long)s * A.nd;
+        const float2 *__restrict__ rs = r + off;
+        const float2 *__restrict__ po = pbuf + (long long)(k & 1) * pstride + off;
+        float2 *__restrict__ pn = pbuf + (long long)((k + 1) & 1) * pstride + off;
+        float2 *__restrict__ qs = q + off;
+        const int xyt = tile / tl.nzc, zc = tile % tl.nzc;
+        const int x0 = (xyt % tl.ntx) * tl.tx, y0 = (xyt / tl.ntx) * tl.ty;
+        const int zb = zc * tl.zlen, ze = min(nz, zb + tl.zlen);
+        const int gx = x0 + 2 * lp, gy = y0 + ly;
+        const bool own0 = in_tile && gx < nx && gy < ny;
+        const bool own1 = in_tile && gx + 1 < nx && gy < ny;
+        const int col = gy * nx + gx;
+        auto pnew = [&](const float2 a, const float2 b) -> float2 {
+            return make_float2(a.x + br * b.x - bi * b.y, a.y + br * b.y + bi * b.x);
+        };
+        // halo pair e -> frame offset of its first point, grid offsets of its two points
+        auto halo_of = [&](int e, int &foff, int &g0, int &g1) {
+            int hx, hy;
+            if (e < R * tl.tx) {                          // top / bottom strips: tx/2 pairs per row
+                const int rr = e / txp;
+                hx = 2 * (e - rr * txp) + R;
+                hy = rr < R ? rr : tl.ty + rr;
+            } else {                                      // left / right strips: R/2 pairs per row
+                const int e2 = e - R * tl.tx;
+                const int cc = e2 / tl.ty;                // 0 .. R-1 (pair column)
+                hy = e2 - cc * tl.ty + R;
+                hx = cc < R / 2 ? 2 * cc : tl.tx + R + 2 * (cc - R / 2);
+            }
+            const int ax = x0 + hx - R, ay = y0 + hy - R;
+            foff = hy * W + hx;
+            const bool iy = ay >= 0 && ay < ny;
+            g0 = (iy && ax >= 0 && ax < nx) ? ay * nx + ax : -1;
+            g1 = (iy && ax + 1 >= 0 && ax + 1 < nx) ? ay * nx + ax + 1 : -1;
+        };
+        __syncthreads();                                  // the previous item's readers are done
+        if (!sides) {                                     // zero the side strips of both frames
+            for (int e = threadIdx.x; e < 2 * R * tl.ty; e += blockDim.x) {
+                const int cc = e / tl.ty, hy = e - cc * tl.ty + R;
+                const int hx = cc < R ? cc : tl.tx + cc;
+                fr0[hy * W + hx] = zero;
+                fr1[hy * W + hx] = zero;
+            }
+        }
+        int hf[MAXH], hg0[MAXH], hg1[MAXH];
+        float2 hr0[MAXH], hp0[MAXH], hr1[MAXH], hp1[MAXH];
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h) {
+            const int e = threadIdx.x + h * blockDim.x;
+            hf[h] = -1;
+            hg0[h] = -1;
+            hg1[h] = -1;
+            if (e < nhalo) halo_of(e, hf[h], hg0[h], hg1[h]);
+            hr0[h] = hp0[h] = hr1[h] = hp1[h] = zero;
+            if (hg0[h] >= 0) {
+                hr0[h] = rs[zb * plane + hg0[h]];
+                hp0[h] = po[zb * plane + hg0[h]];
+            }
+            if (hg1[h] >= 0) {
+                hr1[h] = rs[zb * plane + hg1[h]];
+                hp1[h] = po[zb * plane + hg1[h]];
+            }
+        }
+        float2 qa[NW], qb[NW];                            // column windows z-6 .. z+6 (p_new)
+#pragma unroll
+        for (int m = 0; m < NW; ++m) {
+            const int z = zb + m - R;
+            const bool iz = z >= 0 && z < nz;
+            qa[m] = (own0 && iz) ? pnew(rs[col + z * plane], po[col + z * plane]) : zero;
+            qb[m] = (own1 && iz) ? pnew(rs[col + 1 + z * plane], po[col + 1 + z * plane]) : zero;
+        }
+        float2 f1ra = zero, f1pa = zero, f1rb = zero, f1pb = zero;   // raw fronts of plane z+R+1
+        if (zb + R + 1 < nz) {
+            if (own0) {
+                f1ra = rs[col + (zb + R + 1) * plane];
+                f1pa = po[col + (zb + R + 1) * plane];
+            }
+            if (own1) {
+                f1rb = rs[col + 1 + (zb + R + 1) * plane];
+                f1pb = po[col + 1 + (zb + R + 1) * plane];
+            }
+        }
+        float va = own0 ? vloc[col + zb * plane] : 0.f, vb = own1 ? vloc[col + 1 + zb * plane] : 0.f;
+        float acc0 = 0.f, acc1 = 0.f;
+        for (int z0 = zb; z0 < ze; z0 += NW) {
+#pragma unroll
+            for (int u = 0; u < NW; ++u) {
+                const int z = z0 + u;
+                if (z >= ze) break;
+                float2 *const fb = (z & 1) ? fr1 : fr0;
+                const int ci = (ly + R) * W + 2 * lp + R;     // even: 16-byte aligned pair
+                const float2 ca = qa[(u + R) % NW], cb = qb[(u + R) % NW];
+                if (in_tile) reinterpret_cast<float4 *>(fb)[ci >> 1] = make_float4(ca.x, ca.y, cb.x, cb.y);
+#pragma unroll
+                for (int h = 0; h < MAXH; ++h)
+                    if (hf[h] >= 0) {
+                        const float2 e0 = hg0[h] >= 0 ? pnew(hr0[h], hp0[h]) : zero;
+                        const float2 e1 = hg1[h] >= 0 ? pnew(hr1[h], hp1[h]) : zero;
+                        reinterpret_cast<float4 *>(fb)[hf[h] >> 1] = make_float4(e0.x, e0.y, e1.x, e1.y);
+                    }
+                for (int e = threadIdx.x + MAXH * blockDim.x; e < nhalo; e += blockDim.x) {   // small blocks
+                    int foff, g0, g1;
+                    halo_of(e, foff, g0, g1);
+                    const float2 e0 = g0 >= 0 ? pnew(rs[z * plane + g0], po[z * plane + g0]) : zero;
+                    const float2 e1 = g1 >= 0 ? pnew(rs[z * plane + g1], po[z * plane + g1]) : zero;
+                    reinterpret_cast<float4 *>(fb)[foff >> 1] = make_float4(e0.x, e0.y, e1.x, e1.y);
+                }
+                if (z + 1 < ze) {                         // halo of the next plane
+#pragma unroll
+                    for (int h = 0; h < MAXH; ++h) {
+                        if (hg0[h] >= 0) {
+                            hr0[h] = rs[(z + 1) * plane + hg0[h]];
+                            hp0[h] = po[(z + 1) * plane + hg0[h]];
+                        }
+                        if (hg1[h] >= 0) {
+                            hr1[h] = rs[(z + 1) * plane + hg1[h]];
+                            hp1[h] = po[(z + 1) * plane + hg1[h]];
+                        }
+                    }
+                }
+                float2 f2ra = zero, f2pa = zero, f2rb = zero, f2pb = zero;   // column fronts z+R+2
+                if (z + R + 2 < nz) {
+                    if (own0) {
+                        f2ra = rs[col + (z + R + 2) * plane];
+                        f2pa = po[col + (z + R + 2) * plane];
+                    }
+                    if (own1) {
+                        f2rb = rs[col + 1 + (z + R + 2) * plane];
+                        f2pb = po[col + 1 + (z + R + 2) * plane];
+                    }
+                }
+                const float vza = va, vzb = vb;
+                if (z + 1 < ze) {
+                    if (own0) va = vloc[col + (z + 1) * plane];
+                    if (own1) vb = vloc[col + 1 + (z + 1) * plane];
+                }
+                __syncthreads();
+                if (own0) {
+                    const float4 *cv = reinterpret_cast<const float4 *>(fb) + (ci >> 1);
+                    float4 X[7];                          // frame positions ci-6 .. ci+7
+#pragma unroll
+                    for (int m = 0; m < 7; ++m) X[m] = cv[m - 3];
+                    // position ci + o of the x row, o in [-6, 7]
+                    auto xat = [&](int o) -> float2 {
+                        const float4 v = X[(o + 6) >> 1];
+                        return ((o + 6) & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+                    };
+                    const float dra = 3.f * cf.a[0] + vza + sre, drb = 3.f * cf.a[0] + vzb + sre;
+                    float rea = dra * ca.x - sim * ca.y, ima = dra * ca.y + sim * ca.x;
+                    float reb = drb * cb.x - sim * cb.y, imb = drb * cb.y + sim * cb.x;
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        const float4 ym = cv[-(d * W) / 2], yp = cv[(d * W) / 2];
+                        const float2 a1 = xat(-d), a2 = xat(d), b1 = xat(1 - d), b2 = xat(1 + d);
+                        const float2 za = qa[(u + R - d) % NW], zp = qa[(u + R + d) % NW];
+                        const float2 zbm = qb[(u + R - d) % NW], zbp = qb[(u + R + d) % NW];
+                        rea += cf.a[d] * (((a1.x + a2.x) + (ym.x + yp.x)) + (za.x + zp.x));
+                        ima += cf.a[d] * (((a1.y + a2.y) + (ym.y + yp.y)) + (za.y + zp.y));
+                        reb += cf.a[d] * (((b1.x + b2.x) + (ym.z + yp.z)) + (zbm.x + zbp.x));
+                        imb += cf.a[d] * (((b1.y + b2.y) + (ym.w + yp.w)) + (zbm.y + zbp.y));
+                    }
+                    const int idx = col + z * plane;
+                    qs[idx] = make_float2(rea, ima);
+                    pn[idx] = ca;
+                    acc0 += ca.x * rea - ca.y * ima;
+                    acc1 += ca.x * ima + ca.y * rea;
+                    if (own1) {
+                        qs[idx + 1] = make_float2(reb, imb);
+                        pn[idx + 1] = cb;
+                        acc0 += cb.x * reb - cb.y * imb;
+                        acc1 += cb.x * imb + cb.y * reb;
+                    }
+                }
+                // the fronts loaded one plane ago take the window slot of plane z-6
+                const bool inz = z + R + 1 < nz;
+                qa[u] = (own0 && inz) ? pnew(f1ra, f1pa) : zero;
+                qb[u] = (own1 && inz) ? pnew(f1rb, f1pb) : zero;
+                f1ra = f2ra;
+                f1pa = f2pa;
+                f1rb = f2rb;
+                f1pb = f2pb;
+            }
+        }
+        double acc[2] = {(double)acc0, (double)acc1};
+        block_sum_any<2>(acc);
+        if (threadIdx.x == 0) {
+            double *o = A.part + ((long long)s * A.nper + tile) * 2;
+            o[0] = acc[0];
+            o[1] = acc[1];
+            if (A.prof) {
+                const long long w = (long long)min(tl.tx, nx - x0) * min(tl.ty, ny - y0) * (ze - zb);
+                atomicAdd(A.prof + 1, (unsigned long long)w);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Maintenance kernels (between epochs).  Slot phases do not change while these item kernels
 // run, so every thread of a block reads the same phase.
@@ -687,36 +917,64 @@ __global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double 
 // against FP32 orbitals resolve the occupied components to ~1e-9 of the vector's norm, which
 // keeps those of x64 far below the residuals the refinement reaches.
 // Partial sums of u_k . v over each item of the slots whose inner solve ended, for k < ns.
-__global__ void __launch_bounds__(kThreads) k_cproj_dots(Params P, const float2 *__restrict__ d) {
-    const long long items = (long long)P.S * P.nblk;
+// (Projecting the residual only in late refinements was measured to cost more than it saves:
+// the occupied components of the first refinement's residual raise the next inner solve's
+// iterations by 15% at 40^3.)
+// A work item is one chunk of grid points of kSlotGroup consecutive slots: each orbital value
+// loaded (from L2) serves all of them, and one block reduction per orbital covers the group.
+constexpr int kSlotGroup = 4;
+__global__ void __launch_bounds__(kThreads) k_cproj_dots(Params P, const float2 *__restrict__ v) {
+    const int ngroups = (P.S + kSlotGroup - 1) / kSlotGroup;
+    const long long items = (long long)ngroups * P.nblk;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
-        if (P.slots[s].phase != kInnerDone) continue;
-        const long long off = (long long)s * P.g.nd;
-        float2 dv[kPPT];
+        const int g = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
+        bool act[kSlotGroup];
+        bool any = false;
 #pragma unroll
-        for (int t = 0; t < kPPT; ++t) {
-            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
-            dv[t] = idx < P.g.nd ? d[off + idx] : make_float2(0.f, 0.f);
+        for (int q = 0; q < kSlotGroup; ++q) {
+            const int s = g * kSlotGroup + q;
+            act[q] = s < P.S && P.slots[s].phase == kInnerDone;
+            any = any || act[q];
         }
-        for (int k = 0; k < P.ns; ++k) {
-            float a0 = 0.f, a1 = 0.f;
+        if (!any) continue;                              // uniform per block
+        float2 vv[kSlotGroup][kPPT];
+#pragma unroll
+        for (int q = 0; q < kSlotGroup; ++q)
 #pragma unroll
             for (int t = 0; t < kPPT; ++t) {
                 const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
-                if (idx < P.g.nd) {
-                    const float u = P.psi32[(long long)k * P.g.nd + idx];
-                    a0 += u * dv[t].x;
-                    a1 += u * dv[t].y;
+                vv[q][t] = (act[q] && idx < P.g.nd) ? v[(long long)(g * kSlotGroup + q) * P.g.nd + idx]
+                                                    : make_float2(0.f, 0.f);
+            }
+        for (int k = 0; k < P.ns; ++k) {
+            float uu[kPPT];
+#pragma unroll
+            for (int t = 0; t < kPPT; ++t) {
+                const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+                uu[t] = idx < P.g.nd ? P.psi32[(long long)k * P.g.nd + idx] : 0.f;
+            }
+            double acc[2 * kSlotGroup];
+#pragma unroll
+            for (int q = 0; q < kSlotGroup; ++q) {
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int t = 0; t < kPPT; ++t) {
+                    a0 += uu[t] * vv[q][t].x;
+                    a1 += uu[t] * vv[q][t].y;
                 }
+                acc[2 * q] = a0;
+                acc[2 * q + 1] = a1;
             }
-            double v[2] = {(double)a0, (double)a1};
-            block_sum<2>(v);
-            if (threadIdx.x == 0) {
-                double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k) * 2;
-                o[0] = v[0];
-                o[1] = v[1];
-            }
+            block_sum<2 * kSlotGroup>(acc);
+            if (threadIdx.x == 0)
+#pragma unroll
+                for (int q = 0; q < kSlotGroup; ++q)
+                    if (act[q]) {
+                        const int s = g * kSlotGroup + q;
+                        double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k) * 2;
+                        o[0] = acc[2 * q];
+                        o[1] = acc[2 * q + 1];
+                    }
         }
     }
 }
@@ -804,6 +1062,7 @@ __global__ void k_state(Params P) {
 }
 
 // Partial sums of u_k . x64 (complex) over each item of the finished slots, for k < ns.
+constexpr int kProjGroup = 8;   // orbitals reduced together (one block reduction per group)
 __global__ void __launch_bounds__(kThreads) k_proj_dots(Params P, const double2 *__restrict__ x64) {
     const long long items = (long long)P.S * P.nblk;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
@@ -816,23 +1075,32 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(Params P, const double2 
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
             xv[t] = idx < P.g.nd ? x64[off + idx] : make_double2(0.0, 0.0);
         }
-        for (int k = 0; k < P.ns; ++k) {
-            double v[2] = {0.0, 0.0};
+        for (int k0 = 0; k0 < P.ns; k0 += kProjGroup) {
+            double v[2 * kProjGroup];
 #pragma unroll
-            for (int t = 0; t < kPPT; ++t) {
-                const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
-                if (idx < P.g.nd) {
-                    const double u = P.psi[(long long)k * P.g.nd + idx];
-                    v[0] += u * xv[t].x;
-                    if (!P.proj_re_only) v[1] += u * xv[t].y;
+            for (int g = 0; g < kProjGroup; ++g) {
+                double a0 = 0.0, a1 = 0.0;
+                if (k0 + g < P.ns) {
+#pragma unroll
+                    for (int t = 0; t < kPPT; ++t) {
+                        const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+                        if (idx < P.g.nd) {
+                            const double u = P.psi[(long long)(k0 + g) * P.g.nd + idx];
+                            a0 += u * xv[t].x;
+                            if (!P.proj_re_only) a1 += u * xv[t].y;
+                        }
+                    }
                 }
+                v[2 * g] = a0;
+                v[2 * g + 1] = a1;
             }
-            block_sum<2>(v);
-            if (threadIdx.x == 0) {
-                double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k) * 2;
-                o[0] = v[0];
-                o[1] = v[1];
-            }
+            block_sum<2 * kProjGroup>(v);
+            if (threadIdx.x == 0)
+                for (int g = 0; g < kProjGroup && k0 + g < P.ns; ++g) {
+                    double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k0 + g) * 2;
+                    o[0] = v[2 * g];
+                    o[1] = v[2 * g + 1];
+                }
         }
     }
 }
@@ -1093,11 +1361,17 @@ struct SolveSpec {
 
 // xy tiles of the stencil kernel: at most 64 columns wide and at most max_threads grid columns
 // (one thread each) per block.
-Tiles pick_tiles(int nx, int ny, int max_threads) {
+// With pairs, tiles are an even number of columns wide and a thread takes two of them.
+Tiles pick_tiles(int nx, int ny, int max_threads, bool pairs = false) {
     Tiles t;
     t.ntx = (nx + 63) / 64;
     t.tx = (nx + t.ntx - 1) / t.ntx;
-    const int ty_max = std::max(1, (max_threads - 31) / t.tx);
+    if (pairs) {
+        t.tx += t.tx & 1;
+        t.ntx = (nx + t.tx - 1) / t.tx;
+    }
+    const int per_row = pairs ? t.tx / 2 : t.tx;
+    const int ty_max = std::max(1, (pairs ? max_threads : max_threads - 31) / per_row);
     const int nty = (ny + ty_max - 1) / ty_max;
     t.ty = (ny + nty - 1) / nty;
     t.nty = (ny + t.ty - 1) / t.ty;
@@ -1159,7 +1433,8 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     }
     const long long pstride = (long long)n;
     const int variant = std::max(0, std::min(2, c.opt.stencil_shape));
-    Tiles tl = pick_tiles(c.nx, c.ny, mixed ? kPaShapes32[variant].max_threads : kPaShape64.max_threads);
+    const PaShape shape = mixed ? kPaShapes32[variant] : kPaShape64;
+    Tiles tl = pick_tiles(c.nx, c.ny, shape.max_threads, shape.pairs != 0);
     if (c.opt.z_chunks > 1) {
         tl.zlen = (c.nz + c.opt.z_chunks - 1) / c.opt.z_chunks;
         tl.nzc = (c.nz + tl.zlen - 1) / tl.zlen;
@@ -1202,10 +1477,10 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     P.count = count;
     P.sys_out = sys_out;
     // mixed form with P_c applied to the right-hand sides: the refinement works in the
-    // unoccupied space, and the finished solution is projected in FP64 (the FP32 projections
-    // leave occupied components of ~1e-9..1e-8 of its norm)
+    // unoccupied space.  The FP32 projections leave occupied components of ~1e-9 of the
+    // solution's norm; below that tolerance the finished solution is also projected in FP64.
     P.cproject = mixed && sp.Tc != nullptr;
-    P.project = c.opt.project_solution != 0 || sp.grad != nullptr || P.cproject;
+    P.project = c.opt.project_solution != 0 || sp.grad != nullptr || (P.cproject && c.opt.tol < 1e-9);
     P.proj_re_only = sp.drho != nullptr && sp.grad == nullptr;
     P.ns = c.ns;
     P.psi = c.psi64;
@@ -1235,14 +1510,17 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const long long items = (long long)S * nblk;
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, (long long)dev_sms * 8));
     const unsigned wgrid = cdiv(S, kWarpsPerBlock);      // one warp per slot
-    const int pa_threads = (tl.tx * tl.ty + 31) / 32 * 32;
-    const int pa_halo = tl.ntx > 1 ? 2 * kRadius * (tl.tx + tl.ty) : 2 * kRadius * tl.tx;
+    const int per_row = shape.pairs ? tl.tx / 2 : tl.tx;
+    const int pa_threads = (per_row * tl.ty + 31) / 32 * 32;
+    // halo elements (pairs of elements for the two-column kernel) per plane
+    const int pa_halo = shape.pairs ? (tl.ntx > 1 ? kRadius * (tl.tx + tl.ty) : kRadius * tl.tx)
+                                    : (tl.ntx > 1 ? 2 * kRadius * (tl.tx + tl.ty) : 2 * kRadius * tl.tx);
     const bool pa_h1 = pa_halo <= pa_threads;
     using Pa32 = void (*)(IterArgs, Tiles, const float2 *, float2 *, long long, float2 *, const float *, Coef<float>);
     static const Pa32 pa32_table[3][2] = {
         {k_cocg_pa<float, 1, 640, 1>, k_cocg_pa<float, 2, 640, 1>},
-        {k_cocg_pa<float, 1, 416, 2>, k_cocg_pa<float, 2, 416, 2>},
-        {k_cocg_pa<float, 1, 288, 3>, k_cocg_pa<float, 2, 288, 3>}};
+        {k_cocg_pa2<1, 512>, k_cocg_pa2<2, 512>},
+        {k_cocg_pa2<1, 384>, k_cocg_pa2<2, 384>}};
     const Pa32 pa32 = pa32_table[variant][pa_h1 ? 0 : 1];
     auto pa64 = pa_h1 ? k_cocg_pa<double, 1, 448, 1> : k_cocg_pa<double, 2, 448, 1>;
     const size_t pa_smem = 2 * (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);

@@ -287,7 +287,9 @@ class Context:
         _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
         return EcResult(float(ec[0]), float(ec[1]), ecm, lam, st, stats_dict(stats, nw))
 
-    AUTOTUNE_CANDIDATES = [f"stencil block <= {t} threads, {z} z chunk(s)" for t in (640, 416, 288) for z in (1, 2)]
+    AUTOTUNE_CANDIDATES = [f"stencil {shape}, {z} z chunk(s)"
+                           for shape in ("1 column/thread <= 640 threads", "2 columns/thread <= 512 threads",
+                                         "2 columns/thread <= 384 threads") for z in (1, 2)]
 
     def autotune(self, omega: float, V, stream=None):
         """rpa_autotune: time the COCG kernel configurations on this workload, keep the fastest.

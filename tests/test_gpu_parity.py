@@ -297,3 +297,24 @@ def test_lih72_sampled_column_matches_oracle(rpa):
     assert code == rpa.RPA_OK
     ref = oracle.Oracle.from_system(s).chi_tilde(V[:1], omega, 1e-9)
     assert relerr(R.cpu().numpy()[:1], ref) < 1e-6
+
+
+@pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11)])
+@pytest.mark.parametrize("shape", [0, 1])
+def test_stencil_variants_match_oracle(rpa, shape, grid):
+    """(70, 3, 9): two x tiles with side halos and more halo elements per plane than twice the
+    block's threads (the kernels' fallback halo loop); (15, 13, 11): an odd nx, where the
+    two-column kernel holds a column past the box at zero."""
+    s = synth.small_system(grid, h=0.5, n_s=2, n_wells=2, seed=29)
+    g = oracle.Grid(s.nx, s.ny, s.nz, s.h)
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal((3, s.n_d))
+    orbs = np.array([0, 1, 1])
+    omega, tol = 0.4, 1e-11
+    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=rpa.RPA_MIXED, stencil_shape=shape)) as ctx:
+        x, _, st, code = ctx.sternheimer_solve(omega, orbs, cuda(b), project=False)
+    assert code == rpa.RPA_OK
+    sig = -s.eps[orbs] + 1j * omega
+    ref, _, rst = oracle.cocg(g, s.vloc, sig, b.astype(complex), tol, 100000)
+    assert np.all(rst == 0)
+    assert relerr(x.cpu().numpy(), ref) < 1e-8
