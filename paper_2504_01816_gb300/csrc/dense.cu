@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kTile = 32;     // output tile of the Gram kernel
 constexpr int kKc = 32;       // contraction chunk staged in shared memory
+constexpr int kEigThreads = 256;   // one block for the small Rayleigh-Ritz eigenproblem
 
 // partial[z][a][b] = sum_{r in chunk z} A[a][r] B[b][r]
 __global__ void __launch_bounds__(256) k_gram(const double *__restrict__ A, int na, const double *__restrict__ B,
@@ -156,15 +157,25 @@ __global__ void k_symmetrize(double *C, int n) {
 // Householder reduction of the symmetric matrix A (n x n, row-major, destroyed) to tridiagonal
 // form, then every eigenvalue by bisection on Sturm counts (one thread per eigenvalue), then
 // the energy sum in ascending order.  One block.  work: 3n doubles.
-__global__ void __launch_bounds__(1024) k_sym_eigvals(double *__restrict__ A, int n, double *__restrict__ lam,
-                                                      double *__restrict__ work, double weight,
-                                                      double *__restrict__ e_out) {
+// With use_smem the matrix and the work vectors are copied to shared memory first (n^2 + 3n
+// doubles); A is then left unchanged.
+__global__ void __launch_bounds__(kEigThreads) k_sym_eigvals(double *__restrict__ Ag, int n, double *__restrict__ lam,
+                                                             double *__restrict__ workg, double weight,
+                                                             double *__restrict__ e_out, int use_smem) {
     __shared__ double red[32];
     __shared__ double sh_scalar[2];
+    extern __shared__ double dyn[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double *A = Ag, *work = workg;
+    if (use_smem) {
+        A = dyn;
+        work = dyn + (size_t)n * n;
+        for (long long e = tid; e < (long long)n * n; e += nt) A[e] = Ag[e];
+        __syncthreads();
+    }
     double *v = work;           // Householder vector (length n, entries k+1..n-1 used)
     double *p = work + n;       // A v
     double *d = work + 2 * n;   // diagonal, then off-diagonal in A's subdiagonal
-    const int tid = threadIdx.x, nt = blockDim.x;
     auto block_sum = [&](double x) -> double {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if ((tid & 31) == 0) red[tid >> 5] = x;
@@ -311,7 +322,11 @@ void symmetrize(double *C, int n, cudaStream_t s) {
 }
 
 void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out, cudaStream_t s) {
-    k_sym_eigvals<<<1, 1024, 0, s>>>(C, n, lam, work, weight, e_out);
+    const size_t sh = sizeof(double) * ((size_t)n * n + 3 * (size_t)n);
+    const bool use_smem = sh <= 200 * 1024;
+    if (use_smem && sh > 48 * 1024)
+        RPA_CUDA(cudaFuncSetAttribute(k_sym_eigvals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_sym_eigvals<<<1, kEigThreads, use_smem ? sh : 0, s>>>(C, n, lam, work, weight, e_out, use_smem ? 1 : 0);
     RPA_LAUNCH("sym_eigvals");
     count_launches(1);
 }
