@@ -84,9 +84,9 @@ typedef struct {
                                   more chunks give more parallel items when few systems are in flight,
                                   at the price of re-reading a 6-plane overlap per chunk */
     int stencil_shape;         /* variant of the FP32 stencil kernel: 0 = one grid column per thread,
-                                  up to 640 threads per block; 1 = two columns per thread, up to 512
-                                  threads; 2 = two columns per thread, up to 384 threads;
-                                  rpa_autotune sets it */
+                                  up to 640 threads per block; 1 = one column per thread, up to 320
+                                  threads, two blocks per SM; 2 = two columns per thread, up to 384
+                                  threads; rpa_autotune sets it */
     int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy

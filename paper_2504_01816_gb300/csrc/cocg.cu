@@ -405,13 +405,14 @@ struct Tiles {
 // z+1 and the column front two planes ahead are in flight while plane z is computed.  Values
 // outside the box are zero.
 // Variants of the FP32 stencil kernel the autotuner (rpa_autotune) chooses from, by
-// rpa_options.stencil_shape: 0 = one column per thread, up to 640 threads per block; 1 = two
-// columns per thread, up to 512 threads; 2 = two columns per thread, up to 384 threads (more
-// registers, no spills).  The FP64 form has one shape.
+// rpa_options.stencil_shape: 0 = one column per thread, up to 640 threads per block; 1 = one
+// column per thread, up to 320 threads and two blocks per SM (one block computes while the
+// other waits at its per-plane barrier; same 96 registers); 2 = two columns per thread, up to 384
+// threads.  The FP64 form has one shape.
 struct PaShape {
     int max_threads, min_blocks, pairs;
 };
-constexpr PaShape kPaShapes32[3] = {{640, 1, 0}, {512, 1, 1}, {384, 1, 1}};
+constexpr PaShape kPaShapes32[3] = {{640, 1, 0}, {320, 2, 0}, {384, 1, 1}};
 constexpr PaShape kPaShape64 = {448, 1, 0};
 // MAXH: halo elements per thread that are prefetched into registers; any rest loads in place.
 template <typename T, int MAXH, int MAXT, int MINB>
@@ -1519,7 +1520,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     using Pa32 = void (*)(IterArgs, Tiles, const float2 *, float2 *, long long, float2 *, const float *, Coef<float>);
     static const Pa32 pa32_table[3][2] = {
         {k_cocg_pa<float, 1, 640, 1>, k_cocg_pa<float, 2, 640, 1>},
-        {k_cocg_pa2<1, 512>, k_cocg_pa2<2, 512>},
+        {k_cocg_pa<float, 1, 320, 2>, k_cocg_pa<float, 2, 320, 2>},
         {k_cocg_pa2<1, 384>, k_cocg_pa2<2, 384>}};
     const Pa32 pa32 = pa32_table[variant][pa_h1 ? 0 : 1];
     auto pa64 = pa_h1 ? k_cocg_pa<double, 1, 448, 1> : k_cocg_pa<double, 2, 448, 1>;

@@ -288,7 +288,7 @@ class Context:
         return EcResult(float(ec[0]), float(ec[1]), ecm, lam, st, stats_dict(stats, nw))
 
     AUTOTUNE_CANDIDATES = [f"stencil {shape}, {z} z chunk(s)"
-                           for shape in ("1 column/thread <= 640 threads", "2 columns/thread <= 512 threads",
+                           for shape in ("1 column/thread <= 640 threads", "1 column/thread <= 320 threads x 2 blocks",
                                          "2 columns/thread <= 384 threads") for z in (1, 2)]
 
     def autotune(self, omega: float, V, stream=None):

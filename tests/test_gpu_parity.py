@@ -300,7 +300,7 @@ def test_lih72_sampled_column_matches_oracle(rpa):
 
 
 @pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11)])
-@pytest.mark.parametrize("shape", [0, 1])
+@pytest.mark.parametrize("shape", [0, 1, 2])
 def test_stencil_variants_match_oracle(rpa, shape, grid):
     """(70, 3, 9): two x tiles with side halos and more halo elements per plane than twice the
     block's threads (the kernels' fallback halo loop); (15, 13, 11): an odd nx, where the
