@@ -17,8 +17,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                         quadrature of the dense integrand; convergence in N_omega
   rpa_ec_gradient       central finite differences of a dense sum-over-states E_c built
                         from the unoccupied eigenpairs of the projected Hamiltonian
+  gauss_sq_trace        exactness for polynomials of degree <= 2 N_o - 1 (Gauss rule); order 1
+                        is sum f(C_rr); order >= the dimension is Tr f(C) by dense eigenvalues
 """
 from .rpa_oracle import *  # noqa: F401,F403
 from .rpa_oracle import (Oracle, Grid, Coulomb, SolveStats, EcResult, fd_weights, apply_h, cocg,  # noqa: F401
                          frequency_quadrature, g_rpa, orthonormalize_cholesky, rpa_ec, num_threads,
-                         set_threads, second_difference_1d, NotSPD, rpa_ec_gradient)
+                         set_threads, second_difference_1d, NotSPD, rpa_ec_gradient, gauss_sq_trace)

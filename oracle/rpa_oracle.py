@@ -369,15 +369,51 @@ class EcResult:
     ritz_vectors: Optional[List[np.ndarray]] = None   # per frequency (ascending omega), rows y_i
 
 
+def gauss_sq_trace(C: np.ndarray, n_o: int, f) -> float:
+    """Tr f(C) of a symmetric matrix by Gauss spectral quadrature (Section "Implementation",
+    Algorithm 1): for each standard basis vector e_r, n_o steps of the Lanczos iteration with C
+    started from e_r give a tridiagonal matrix J (diagonal alpha, off-diagonal beta); the
+    eigenvalues of J are the quadrature nodes and the squares of the first components of its
+    eigenvectors the weights, e_r^T f(C) e_r ~ sum_j Q_1j^2 f(theta_j).  A Lanczos run that
+    exhausts its Krylov space (beta = 0) stops early; its rule is then exact."""
+    n = C.shape[0]
+    scale = max(float(np.max(np.abs(C))), 1e-300)
+    total = 0.0
+    for r in range(n):
+        q_prev = np.zeros(n)
+        q = np.zeros(n)
+        q[r] = 1.0
+        alpha, beta = [], []
+        b = 0.0
+        for k in range(n_o):
+            w = C @ q - b * q_prev
+            a = float(q @ w)
+            w = w - a * q
+            alpha.append(a)
+            if k == n_o - 1:
+                break
+            b = float(np.linalg.norm(w))
+            if b <= 1e-13 * scale:
+                break
+            beta.append(b)
+            q_prev, q = q, w / b
+        J = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+        theta, Q = np.linalg.eigh(J)
+        total += float(np.sum(Q[0, :] ** 2 * f(theta)))
+    return total
+
+
 def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, omega0: float = 1.0,
            max_subspace_iters: int = 100, fixed_iters: Optional[int] = None, maxit: int = 100000,
            verbose: bool = False, project_solution: bool = False, keep_ritz: bool = False,
-           independent_frequencies: bool = False) -> EcResult:
+           independent_frequencies: bool = False, sq_order: int = 0) -> EcResult:
     """E_c by Algorithm 1 with Rayleigh-Ritz: frequencies from highest to lowest, the subspace
     carried over from each frequency to the next; at each frequency iterate
     R = chi~0 V, C = V^T R, lambda = eig(C), E_cm = (w_m/2pi) sum g(lambda), M = R^T R = L L^T,
     V = R L^{-T} while |E_cm - E_cm_old| > eps_c * N_atoms / N_omega (eps_c in Ha/atom), at least
-    two iterations (E_cm starts at 0).  fixed_iters runs exactly that many iterations instead."""
+    two iterations (E_cm starts at 0).  fixed_iters runs exactly that many iterations instead.
+    sq_order > 0 evaluates E_cm = (w_m/2pi) Tr g(C) by Gauss spectral quadrature of that order
+    (gauss_sq_trace), the paper's choice; lambda are still the Ritz values."""
     omegas, weights = frequency_quadrature(n_omega, omega0)
     V = orthonormalize_cholesky(np.asarray(V0, dtype=np.float64))
     n_r = V.shape[0]
@@ -401,7 +437,8 @@ def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, om
             lam, Qc = np.linalg.eigh(C)
             if keep_ritz:
                 ritz[m] = Qc.T @ V
-            ecm = weights[m] / (2.0 * math.pi) * float(np.sum(g_rpa(lam)))
+            tr = gauss_sq_trace(C, sq_order, g_rpa) if sq_order > 0 else float(np.sum(g_rpa(lam)))
+            ecm = weights[m] / (2.0 * math.pi) * tr
             V = orthonormalize_cholesky(R)
             it += 1
             if verbose:

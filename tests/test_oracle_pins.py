@@ -292,3 +292,51 @@ def test_frozen_subspace_gradient_is_exact_derivative():
                                    independent_frequencies=True).e_c)
         fd = (e[0] - e[1]) / (2 * d)
         assert abs(grad[r] - fd) < 1e-6 * np.max(np.abs(grad)), (r, grad[r], fd)
+
+
+# ------------------------------------------------------------------ Gauss spectral quadrature
+def _random_symmetric(n, seed, shift=0.0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    return 0.5 * (A + A.T) / math.sqrt(n) + shift * np.eye(n)
+
+
+@pytest.mark.parametrize("n_o", [1, 2, 3, 4])
+def test_gauss_sq_is_exact_for_polynomials_up_to_degree_2n_minus_1(n_o):
+    """An N_o-node Gauss rule integrates polynomials of degree <= 2 N_o - 1 exactly, so the SQ
+    trace of C^k equals Tr C^k (computed by matrix powers) for k <= 2 N_o - 1, and not beyond."""
+    C = _random_symmetric(12, 5)
+    for k in range(0, 2 * n_o):
+        exact = float(np.trace(np.linalg.matrix_power(C, k)))
+        sq = oracle.gauss_sq_trace(C, n_o, lambda x, k=k: x ** k)
+        assert abs(sq - exact) <= 1e-11 * max(1.0, abs(exact)), (n_o, k)
+    k = 2 * n_o
+    exact = float(np.trace(np.linalg.matrix_power(C, k)))
+    assert abs(oracle.gauss_sq_trace(C, n_o, lambda x: x ** k) - exact) > 1e-8 * abs(exact)
+
+
+def test_gauss_sq_order_one_is_the_diagonal():
+    C = _random_symmetric(9, 6, shift=-1.5)
+    f = lambda x: np.log1p(-x) + x  # noqa: E731
+    assert abs(oracle.gauss_sq_trace(C, 1, f) - float(np.sum(f(np.diag(C))))) < 1e-13
+
+
+def test_gauss_sq_of_full_order_is_the_trace_by_eigenvalues():
+    """With N_o >= n the Lanczos runs exhaust their Krylov spaces: the rule is exact for g."""
+    C = -0.4 * np.abs(_random_symmetric(10, 7)) - 0.2 * np.eye(10)
+    lam = np.linalg.eigvalsh(C)
+    exact = float(np.sum(np.log1p(-lam) + lam))
+    assert abs(oracle.gauss_sq_trace(C, 10, oracle.g_rpa) - exact) < 1e-11 * abs(exact)
+    # and a modest order is already close for the smooth g (the paper's N_o = 3..7)
+    assert abs(oracle.gauss_sq_trace(C, 4, oracle.g_rpa) - exact) < 1e-3 * abs(exact)
+
+
+def test_rpa_ec_with_full_order_sq_equals_rayleigh_ritz():
+    s = synth.workload("tiny15").system
+    o = oracle.Oracle.from_system(s)
+    V0 = synth.trial_vectors(0, 8, s.n_d)
+    rr = oracle.rpa_ec(o, V0, 2, tol=1e-10, eps_c=0.0, fixed_iters=1)
+    sq = oracle.rpa_ec(o, V0, 2, tol=1e-10, eps_c=0.0, fixed_iters=1, sq_order=8)
+    sq3 = oracle.rpa_ec(o, V0, 2, tol=1e-10, eps_c=0.0, fixed_iters=1, sq_order=3)
+    assert np.allclose(sq.e_c_per_omega, rr.e_c_per_omega, rtol=1e-11, atol=0)
+    assert abs(sq3.e_c - rr.e_c) < 1e-3 * abs(rr.e_c)
