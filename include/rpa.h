@@ -91,6 +91,12 @@ typedef struct {
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
                                   of the fixed subspace span(V0) at every frequency */
+    int sq_order;              /* 0: E_c,m = (w_m/2pi) sum_i g(lambda_i) over the Rayleigh-Ritz values;
+                                  N_o in 1..32: E_c,m = (w_m/2pi) Tr g(V^T chi~0 V) by Gauss spectral
+                                  quadrature of order N_o (Lanczos from each basis vector, the paper's
+                                  evaluation; exact for N_o >= N_r).  The Ritz values are returned
+                                  either way.  rpa_ec_gradient requires 0 (it differentiates the
+                                  Rayleigh-Ritz energy). */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8
@@ -126,7 +132,8 @@ typedef struct {
 
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
- * profile 0, project_solution 0, z_chunks 0, stencil_shape 0, independent_frequencies 0. */
+ * profile 0, project_solution 0, z_chunks 0, stencil_shape 0, independent_frequencies 0,
+ * sq_order 0. */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).

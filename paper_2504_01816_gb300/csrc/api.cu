@@ -103,6 +103,7 @@ void validate_options(const rpa_options &o) {
     if (o.batch_systems < 0) fail(RPA_ERR_INVALID, "batch_systems must be >= 0");
     if (o.z_chunks < 0 || o.z_chunks > 64) fail(RPA_ERR_INVALID, "z_chunks must be in [0, 64]");
     if (o.stencil_shape < 0 || o.stencil_shape > 2) fail(RPA_ERR_INVALID, "stencil_shape must be 0, 1 or 2");
+    if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
 }
 
 // Gauss-Legendre nodes and weights on (-1, 1) by Newton iteration on P_n, then the map
@@ -221,6 +222,7 @@ void rpa_default_options(rpa_options *o) {
     o->z_chunks = 0;
     o->stencil_shape = 0;
     o->independent_frequencies = 0;
+    o->sq_order = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }
@@ -523,17 +525,19 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
                 RPA_CUDA(cudaMemcpyAsync(Cprev, Wm, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
                 RPA_CUDA(cudaMemcpyAsync(Vprev, V, blk, cudaMemcpyDeviceToDevice, s));
             }
+            // Gauss spectral quadrature reads C before the eigensolver may overwrite it
+            if (o.sq_order > 0) sq_trace(Wm, n_r, o.sq_order, work, wt[m] / (2.0 * M_PI), ecm_dev + 1, s);
             sym_eigvals(Wm, n_r, lam, work, wt[m] / (2.0 * M_PI), ecm_dev, s);
             // orthonormalisation: M = R^T R = L L^T, V = R L^{-T}
             orthonormalize(R, V);
             RPA_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * n_r, cudaMemcpyDeviceToHost, s));
-            RPA_CUDA(cudaMemcpyAsync(h_scal.data(), ecm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaMemcpyAsync(h_scal.data(), ecm_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
             RPA_CUDA(cudaEventRecord(b, s));
             RPA_CUDA(cudaEventSynchronize(b));
             c.stats.ms_subspace += ms_between(a, b);
             cudaEventDestroy(a);
             cudaEventDestroy(b);
-            ecm = h_scal[0];
+            ecm = o.sq_order > 0 ? h_scal[1] : h_scal[0];
             ++it;
             if (o.fixed_subspace_iters > 0) {
                 if (it >= o.fixed_subspace_iters) break;
@@ -603,6 +607,8 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
     rpa_status st = guarded([&] {
         if (!ctx || !V0_dev || !grad_dev) fail(RPA_ERR_INVALID, "NULL argument");
         Ctx &c = ctx->impl;
+        if (c.opt.sq_order != 0)
+            fail(RPA_ERR_INVALID, "rpa_ec_gradient differentiates the Rayleigh-Ritz energy: set sq_order = 0");
         const int saved = c.opt.project_solution;
         c.opt.project_solution = 1;
         try {

@@ -277,6 +277,123 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eigvals(double *__restrict_
     }
 }
 
+// Gauss spectral quadrature of Tr g(C), g(x) = log(1 - x) + x (Section "Implementation",
+// Algorithm 1).  Block r runs n_o Lanczos steps with C from the basis vector e_r; the resulting
+// tridiagonal J (alpha, beta) is the Jacobi matrix of a Gauss rule whose nodes are its
+// eigenvalues (bisection on Sturm counts) and whose weights are the squared first components
+// of its eigenvectors, here 1 / sum_k p_k(theta)^2 with the orthonormal polynomials
+// p_0 = 1, beta_k p_{k+1} = (theta - alpha_k) p_k - beta_{k-1} p_{k-1} (Golub-Welsch).  A run
+// whose Krylov space is exhausted (beta <= 1e-13 max|C|) stops early; its rule is then exact.
+// part[r] = e_r^T g(C) e_r as the rule gives it.
+constexpr int kSqThreads = 128;
+__global__ void __launch_bounds__(kSqThreads) k_sq_trace(const double *__restrict__ C, int n, int n_o,
+                                                         double *__restrict__ part) {
+    extern __shared__ double sq_sh[];
+    double *qp = sq_sh, *q = sq_sh + n, *w = sq_sh + 2 * n;
+    __shared__ double al[kMaxSqOrder], be[kMaxSqOrder], red[kSqThreads / 32];
+    __shared__ int m_sh;
+    const int r = blockIdx.x, tid = threadIdx.x;
+    auto bsum = [&](double x) -> double {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = x;
+        __syncthreads();
+        double s = 0.0;
+        for (int i = 0; i < kSqThreads / 32; ++i) s += red[i];
+        return s;
+    };
+    double mx = 0.0;
+    for (long long e = tid; e < (long long)n * n; e += kSqThreads) mx = fmax(mx, fabs(C[e]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    double scale = 0.0;
+    for (int i = 0; i < kSqThreads / 32; ++i) scale = fmax(scale, red[i]);
+    for (int i = tid; i < n; i += kSqThreads) {
+        qp[i] = 0.0;
+        q[i] = (i == r) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int m = 0;
+    double b = 0.0;
+    for (int k = 0; k < n_o; ++k) {
+        double part_a = 0.0;
+        for (int i = tid; i < n; i += kSqThreads) {
+            double s = -b * qp[i];
+            for (int j = 0; j < n; ++j) s += C[(long long)i * n + j] * q[j];
+            w[i] = s;
+            part_a += q[i] * s;
+        }
+        const double a = bsum(part_a);
+        m = k + 1;
+        if (tid == 0) al[k] = a;
+        if (k == n_o - 1) break;
+        double part_b = 0.0;
+        for (int i = tid; i < n; i += kSqThreads) {
+            w[i] -= a * q[i];
+            part_b += w[i] * w[i];
+        }
+        b = sqrt(bsum(part_b));
+        if (!(b > 1e-13 * scale)) break;
+        if (tid == 0) be[k] = b;
+        for (int i = tid; i < n; i += kSqThreads) {
+            qp[i] = q[i];
+            q[i] = w[i] / b;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) m_sh = m;
+    __syncthreads();
+    m = m_sh;
+    double contrib = 0.0;
+    if (tid < m) {
+        // Gershgorin interval of J, then bisection for its (tid)-th smallest eigenvalue
+        double lo = 1e300, hi = -1e300;
+        for (int i = 0; i < m; ++i) {
+            const double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+            lo = fmin(lo, al[i] - rad);
+            hi = fmax(hi, al[i] + rad);
+        }
+        const double pad = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+        lo -= pad;
+        hi += pad;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            int cnt = 0;
+            double d = al[0] - mid;
+            if (d < 0) ++cnt;
+            for (int i = 1; i < m; ++i) {
+                if (d == 0.0) d = 1e-300;
+                d = al[i] - mid - be[i - 1] * be[i - 1] / d;
+                if (d < 0) ++cnt;
+            }
+            if (cnt > tid) hi = mid;
+            else lo = mid;
+        }
+        const double th = 0.5 * (lo + hi);
+        // weight 1 / sum_k p_k(theta)^2
+        double p0 = 1.0, p1 = 0.0, ssq = 1.0;
+        for (int k = 0; k + 1 < m; ++k) {
+            const double pn = ((th - al[k]) * p0 - (k > 0 ? be[k - 1] * p1 : 0.0)) / be[k];
+            p1 = p0;
+            p0 = pn;
+            ssq += pn * pn;
+        }
+        contrib = (log1p(-th) + th) / ssq;
+    }
+    const double s = bsum(contrib);
+    if (tid == 0) part[r] = s;
+}
+
+// e_out = weight * sum_r part[r], in order.
+__global__ void k_sq_sum(const double *__restrict__ part, int n, double weight, double *__restrict__ e_out) {
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) s += part[r];
+    *e_out = weight * s;
+}
+
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
@@ -319,6 +436,15 @@ void symmetrize(double *C, int n, cudaStream_t s) {
     k_symmetrize<<<cdiv((long long)n * n, 256), 256, 0, s>>>(C, n);
     RPA_LAUNCH("symmetrize");
     count_launches(1);
+}
+
+void sq_trace(const double *C, int n, int n_o, double *part, double weight, double *e_out, cudaStream_t s) {
+    const size_t sh = sizeof(double) * 3 * (size_t)n;
+    if (sh > 48 * 1024) RPA_CUDA(cudaFuncSetAttribute(k_sq_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_sq_trace<<<n, kSqThreads, sh, s>>>(C, n, n_o, part);
+    k_sq_sum<<<1, 1, 0, s>>>(part, n, weight, e_out);
+    RPA_LAUNCH("sq_trace");
+    count_launches(2);
 }
 
 void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out, cudaStream_t s) {

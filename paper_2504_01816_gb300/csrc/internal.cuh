@@ -14,6 +14,7 @@ namespace rpa {
 
 constexpr int kRadius = 6;              // 12th-order centred differences
 constexpr int kMaxOmega = 64;
+constexpr int kMaxSqOrder = 32;     // largest Gauss spectral quadrature order
 
 // ------------------------------------------------------------------------------------------
 // Errors: every internal failure throws rpa::Error; the C entry points catch it and turn it
@@ -170,6 +171,8 @@ void cholesky(double *M, int n, int *dev_info, cudaStream_t s);
 void tri_inverse(const double *L, int n, double *Linv, cudaStream_t s);
 // Ascending eigenvalues of the symmetric n x n matrix C (row-major, destroyed), then
 // e_out = weight * sum_i [log1p(-lam_i) + lam_i].
+// e_out = weight * Tr g(C) by Gauss spectral quadrature of order n_o (part: n doubles of scratch)
+void sq_trace(const double *C, int n, int n_o, double *part, double weight, double *e_out, cudaStream_t s);
 void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out,
                  cudaStream_t s);
 void symmetrize(double *C, int n, cudaStream_t s);

@@ -41,7 +41,7 @@ class rpa_options(ctypes.Structure):
                 ("fixed_subspace_iters", ctypes.c_int), ("n_atoms", ctypes.c_int),
                 ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int), ("project_solution", ctypes.c_int),
                 ("z_chunks", ctypes.c_int), ("stencil_shape", ctypes.c_int),
-                ("independent_frequencies", ctypes.c_int)]
+                ("independent_frequencies", ctypes.c_int), ("sq_order", ctypes.c_int)]
 
 
 PROF_SLOTS = 8
@@ -170,6 +170,7 @@ class Options:
     z_chunks: int = 0
     stencil_shape: int = 0
     independent_frequencies: int = 0
+    sq_order: int = 0
 
     def to_c(self) -> rpa_options:
         o = rpa_options()

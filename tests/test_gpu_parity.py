@@ -318,3 +318,30 @@ def test_stencil_variants_match_oracle(rpa, shape, grid):
     ref, _, rst = oracle.cocg(g, s.vloc, sig, b.astype(complex), tol, 100000)
     assert np.all(rst == 0)
     assert relerr(x.cpu().numpy(), ref) < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ec_by_gauss_spectral_quadrature_matches_oracle(rpa, prec, tiny):
+    """E_c evaluated by Gauss spectral quadrature of order 3 (the paper's N_o) on the projected
+    matrix, and order N_r, where it equals the Rayleigh-Ritz energy."""
+    s = tiny
+    n_r, n_omega, iters, tol = 8, 3, 2, 1e-10
+    V0 = synth.trial_vectors(0, n_r, s.n_d)
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms, sq_order=3)
+    with rpa.Context.from_system(s, o) as ctx:
+        res3 = ctx.ec(cuda(V0))
+        ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters,
+                             n_atoms=s.n_atoms, sq_order=n_r))
+        resn = ctx.ec(cuda(V0))
+        ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms))
+        rr = ctx.ec(cuda(V0))
+        with pytest.raises(rpa.RpaError):
+            ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters,
+                                 n_atoms=s.n_atoms, sq_order=3))
+            ctx.ec_gradient(cuda(V0))
+    ref3 = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, n_omega, tol=tol, eps_c=0.0, fixed_iters=iters,
+                         sq_order=3)
+    assert np.max(np.abs(res3.e_c_per_omega - ref3.e_c_per_omega)) < 1e-8
+    assert abs(res3.e_c - ref3.e_c) < 1e-8
+    assert np.max(np.abs(resn.e_c_per_omega - rr.e_c_per_omega)) < 1e-11
