@@ -94,6 +94,8 @@ struct Params {
     int nsys;
     int *count;        // slots busy + systems waiting (for the host)
     int *sys_out;      // [4][nsys] per system: iterations, status, refinements, near-breakdowns
+    int *fin_list;     // [S] the finished slots of this maintenance pass, in slot order
+    int *fin_cnt;      // their number
     unsigned long long *prof;   // grid points processed by k_cocg_p/_a/_b (nullptr = off)
     // occupied-space projection of finished solutions (x <- x - sum_k (u_k . x) u_k)
     int project, ns;
@@ -120,13 +122,6 @@ struct IterArgs {
     int nx, ny, nz;
     int nper;                      // work items per slot (stencil tiles, or chunks)
 };
-
-__device__ __forceinline__ void prof_add(const Params &P, int which, int chunk) {
-    if (P.prof && threadIdx.x == 0) {
-        const long long left = P.g.nd - (long long)chunk * kChunk;
-        atomicAdd(P.prof + which, (unsigned long long)(left < kChunk ? left : kChunk));
-    }
-}
 
 // Sum N doubles over the block; the result is valid in thread 0.  Fixed order.
 template <int N>
@@ -410,7 +405,7 @@ struct Tiles {
 // other waits at its per-plane barrier; same 96 registers); 2 = two columns per thread, up to 384
 // threads.  The FP64 form has one shape.
 struct PaShape {
-    int max_threads, min_blocks, pairs;
+    int max_threads, blocks_per_sm, pairs;   // blocks_per_sm: the kernel's launch-bounds minimum
 };
 constexpr PaShape kPaShapes32[3] = {{640, 1, 0}, {320, 2, 0}, {384, 1, 1}};
 constexpr PaShape kPaShape64 = {448, 1, 0};
@@ -1148,15 +1143,54 @@ __device__ __forceinline__ double2 solution_at(const Params &P, const double2 *_
     return x;
 }
 
+// fin_list = the finished slots in slot order (block scan), so that the retiring kernels visit
+// only those, in the same order as a scan over all slots.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_finished_list(Params P) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base = 0;
+    __syncthreads();
+    for (int s0 = 0; s0 < P.S; s0 += blockDim.x) {
+        const int s = s0 + tid;
+        const int f = (s < P.S && P.slots[s].phase == kFinished) ? 1 : 0;
+        int x = f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const int excl = x - f + (warp > 0 ? wsum[warp - 1] : 0);
+        if (f) P.fin_list[base + excl] = s;
+        __syncthreads();
+        if (tid == 0) base += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (tid == 0) *P.fin_cnt = base;
+}
+
 // grad += scale * coef[j] * Re(x^2) for every finished slot, slots added in slot order.
 __global__ void k_retire_grad(Params P, const double2 *__restrict__ x64, const double *__restrict__ coef,
                               double *__restrict__ grad, double scale) {
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P.g.nd;
          idx += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int s = 0; s < P.S; ++s) {
+        const int nf = *P.fin_cnt;
+        for (int i = 0; i < nf; ++i) {
+            const int s = P.fin_list[i];
             const Slot &sl = P.slots[s];
-            if (sl.phase != kFinished) continue;
             const double2 x = solution_at(P, x64, s, idx);
             acc += coef[sl.j] * (x.x * x.x - x.y * x.y);
         }
@@ -1168,13 +1202,15 @@ __global__ void k_retire_grad(Params P, const double2 *__restrict__ x64, const d
 __global__ void k_retire_drho(Params P, const double2 *__restrict__ x64, const double *__restrict__ psi,
                               double *__restrict__ drho, double scale) {
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P.g.nd;
-         idx += (long long)gridDim.x * blockDim.x)
-        for (int s = 0; s < P.S; ++s) {
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int nf = *P.fin_cnt;
+        for (int i = 0; i < nf; ++i) {
+            const int s = P.fin_list[i];
             const Slot &sl = P.slots[s];
-            if (sl.phase != kFinished) continue;
             drho[(long long)sl.j * P.g.nd + idx] +=
                 scale * psi[(long long)sl.n * P.g.nd + idx] * solution_at(P, x64, s, idx).x;
         }
+    }
 }
 
 // x_out[sys] = x64 for every finished slot.
@@ -1447,11 +1483,12 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     double *partB = partA + (size_t)S * ntiles * 2;
     Slot *slots = (Slot *)c.sys_state.ensure(sizeof(Slot) * S);
     // ints: head, count, cnt[2], list[2][S], then per system: n, j, iters, status, refines,
-    // near-breakdowns
-    const size_t nint = 4 + 2 * (size_t)S + 6 * (size_t)nsys;
+    // near-breakdowns; then the finished-slot count and list [S]
+    const size_t nint = 4 + 2 * (size_t)S + 6 * (size_t)nsys + 1 + (size_t)S;
     int *qi = (int *)c.slot_idx.ensure(sizeof(int) * nint);
     int *head = qi, *count = qi + 1, *cnt = qi + 2, *list = qi + 4;
     int *sys_n = list + 2 * S, *sys_j = sys_n + nsys, *sys_out = sys_j + nsys;
+    int *fin_cnt = sys_out + 4 * (size_t)nsys, *fin_list = fin_cnt + 1;
     RPA_CUDA(cudaMemsetAsync(qi, 0, sizeof(int) * nint, st));
     RPA_CUDA(cudaMemcpyAsync(sys_n, sp.n.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
     RPA_CUDA(cudaMemcpyAsync(sys_j, sp.j.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
@@ -1477,6 +1514,8 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     P.nsys = nsys;
     P.count = count;
     P.sys_out = sys_out;
+    P.fin_list = fin_list;
+    P.fin_cnt = fin_cnt;
     // mixed form with P_c applied to the right-hand sides: the refinement works in the
     // unoccupied space.  The FP32 projections leave occupied components of ~1e-9 of the
     // solution's norm; below that tolerance the finished solution is also projected in FP64.
@@ -1587,6 +1626,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             }
             k_state<<<wgrid, kThreads, 0, ss>>>(P);
         }
+        k_finished_list<<<1, 1024, 0, ss>>>(P);
         if (P.project) {
             k_proj_dots<<<grid, kThreads, 0, ss>>>(P, x64);
             k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P, kFinished);
@@ -1644,7 +1684,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         RPA_LAUNCH("cocg iterations");
         maintenance(ss);
     };
-    const int per_maint = (mixed ? 7 : 4) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
+    const int per_maint = (mixed ? 8 : 5) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
     const int per_epoch = 4 * kEpoch + per_maint;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
