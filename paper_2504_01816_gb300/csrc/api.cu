@@ -361,7 +361,6 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         double *t1 = (double *)c.blockA.ensure(blk);
         double *t2 = (double *)c.blockB.ensure(blk);
         double *R = (double *)c.blockC.ensure(blk);
-        const int saved_zc = c.opt.z_chunks;
         const int nvar = c.opt.prec == RPA_MIXED ? 3 : 1;
         double best = 1e300;
         int best_i = 0;
@@ -391,7 +390,6 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         cudaEventDestroy(b);
         c.opt.stencil_shape = best_i / 2;
         c.opt.z_chunks = best_i % 2 + 1;
-        (void)saved_zc;
         if (chosen_host) *chosen_host = best_i;
     });
 }
