@@ -48,6 +48,18 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_over_ranks(total_ms, solves, device):
+    """Whole-job figures of a replica run: the slowest rank's timed milliseconds and the solves
+    of all ranks together (value = solves / time).  Every rank gets the result."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(solves)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -273,11 +285,7 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = sum(times)
     if world > 1:
-        t = torch.tensor([total_ms, solves], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms, solves = float(tmax[0]), int(t[1])
+        total_ms, solves = aggregate_over_ranks(total_ms, solves, dev)
     value = solves / (total_ms / 1e3)
 
     # end to end through the public API: pinned host V0 -> device, E_c, results back to the host
