@@ -157,7 +157,10 @@ rpa_status rpa_coulomb_apply(rpa_ctx *ctx, double power, const double *in_dev, d
 /* Solve nsys Sternheimer systems (H - eps_n + i omega) x_s = b_s (Eq. 9) by COCG, with n =
  * orbital_idx_host[s].  rhs_dev: N_d x nsys real right-hand sides.  project != 0 replaces
  * b_s by P_c b_s first (removes the occupied components, as the Galerkin initial guess
- * does).  x_dev: N_d x nsys complex (interleaved), written.  iters_dev/status_dev: nsys
+ * does); the equation then lives in the unoccupied space, and in the mixed form the stopping
+ * test is on ||P_c (b - A x)|| and x is returned with its occupied components removed (to
+ * FP64 rounding for tol < 1e-9, else to ~1e-9 of ||x||).  x_dev: N_d x nsys complex
+ * (interleaved), written.  iters_dev/status_dev: nsys
  * ints on the device (iterations, per-system rpa_status), may be NULL.  Returns the worst
  * per-system status. */
 rpa_status rpa_sternheimer_solve(rpa_ctx *ctx, double omega, const int *orbital_idx_host, int nsys,
