@@ -1,5 +1,6 @@
 """Build librpa.so (the CUDA library behind include/rpa.h) in-tree with nvcc for sm_103a."""
 import concurrent.futures
+import fcntl
 import glob
 import os
 import shutil
@@ -35,11 +36,21 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ (in parallel) and link librpa.so; returns its path."""
+    """Compile every .cu under csrc/ (in parallel) and link librpa.so; returns its path.
+    Concurrent callers (one per rank of a multi-process run) take a lock: one builds, the
+    others find the library up to date."""
     if not force and not _stale():
         return LIB
-    nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIB
+        return _build_locked(verbose)
+
+
+def _build_locked(verbose: bool) -> str:
+    nvcc = _nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
