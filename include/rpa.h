@@ -206,10 +206,9 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
 /* rpa_coulomb_apply without any device allocation inside the call.
  *
  * For callers that cannot let the library call cudaMalloc at that point: applications whose
- * device memory is already fully reserved by their own allocator or memory pool (so a fresh
- * cudaMalloc would fail), and latency-bound loops that cannot afford the device-wide
- * synchronisation a cudaMalloc/cudaFree pair can cause.  The paper has no counterpart of this
- * entry point; it computes exactly what rpa_coulomb_apply computes.
+ * device memory is already fully reserved by their own allocator or memory pool, so that a
+ * fresh cudaMalloc would fail (or would fragment the pool they manage).  The paper has no
+ * counterpart of this entry point; it computes exactly what rpa_coulomb_apply computes.
  *
  * Scratch: the library's own statically sized device array of RPA_STATIC_SCRATCH_BYTES.  A call
  * needs 2 * ncols * N_d + N_d doubles (each of the two column blocks rounded up to 256 bytes);
@@ -217,7 +216,8 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
  * provides in_dev and out_dev (N_d x ncols, column-major; they may alias).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  The context's device
- * must be the current device.
+ * must be the current device.  Like rpa_coulomb_apply, the call synchronises `stream` before
+ * it returns.
  * All calls share the one array and it keeps the last call's contents; every scratch word is
  * written before it is read, so nothing needs clearing.  Calls whose work overlaps on the GPU
  * (different streams or threads, any context) race on the array and give wrong results:
