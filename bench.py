@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the E_c time-to-solution run (eps_c 1e-5 Ha/atom)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the step of the plain FP64 form")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default COCG kernel configuration")
+    ap.add_argument("--n-r", type=int, default=0,
+                    help="trial vectors (0 = the workload's); fewer give a smaller case for profiler captures")
     return ap.parse_args()
 
 
@@ -237,6 +239,8 @@ def run_ours(args):
     import synth
 
     w = synth.workload(args.workload, tol=args.tol)
+    if args.n_r > 0:
+        w.n_r = args.n_r
     s = w.system
     V0h = synth.trial_vectors(w.seed, w.n_r, s.n_d)
     dev = torch.device("cuda", local)

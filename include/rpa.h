@@ -83,10 +83,15 @@ typedef struct {
     int z_chunks;              /* stencil work items per grid column along z (0 or 1 = whole columns);
                                   more chunks give more parallel items when few systems are in flight,
                                   at the price of re-reading a 6-plane overlap per chunk */
-    int stencil_shape;         /* variant of the FP32 stencil kernel: 0 = one grid column per thread,
-                                  up to 640 threads per block; 1 = one column per thread, up to 320
-                                  threads, two blocks per SM; 2 = two columns per thread, up to 384
-                                  threads; rpa_autotune sets it */
+    int stencil_shape;         /* COCG kernels of the mixed form.  1..3: two kernels per iteration
+                                  (direction update + stencil, then x/r update) with xy tiles and z
+                                  marching: 1 = one grid column per thread, up to 640 threads per
+                                  block; 2 = one column per thread, up to 320 threads, two blocks per
+                                  SM; 3 = two columns per thread, up to 384 threads.  4 = one fused
+                                  kernel per iteration, one block per system with whole xy planes in
+                                  a shared-memory ring (grids whose nx*ny plane fits, about 2000
+                                  points; else as 1).  0 = automatic: 4 where it fits, else 1.
+                                  rpa_autotune sets it.  The plain FP64 form always uses 1. */
     int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
@@ -97,6 +102,14 @@ typedef struct {
                                   evaluation; exact for N_o >= N_r).  The Ritz values are returned
                                   either way.  rpa_ec_gradient requires 0 (it differentiates the
                                   Rayleigh-Ritz energy). */
+    int contractions;          /* dense contractions of the chi0 application and the Rayleigh-Ritz
+                                  step -- the Kronecker per-axis transforms of nu^1/2, the P_c
+                                  coefficients and C = V^T R: 0 = automatic (tensor cores in the mixed
+                                  form, FP64 in the plain form); 1 = FP64 on CUDA cores; 2 = tensor
+                                  cores (tcgen05: six products of BF16 splits of the FP64 operands,
+                                  FP32 accumulation over k chunks of 64, chunk sums in FP64; ~1e-7
+                                  relative).  The overlap R^T R, the rotation V = R L^-T, Cholesky,
+                                  the eigensolve and rpa_coulomb_apply always use FP64. */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8
@@ -132,8 +145,8 @@ typedef struct {
 
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
- * profile 0, project_solution 0, z_chunks 0, stencil_shape 0, independent_frequencies 0,
- * sq_order 0. */
+ * profile 0, project_solution 0, z_chunks 0, stencil_shape 0 (automatic), independent_frequencies 0,
+ * sq_order 0, contractions 0 (automatic). */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).
@@ -225,14 +238,18 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
 rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *in_dev, double *out_dev,
                                      int ncols, void *stream);
 
+/* Number of configurations rpa_autotune times. */
+#define RPA_AUTOTUNE_CANDIDATES 7
+
 /* Autotuner: times one application of nu^1/2 chi0(i omega) nu^1/2 to the n_r columns of V_dev
- * for each candidate configuration of the COCG kernels -- the three stencil kernel variants of
- * rpa_options.stencil_shape (columns per thread and threads per block, i.e. the xy tile shape)
- * crossed with one or two z chunks per column -- and keeps the fastest for this context by
- * setting its stencil_shape and z_chunks options (mixed form; the plain form has one shape).
- * times_ms_host (may be NULL) receives the 6 timings in the order shape-major; *chosen_host (may
- * be NULL) the index of the chosen candidate.  The context's results do not depend on the
- * choice beyond rounding. */
+ * for each candidate configuration of the COCG kernels and keeps the fastest for this context by
+ * setting its stencil_shape and z_chunks options.  Candidates 0..5: the two-kernel variants
+ * stencil_shape = 1, 2, 3 (columns per thread and threads per block, i.e. the xy tile shape)
+ * crossed with one or two z chunks per column, index 2 (stencil_shape - 1) + (z_chunks - 1);
+ * candidate 6: the fused single-pass kernel (stencil_shape 4).  The plain FP64 form has one
+ * configuration (candidate 0).  times_ms_host (may be NULL) receives RPA_AUTOTUNE_CANDIDATES
+ * timings, -1 for a candidate that does not apply; *chosen_host (may be NULL) the index of the
+ * chosen one.  The context's results do not depend on the choice beyond rounding. */
 rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r, int *chosen_host,
                         double *times_ms_host, void *stream);
 

@@ -29,6 +29,19 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
     fail(st, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
+void allow_dynamic_smem(const void *kernel, size_t need) {
+    int dev = 0, optin = 0;
+    RPA_CUDA(cudaGetDevice(&dev));
+    RPA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    RPA_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const long long avail = (long long)optin - (long long)fa.sharedSizeBytes;
+    if ((long long)need > avail)
+        fail(RPA_ERR_INVALID, "a kernel needs %zu bytes of shared memory, more than the %lld available", need, avail);
+    if (fa.maxDynamicSharedSizeBytes < avail)
+        RPA_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail));
+}
+
 void *DevBuf::ensure(size_t need) {
     if (need <= bytes && ptr) return ptr;
     release();
@@ -63,7 +76,7 @@ Ctx::~Ctx() {
         b->release();
     if (h_state) cudaFreeHost(h_state);
     if (h_count) cudaFreeHost(h_count);
-    cudaFree(d_count);
+    cudaFree(d_tc_err);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -79,6 +92,16 @@ int prof_slot(Ctx &c, const char *name) {
     std::strncpy(c.stats.prof_name[i], name, 31);
     c.stats.prof_name[i][31] = 0;
     return i;
+}
+
+void check_tensor_core_status(Ctx &c, cudaStream_t s) {
+    int h = 0;
+    RPA_CUDA(cudaMemcpyAsync(&h, c.d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RPA_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        RPA_CUDA(cudaMemsetAsync(c.d_tc_err, 0, sizeof(int), s));
+        fail(RPA_ERR_CUDA, "a tensor-core contraction timed out waiting for its MMAs");
+    }
 }
 
 namespace {
@@ -102,8 +125,9 @@ void validate_options(const rpa_options &o) {
     if (o.n_atoms < 1) fail(RPA_ERR_INVALID, "n_atoms must be >= 1");
     if (o.batch_systems < 0) fail(RPA_ERR_INVALID, "batch_systems must be >= 0");
     if (o.z_chunks < 0 || o.z_chunks > 64) fail(RPA_ERR_INVALID, "z_chunks must be in [0, 64]");
-    if (o.stencil_shape < 0 || o.stencil_shape > 2) fail(RPA_ERR_INVALID, "stencil_shape must be 0, 1 or 2");
+    if (o.stencil_shape < 0 || o.stencil_shape > 4) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 4]");
     if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
+    if (o.contractions < 0 || o.contractions > 2) fail(RPA_ERR_INVALID, "contractions must be 0, 1 or 2");
 }
 
 // Gauss-Legendre nodes and weights on (-1, 1) by Newton iteration on P_n, then the map
@@ -179,19 +203,21 @@ int apply_nuchi0_impl(Ctx &c, double omega, const double *V, double *R, int ncol
     for (auto &x : e) RPA_CUDA(cudaEventCreate(&x));
     RPA_CUDA(cudaEventRecord(e[0], s));
     const double *dv = V;
+    const bool tc = use_tensor_cores(c);
     if (symmetric) {
-        coulomb_apply(c, 0.5, V, tmp1, ncols, s);
+        coulomb_apply(c, 0.5, V, tmp1, ncols, s, tc);
         dv = tmp1;
     }
     RPA_CUDA(cudaEventRecord(e[1], s));
     const int worst = chi0_apply(c, omega, dv, tmp2, ncols, s);
     RPA_CUDA(cudaEventRecord(e[2], s));
-    coulomb_apply(c, symmetric ? 0.5 : 1.0, tmp2, R, ncols, s);
+    coulomb_apply(c, symmetric ? 0.5 : 1.0, tmp2, R, ncols, s, tc);
     RPA_CUDA(cudaEventRecord(e[3], s));
     RPA_CUDA(cudaEventSynchronize(e[3]));
     c.stats.ms_coulomb += ms_between(e[0], e[1]) + ms_between(e[2], e[3]);
     c.stats.ms_cocg += ms_between(e[1], e[2]);
     for (auto &x : e) cudaEventDestroy(x);
+    if (tc) check_tensor_core_status(c, s);
     return worst;
 }
 
@@ -223,6 +249,7 @@ void rpa_default_options(rpa_options *o) {
     o->stencil_shape = 0;
     o->independent_frequencies = 0;
     o->sq_order = 0;
+    o->contractions = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }
@@ -277,7 +304,8 @@ rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_ord
             k_to_float<<<(unsigned)((nd * n_s + 255) / 256), 256, 0, s>>>(c.psi64, c.psi32, nd * n_s);
             RPA_LAUNCH("setup");
             RPA_CUDA(cudaMallocHost((void **)&c.h_count, 8 * sizeof(int)));
-            RPA_CUDA(cudaMalloc(&c.d_count, sizeof(int)));
+            RPA_CUDA(cudaMalloc(&c.d_tc_err, sizeof(int)));
+            RPA_CUDA(cudaMemsetAsync(c.d_tc_err, 0, sizeof(int), s));
             RPA_CUDA(cudaMalloc(&c.d_prof_points, sizeof(unsigned long long) * RPA_PROF_SLOTS));
             RPA_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
             {
@@ -361,35 +389,37 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         double *t1 = (double *)c.blockA.ensure(blk);
         double *t2 = (double *)c.blockB.ensure(blk);
         double *R = (double *)c.blockC.ensure(blk);
-        const int nvar = c.opt.prec == RPA_MIXED ? 3 : 1;
+        // candidates 0..5: split kernel variant v (stencil_shape v + 1) with z chunks z + 1, index
+        // 2 v + z; candidate 6: the fused single-pass kernel (stencil_shape 4), where a plane fits
+        const bool mixed = c.opt.prec == RPA_MIXED;
+        const bool fused_ok = mixed && fused_kernel_applies(c);
         double best = 1e300;
         int best_i = 0;
         cudaEvent_t a, b;
         RPA_CUDA(cudaEventCreate(&a));
         RPA_CUDA(cudaEventCreate(&b));
-        for (int v = 0; v < 3; ++v)
-            for (int z = 0; z < 2; ++z) {
-                const int i = 2 * v + z;
-                double ms = 1e300;
-                if (v < nvar) {
-                    c.opt.stencil_shape = v;
-                    c.opt.z_chunks = z + 1;
-                    RPA_CUDA(cudaEventRecord(a, s));
-                    apply_nuchi0_impl(c, omega, V_dev, R, n_r, 1, t1, t2, s);
-                    RPA_CUDA(cudaEventRecord(b, s));
-                    RPA_CUDA(cudaEventSynchronize(b));
-                    ms = ms_between(a, b);
-                    if (ms < best) {
-                        best = ms;
-                        best_i = i;
-                    }
+        for (int i = 0; i < RPA_AUTOTUNE_CANDIDATES; ++i) {
+            const bool run = i == 6 ? fused_ok : (mixed || i == 0);
+            double ms = -1.0;
+            if (run) {
+                c.opt.stencil_shape = i == 6 ? 4 : i / 2 + 1;
+                c.opt.z_chunks = i == 6 ? 1 : i % 2 + 1;
+                RPA_CUDA(cudaEventRecord(a, s));
+                apply_nuchi0_impl(c, omega, V_dev, R, n_r, 1, t1, t2, s);
+                RPA_CUDA(cudaEventRecord(b, s));
+                RPA_CUDA(cudaEventSynchronize(b));
+                ms = ms_between(a, b);
+                if (ms < best) {
+                    best = ms;
+                    best_i = i;
                 }
-                if (times_ms_host) times_ms_host[i] = ms;
             }
+            if (times_ms_host) times_ms_host[i] = ms;
+        }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
-        c.opt.stencil_shape = best_i / 2;
-        c.opt.z_chunks = best_i % 2 + 1;
+        c.opt.stencil_shape = best_i == 6 ? 4 : best_i / 2 + 1;
+        c.opt.z_chunks = best_i == 6 ? 1 : best_i % 2 + 1;
         if (chosen_host) *chosen_host = best_i;
     });
 }
@@ -517,7 +547,10 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
             RPA_CUDA(cudaEventCreate(&b));
             RPA_CUDA(cudaEventRecord(a, s));
             // Rayleigh-Ritz: C = V^T R, eigenvalues, E_cm = (w_m / 2 pi) sum g(lambda)
-            gram(V, n_r, R, n_r, c.nd, Wm, s, c.dense_scratch);
+            if (use_tensor_cores(c))
+                tc_gemm(V, c.nd, 1, R, c.nd, 1, n_r, n_r, c.nd, Wm, s, c.dense_scratch, c.d_tc_err);
+            else
+                gram(V, n_r, R, n_r, c.nd, Wm, s, c.dense_scratch);
             symmetrize(Wm, n_r, s);
             if (grad) {
                 RPA_CUDA(cudaMemcpyAsync(Cprev, Wm, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));

@@ -815,6 +815,435 @@ __global__ void __launch_bounds__(MAXT, 1)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Fused single-pass COCG iteration (mixed form; whole xy planes held in a shared-memory ring).
+// ---------------------------------------------------------------------------------------------
+// The recurrences of COCG rearranged so that one sweep over the state finishes iteration k-1
+// and starts iteration k.  With alpha = alpha_{k-1} and beta = beta_k known at the start
+// (both absent at k = 0), at every grid point:
+//   x_k = x_{k-1} + alpha p_{k-1},  r_k = r_{k-1} - alpha q_{k-1},  p_k = r_k + beta p_{k-1},
+//   q_k = (H - eps_n + i omega) p_k,
+// with the sums rho_k = r_k^T r_k, ||r_k||^2, pi_k = p_k^T q_k, tau_k = r_k^T q_k and
+// theta_k = q_k^T q_k (unconjugated products except the norm).  The block that owns the
+// system then takes the scalar step itself: stop on ||r_k||, else alpha_k = rho_k / pi_k and
+//   rho_{k+1} = (r_k - alpha_k q_k)^T (r_k - alpha_k q_k) = rho_k - 2 alpha_k tau_k + alpha_k^2 theta_k,
+//   beta_{k+1} = rho_{k+1} / rho_k.
+// x, r, p and q are each read and written once per iteration (64 bytes per grid point in
+// complex FP32) instead of the 84 of the two-kernel form, and one launch replaces four.  The
+// true rho_k of every sweep still sets alpha_k; only beta uses the expanded rho.
+//
+// One block owns one system and marches along z.  At step f it forms x, r, p of plane f
+// ("front", loaded one plane ahead into registers), writes them back, and stores p_k of the
+// plane into a ring of kRingPlanes planes in shared memory; after one barrier it applies the
+// 12th-order stencil to plane f-6, whose 6 planes on either side are in the ring.  Rows of a
+// ring plane are padded with kRingPad zero columns, so x neighbours past the box read zeros;
+// y neighbours past the box are predicated off; ring planes outside [0, nz) hold zeros.  A
+// thread owns two x-adjacent points, so a ring access is one 16-byte load for both.  With 14
+// ring planes the plane written at step f+1 is the one read last at step f-1, so one barrier
+// per step suffices.  Each block handles whole systems, so the state is single-buffered: a
+// thread reads q at plane f six steps before it writes q there, and reads back r_k of plane
+// f-6 that it wrote itself.
+constexpr int kRingPlanes = 14;
+constexpr int kRingPad = 6;
+constexpr int kRingMaxThreads = 512;
+
+struct RingArgs {
+    Slot *slots;
+    const int *list_in;            // active slots of this pass
+    const int *cnt_in;
+    int *list_out;                 // slots that continue (next pass)
+    int *cnt_out;
+    int *cnt_clear;                // list counter of the pass after next, cleared here
+    unsigned long long *prof;      // grid points processed (nullptr = off)
+    long long nd;
+    double tol, inner_tol;
+    int maxit;
+    int nx, ny, nz;
+    int hw;                        // point pairs per row: ceil(nx / 2)
+    int hh;                        // row pairs: ceil(ny / 2)
+    int rs;                        // ring row stride (complex elements): 2 hw + kRingPad
+    int ps;                        // ring plane stride (complex elements): ny rs + kRingPad
+};
+
+// Shared-memory bytes of the ring for an nx x ny plane.
+inline size_t ring_bytes(int nx, int ny) {
+    const size_t hw = (size_t)(nx + 1) / 2;
+    return (size_t)kRingPlanes * ((size_t)ny * (2 * hw + kRingPad) + kRingPad) * sizeof(float2);
+}
+
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+// a + s b for a complex scalar s = (sr, si) given as S1 = (sr, sr), S2 = (-si, si)
+__device__ __forceinline__ float2 cax(float2 a, float2 S1, float2 S2, float2 b) {
+    return __ffma2_rn(S2, swp(b), __ffma2_rn(S1, b, a));
+}
+// unconjugated product u^T v accumulated into (re, im)
+__device__ __forceinline__ void cdot(float &re, float &im, float2 u, float2 v) {
+    re = fmaf(u.x, v.x, fmaf(-u.y, v.y, re));
+    im = fmaf(u.x, v.y, fmaf(u.y, v.x, im));
+}
+
+template <bool EVEN>
+__device__ __forceinline__ void ld_pair(const float2 *base, int idx, bool hasb, float2 &a, float2 &b) {
+    if (EVEN) {
+        const float4 v = *reinterpret_cast<const float4 *>(base + idx);
+        a = make_float2(v.x, v.y);
+        b = make_float2(v.z, v.w);
+    } else {
+        a = base[idx];
+        b = hasb ? base[idx + 1] : make_float2(0.f, 0.f);
+    }
+}
+template <bool EVEN>
+__device__ __forceinline__ void st_pair(float2 *base, int idx, bool hasb, float2 a, float2 b) {
+    if (EVEN) {
+        *reinterpret_cast<float4 *>(base + idx) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        base[idx] = a;
+        if (hasb) base[idx + 1] = b;
+    }
+}
+
+// Scalar step of the fused iteration for one slot (thread 0 of its block).  v: rho (re, im),
+// ||r||^2, pi (re, im), tau (re, im), theta (re, im).  Same stopping rules as k_beta/k_alpha.
+__device__ void ring_scalar_step(const RingArgs &A, Slot &sl, int s, const double (&v)[9]) {
+    const int k = sl.iters;
+    const double rn = sqrt(v[2]);
+    const double thr = fmax(A.inner_tol * sl.ref_norm, 0.3 * A.tol * sl.bnorm * sl.scale);
+    const bool conv = rn <= thr;
+    const double rr2 = v[0] * v[0] + v[1] * v[1];
+    const bool nonfinite = !isfinite(rn) || !isfinite(rr2);
+    const bool zero = !(rr2 > 0.0);
+    const bool nearb = k > 0 && !(rr2 > kNearBreak * kNearBreak * v[2] * v[2]);
+    sl.rnorm = rn;
+    sl.iters = k + 1;
+    sl.total_iters += 1;
+    if (conv || k >= A.maxit || nonfinite || zero || nearb) {
+        // x_k is consistent with r_k: the inner solve ends here and the refinement takes over
+        if (nonfinite) sl.discard = 1;
+        if (!conv && (nonfinite || (zero && k == 0))) sl.status = RPA_ERR_BREAKDOWN;
+        if (!conv && !nonfinite && nearb) sl.nearbreak += 1;
+        sl.phase = kInnerDone;
+        return;
+    }
+    const double den = v[3] * v[3] + v[4] * v[4];
+    if (!(den > 0.0) || !isfinite(den)) {
+        sl.status = RPA_ERR_BREAKDOWN;
+        if (!isfinite(den)) sl.discard = 1;
+        sl.phase = kInnerDone;
+        return;
+    }
+    const double ar = (v[0] * v[3] + v[1] * v[4]) / den;   // alpha_k = rho / pi
+    const double ai = (v[1] * v[3] - v[0] * v[4]) / den;
+    const double atr = ar * v[5] - ai * v[6], ati = ar * v[6] + ai * v[5];        // alpha tau
+    const double a2r = ar * ar - ai * ai, a2i = 2.0 * ar * ai;                    // alpha^2
+    const double a2tr = a2r * v[7] - a2i * v[8], a2ti = a2r * v[8] + a2i * v[7];  // alpha^2 theta
+    const double nr_ = v[0] - 2.0 * atr + a2tr, ni_ = v[1] - 2.0 * ati + a2ti;    // rho_{k+1}
+    sl.alpha_re = ar;
+    sl.alpha_im = ai;
+    sl.beta_re = (nr_ * v[0] + ni_ * v[1]) / rr2;
+    sl.beta_im = (ni_ * v[0] - nr_ * v[1]) / rr2;
+    const int pos = atomicAdd(A.cnt_out, 1);
+    A.list_out[pos] = s;
+}
+
+// Two x-adjacent points (x, x+1) of row y from a ring plane: one 16-byte shared load.
+__device__ __forceinline__ void ring_pair(const unsigned char *addr, float2 &a, float2 &b) {
+    const float4 t = *reinterpret_cast<const float4 *>(addr);
+    a = make_float2(t.x, t.y);
+    b = make_float2(t.z, t.w);
+}
+
+template <bool EVEN>
+__global__ void __launch_bounds__(kRingMaxThreads, 1)
+    k_cocg_ring(RingArgs A, float2 *__restrict__ xg, float2 *__restrict__ rg, float2 *__restrict__ pg,
+                float2 *__restrict__ qg, const float *__restrict__ vloc, Coef<float> cf) {
+    extern __shared__ float4 ring4[];
+    unsigned char *const ring = reinterpret_cast<unsigned char *>(ring4);
+    const int tid = threadIdx.x;
+    const int nx = A.nx, ny = A.ny, nz = A.nz, hw = A.hw;
+    const int plane = nx * ny;                     // grid functions have < 2^31 points
+    const int rsb = A.rs * 8, psb = A.ps * 8;      // ring row / plane strides in bytes
+    const bool own = tid < hw * A.hh;
+    const int by = own ? tid / hw : 0;
+    const int gx = own ? 2 * (tid - by * hw) : 0, gy = 2 * by;
+    const bool hasb = own && gx + 1 < nx;          // point (x+1) lies in the box (odd nx)
+    const bool row1 = own && gy + 1 < ny;          // row y+1 lies in the box (odd ny)
+    const int col0 = gy * nx + gx, col1 = col0 + nx;          // in-plane index of (x, y), (x, y+1)
+    const int rb0 = gy * rsb + (kRingPad + gx) * 8;           // ring byte offsets of the two pairs
+    const int rb1 = rb0 + rsb;
+    const int rb1z = row1 ? rb1 : 0;               // row y+1, or the (zero) start of the plane
+    const float2 zero = make_float2(0.f, 0.f);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (blockIdx.x == 0 && tid == 0) *A.cnt_clear = 0;
+    for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
+    const float2 c0 = make_float2(3.f * cf.a[0], 3.f * cf.a[0]);
+    const int n_items = *A.cnt_in;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int s = A.list_in[it];
+        Slot &sl = A.slots[s];
+        const bool first = sl.iters == 0;
+        const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
+        const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
+        const float shr = (float)sl.shift_re, shi = (float)sl.shift_im;
+        const long long off = (long long)s * A.nd;
+        float2 *const xs = xg + off;
+        float2 *const rsv = rg + off;
+        float2 *const psv = pg + off;
+        float2 *const qs = qg + off;
+        __syncthreads();                           // the previous item's ring readers are done
+        if (own) {                                 // planes -6 .. -1 (ring slots 8 .. 13) are zero
+#pragma unroll
+            for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                *reinterpret_cast<float4 *>(ring + m * psb + rb0) = zero4;
+                if (row1) *reinterpret_cast<float4 *>(ring + m * psb + rb1) = zero4;
+            }
+        }
+        // raw front of plane 0 (x, r, p, q of rows y and y+1)
+        float2 fx[4], fr[4], fp[4], fq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fx[i] = fr[i] = fp[i] = fq[i] = zero;
+        if (own) {
+            ld_pair<EVEN>(rsv, col0, hasb, fr[0], fr[1]);
+            if (row1) ld_pair<EVEN>(rsv, col1, hasb, fr[2], fr[3]);
+            if (!first) {
+                ld_pair<EVEN>(xs, col0, hasb, fx[0], fx[1]);
+                ld_pair<EVEN>(psv, col0, hasb, fp[0], fp[1]);
+                ld_pair<EVEN>(qs, col0, hasb, fq[0], fq[1]);
+                if (row1) {
+                    ld_pair<EVEN>(xs, col1, hasb, fx[2], fx[3]);
+                    ld_pair<EVEN>(psv, col1, hasb, fp[2], fp[3]);
+                    ld_pair<EVEN>(qs, col1, hasb, fq[2], fq[3]);
+                }
+            }
+        }
+        float a_rho_r = 0.f, a_rho_i = 0.f, a_nr = 0.f, a_pi_r = 0.f, a_pi_i = 0.f;
+        float a_tau_r = 0.f, a_tau_i = 0.f, a_th_r = 0.f, a_th_i = 0.f;
+        const int nsteps = nz + kRadius;
+        // rolled loop: unrolled over the ring (compile-time slots) it needs far more registers
+        for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
+            // r_k and V of the stencil's plane z = f - 6 (r_k written at step z), in flight during the
+            // front and the barrier
+            const int z = f - kRadius;
+            float2 rk[4] = {zero, zero, zero, zero};
+            float vv[4] = {0.f, 0.f, 0.f, 0.f};
+            if (own && z >= 0) {
+                const int g0 = z * plane + col0, g1 = g0 + nx;
+                ld_pair<EVEN>(rsv, g0, hasb, rk[0], rk[1]);
+                vv[0] = vloc[g0];
+                vv[1] = hasb ? vloc[g0 + 1] : 0.f;
+                if (row1) {
+                    ld_pair<EVEN>(rsv, g1, hasb, rk[2], rk[3]);
+                    vv[2] = vloc[g1];
+                    vv[3] = hasb ? vloc[g1 + 1] : 0.f;
+                }
+            }
+            // 1. front plane f: x_k, r_k, p_k of the 2 x 2 points, p_k into ring slot u
+            float2 pk[4] = {zero, zero, zero, zero};
+            if (own && f < nz) {
+                float2 rr[4];
+                if (first) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) rr[i] = pk[i] = fr[i];
+                } else {
+                    const float2 A1 = make_float2(alr, alr), A2 = make_float2(-ali, ali);
+                    const float2 N1 = make_float2(-alr, -alr), N2 = make_float2(ali, -ali);
+                    const float2 B1 = make_float2(ber, ber), B2 = make_float2(-bei, bei);
+                    float2 xx[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        xx[i] = cax(fx[i], A1, A2, fp[i]);
+                        rr[i] = cax(fr[i], N1, N2, fq[i]);
+                        pk[i] = cax(rr[i], B1, B2, fp[i]);
+                    }
+                    st_pair<EVEN>(xs, f * plane + col0, hasb, xx[0], xx[1]);
+                    st_pair<EVEN>(rsv, f * plane + col0, hasb, rr[0], rr[1]);
+                    if (row1) {
+                        st_pair<EVEN>(xs, f * plane + col1, hasb, xx[2], xx[3]);
+                        st_pair<EVEN>(rsv, f * plane + col1, hasb, rr[2], rr[3]);
+                    }
+                }
+                if (!hasb) pk[1] = pk[3] = zero;
+                if (!row1) pk[2] = pk[3] = zero;
+                st_pair<EVEN>(psv, f * plane + col0, hasb, pk[0], pk[1]);
+                if (row1) st_pair<EVEN>(psv, f * plane + col1, hasb, pk[2], pk[3]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool in = (i & 1 ? hasb : true) && (i & 2 ? row1 : true);
+                    if (in) {
+                        cdot(a_rho_r, a_rho_i, rr[i], rr[i]);
+                        a_nr = fmaf(rr[i].x, rr[i].x, fmaf(rr[i].y, rr[i].y, a_nr));
+                    }
+                }
+            }
+            if (own) {
+                *reinterpret_cast<float4 *>(ring + u * psb + rb0) = make_float4(pk[0].x, pk[0].y, pk[1].x, pk[1].y);
+                if (row1) *reinterpret_cast<float4 *>(ring + u * psb + rb1) = make_float4(pk[2].x, pk[2].y, pk[3].x, pk[3].y);
+            }
+            // 2. the next front plane, in flight during the stencil below
+            if (own) {
+                if (f + 1 < nz) {
+                    const int g0 = (f + 1) * plane + col0, g1 = g0 + nx;
+                    ld_pair<EVEN>(rsv, g0, hasb, fr[0], fr[1]);
+                    if (row1) ld_pair<EVEN>(rsv, g1, hasb, fr[2], fr[3]);
+                    if (!first) {
+                        ld_pair<EVEN>(xs, g0, hasb, fx[0], fx[1]);
+                        ld_pair<EVEN>(psv, g0, hasb, fp[0], fp[1]);
+                        ld_pair<EVEN>(qs, g0, hasb, fq[0], fq[1]);
+                        if (row1) {
+                            ld_pair<EVEN>(xs, g1, hasb, fx[2], fx[3]);
+                            ld_pair<EVEN>(psv, g1, hasb, fp[2], fp[3]);
+                            ld_pair<EVEN>(qs, g1, hasb, fq[2], fq[3]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // 3. q_k = (H + sigma) p_k on plane z, its 6 neighbour planes from the ring
+            if (own && z >= 0) {
+                const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
+                const unsigned char *const pz = ring + cz * psb;
+                const float2 SH = make_float2(shr, shr), SI = make_float2(-shi, shi);
+                // centre and x neighbours of one row: 7 16-byte loads (positions x-6 .. x+7)
+                auto xrow = [&](const unsigned char *pr, float va, float vb, float2 &ca, float2 &cb, float2 &qa,
+                                float2 &qb) {
+                    float4 X[7];
+#pragma unroll
+                    for (int m = 0; m < 7; ++m) X[m] = *reinterpret_cast<const float4 *>(pr - 48 + 16 * m);
+                    auto xat = [&](int o) -> float2 {
+                        const float4 t = X[(o + 6) >> 1];
+                        return ((o + 6) & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
+                    };
+                    ca = xat(0);
+                    cb = xat(1);
+                    qa = __ffma2_rn(SI, swp(ca), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(va, va))), ca));
+                    qb = __ffma2_rn(SI, swp(cb), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(vb, vb))), cb));
+#pragma unroll
+                    for (int d = 1; d <= kRadius; ++d) {
+                        const float2 cd = make_float2(cf.a[d], cf.a[d]);
+                        qa = __ffma2_rn(cd, __fadd2_rn(xat(-d), xat(d)), qa);
+                        qb = __ffma2_rn(cd, __fadd2_rn(xat(1 - d), xat(1 + d)), qb);
+                    }
+                };
+                float2 c0_, c1_, c2_, c3_, q0, q1, q2, q3;
+                xrow(pz + rb0, vv[0], vv[1], c0_, c1_, q0, q1);
+                // row y+1 outside the box (odd ny): its values are zero neighbours of row y, and its
+                // own q is discarded (the loads repeat row y, an address inside the plane)
+                xrow(pz + (row1 ? rb1 : rb0), vv[2], vv[3], c2_, c3_, q2, q3);
+                if (!row1) c2_ = c3_ = zero;
+                // y neighbours: rows y-6 .. y-1 and y+2 .. y+7 from the ring (the plane's first 16
+                // bytes are padding, i.e. zero, and stand for rows outside the box); rows y and
+                // y+1 are the centres above
+#pragma unroll
+                for (int d = 1; d <= kRadius; ++d) {
+                    float2 u0, u1, l0, l1;              // rows y-d and y+1+d
+                    ring_pair(pz + (gy - d >= 0 ? rb0 - d * rsb : 0), u0, u1);
+                    ring_pair(pz + (gy + 1 + d < ny ? rb1 + d * rsb : 0), l0, l1);
+                    // row y at distance d: rows y-d and y+d; row y+1: rows y+1-d and y+1+d
+                    float2 dn0, dn1, up0, up1;          // row y+d (for row y), row y+1-d (for row y+1)
+                    if (d == 1) {
+                        dn0 = c2_; dn1 = c3_;         // row y+1
+                        up0 = c0_; up1 = c1_;         // row y
+                    } else {
+                        ring_pair(pz + (gy + d < ny ? rb0 + d * rsb : 0), dn0, dn1);
+                        ring_pair(pz + (gy + 1 - d >= 0 ? rb1 - d * rsb : 0), up0, up1);
+                    }
+                    const int sm = cz >= d ? cz - d : cz + kRingPlanes - d;
+                    const int sp = cz + d < kRingPlanes ? cz + d : cz + d - kRingPlanes;
+                    float2 zm0, zm1, zm2, zm3, zp0, zp1, zp2, zp3;
+                    ring_pair(ring + sm * psb + rb0, zm0, zm1);
+                    ring_pair(ring + sp * psb + rb0, zp0, zp1);
+                    ring_pair(ring + sm * psb + rb1z, zm2, zm3);  // row y+1 outside the box: padding
+                    ring_pair(ring + sp * psb + rb1z, zp2, zp3);
+                    const float2 cd = make_float2(cf.a[d], cf.a[d]);
+                    q0 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u0, dn0), __fadd2_rn(zm0, zp0)), q0);
+                    q1 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u1, dn1), __fadd2_rn(zm1, zp1)), q1);
+                    q2 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up0, l0), __fadd2_rn(zm2, zp2)), q2);
+                    q3 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up1, l1), __fadd2_rn(zm3, zp3)), q3);
+                }
+                st_pair<EVEN>(qs, z * plane + col0, hasb, q0, q1);
+                if (row1) st_pair<EVEN>(qs, z * plane + col1, hasb, q2, q3);
+                cdot(a_pi_r, a_pi_i, c0_, q0);
+                cdot(a_tau_r, a_tau_i, rk[0], q0);
+                cdot(a_th_r, a_th_i, q0, q0);
+                if (hasb) {
+                    cdot(a_pi_r, a_pi_i, c1_, q1);
+                    cdot(a_tau_r, a_tau_i, rk[1], q1);
+                    cdot(a_th_r, a_th_i, q1, q1);
+                }
+                if (row1) {
+                    cdot(a_pi_r, a_pi_i, c2_, q2);
+                    cdot(a_tau_r, a_tau_i, rk[2], q2);
+                    cdot(a_th_r, a_th_i, q2, q2);
+                    if (hasb) {
+                        cdot(a_pi_r, a_pi_i, c3_, q3);
+                        cdot(a_tau_r, a_tau_i, rk[3], q3);
+                        cdot(a_th_r, a_th_i, q3, q3);
+                    }
+                }
+            }
+        }
+        double v[9] = {a_rho_r, a_rho_i, a_nr, a_pi_r, a_pi_i, a_tau_r, a_tau_i, a_th_r, a_th_i};
+        block_sum_any<9>(v);
+        if (tid == 0) {
+            ring_scalar_step(A, sl, s, v);
+            if (A.prof) atomicAdd(A.prof + 1, (unsigned long long)A.nd);
+        }
+    }
+}
+
+// Active list of the first pass of an epoch: the slots whose inner solve runs, in slot order
+// (block scan); clears the other list counters.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_ring_list(Params P) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base = 0;
+    if (tid < 3) P.cnt[1 + tid] = 0;
+    __syncthreads();
+    for (int s0 = 0; s0 < P.S; s0 += blockDim.x) {
+        const int s = s0 + tid;
+        const int f = (s < P.S && P.slots[s].phase == kInner) ? 1 : 0;
+        int x = f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        const int excl = x - f + (warp > 0 ? wsum[warp - 1] : 0);
+        if (f) P.list[base + excl] = s;
+        __syncthreads();
+        if (tid == 0) base += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (tid == 0) P.cnt[0] = base;
+}
+
+using RingFn = void (*)(RingArgs, float2 *, float2 *, float2 *, float2 *, const float *, Coef<float>);
+
+// The fused kernel applies when a plane's ring fits in a block's shared memory (beside the
+// kernel's static shared memory) and a plane has at most kRingMaxThreads blocks of 2 x 2 points.
+bool ring_fits(int nx, int ny, RingFn fn, int smem_optin) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    const long long blocks = (long long)((nx + 1) / 2) * ((ny + 1) / 2);
+    return blocks <= kRingMaxThreads && ring_bytes(nx, ny) + fa.sharedSizeBytes <= (size_t)smem_optin;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Maintenance kernels (between epochs).  Slot phases do not change while these item kernels
 // run, so every thread of a block reads the same phase.
 // ---------------------------------------------------------------------------------------------
@@ -1469,7 +1898,17 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         q = cv.take<double2>(n);
     }
     const long long pstride = (long long)n;
-    const int variant = std::max(0, std::min(2, c.opt.stencil_shape));
+    int dev_sms = 0, smem_optin = 0;
+    RPA_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
+    RPA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
+    // rpa_options.stencil_shape: 0 = automatic (the fused kernel where a plane fits its ring, else
+    // split variant 1), 1..3 = the split kernels' variants, 4 = the fused kernel (split variant 1
+    // where a plane does not fit).  The plain FP64 form always runs the split kernels.
+    const int want = std::max(0, std::min(4, c.opt.stencil_shape));
+    const bool even_nx = (c.nx % 2) == 0;
+    const RingFn ring_fn = even_nx ? k_cocg_ring<true> : k_cocg_ring<false>;
+    const bool use_ring = mixed && (want == 0 || want == 4) && ring_fits(c.nx, c.ny, ring_fn, smem_optin);
+    const int variant = (want >= 1 && want <= 3) ? want - 1 : 0;
     const PaShape shape = mixed ? kPaShapes32[variant] : kPaShape64;
     Tiles tl = pick_tiles(c.nx, c.ny, shape.max_threads, shape.pairs != 0);
     if (c.opt.z_chunks > 1) {
@@ -1482,12 +1921,13 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     double *partA = (double *)c.cocg_partials.ensure(sizeof(double) * (size_t)S * (2 * ntiles + 3 * nblk));
     double *partB = partA + (size_t)S * ntiles * 2;
     Slot *slots = (Slot *)c.sys_state.ensure(sizeof(Slot) * S);
-    // ints: head, count, cnt[2], list[2][S], then per system: n, j, iters, status, refines,
-    // near-breakdowns; then the finished-slot count and list [S]
-    const size_t nint = 4 + 2 * (size_t)S + 6 * (size_t)nsys + 1 + (size_t)S;
+    // ints: head, count, cnt[4], list[4][S], then per system: n, j, iters, status, refines,
+    // near-breakdowns; then the finished-slot count and list [S].  The split kernels use lists 0
+    // and 1 (by iteration parity), the fused kernel all four in rotation.
+    const size_t nint = 6 + 4 * (size_t)S + 6 * (size_t)nsys + 1 + (size_t)S;
     int *qi = (int *)c.slot_idx.ensure(sizeof(int) * nint);
-    int *head = qi, *count = qi + 1, *cnt = qi + 2, *list = qi + 4;
-    int *sys_n = list + 2 * S, *sys_j = sys_n + nsys, *sys_out = sys_j + nsys;
+    int *head = qi, *count = qi + 1, *cnt = qi + 2, *list = qi + 6;
+    int *sys_n = list + 4 * S, *sys_j = sys_n + nsys, *sys_out = sys_j + nsys;
     int *fin_cnt = sys_out + 4 * (size_t)nsys, *fin_list = fin_cnt + 1;
     RPA_CUDA(cudaMemsetAsync(qi, 0, sizeof(int) * nint, st));
     RPA_CUDA(cudaMemcpyAsync(sys_n, sp.n.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
@@ -1545,8 +1985,6 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         ia_b[par].nper = nblk;
     }
 
-    int dev_sms = 0;
-    RPA_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
     const long long items = (long long)S * nblk;
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, (long long)dev_sms * 8));
     const unsigned wgrid = cdiv(S, kWarpsPerBlock);      // one warp per slot
@@ -1564,10 +2002,8 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const Pa32 pa32 = pa32_table[variant][pa_h1 ? 0 : 1];
     auto pa64 = pa_h1 ? k_cocg_pa<double, 1, 448, 1> : k_cocg_pa<double, 2, 448, 1>;
     const size_t pa_smem = 2 * (size_t)(tl.tx + 2 * kRadius) * (tl.ty + 2 * kRadius) * (mixed ? 8 : 16);
-    if (pa_smem > 48 * 1024) {
-        if (mixed) RPA_CUDA(cudaFuncSetAttribute(pa32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
-        else RPA_CUDA(cudaFuncSetAttribute(pa64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
-    }
+    if (mixed) allow_dynamic_smem((const void *)pa32, pa_smem);
+    else allow_dynamic_smem((const void *)pa64, pa_smem);
     int pa_per_sm = 1;
     if (mixed)
         RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa_per_sm, pa32, pa_threads, pa_smem));
@@ -1579,21 +2015,63 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const Coef<double> cf64 = cast_coef<double>(c.coef);
     const double scale = 4.0 / (c.h * c.h * c.h);
 
-    // profiling: events around every launch of the three item kernels
+    // the fused kernel: one block per system, four rotating active lists
+    RingArgs ra[4];
+    unsigned ring_grid = 1, ring_threads = 32;
+    size_t ring_smem = 0;
+    if (use_ring) {
+        const int hw = (c.nx + 1) / 2;
+        for (int i = 0; i < 4; ++i) {
+            RingArgs a{};
+            a.slots = slots;
+            a.list_in = list + i * S;
+            a.cnt_in = cnt + i;
+            a.list_out = list + ((i + 1) & 3) * S;
+            a.cnt_out = cnt + ((i + 1) & 3);
+            a.cnt_clear = cnt + ((i + 2) & 3);
+            a.nd = nd;
+            a.tol = c.opt.tol;
+            a.inner_tol = c.opt.inner_tol;
+            a.maxit = c.opt.maxit;
+            a.nx = c.nx;
+            a.ny = c.ny;
+            a.nz = c.nz;
+            a.hw = hw;
+            a.hh = (c.ny + 1) / 2;
+            a.rs = 2 * hw + kRingPad;
+            a.ps = c.ny * a.rs + kRingPad;
+            ra[i] = a;
+        }
+        ring_smem = ring_bytes(c.nx, c.ny);
+        ring_threads = (unsigned)((hw * ((c.ny + 1) / 2) + 31) / 32 * 32);
+        allow_dynamic_smem((const void *)ring_fn, ring_smem);
+        int per_sm = 1;
+        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_fn, (int)ring_threads, ring_smem));
+        ring_grid = (unsigned)std::max<long long>(1, std::min<long long>(S, (long long)dev_sms * std::max(1, per_sm)));
+    }
+
+    // profiling: events around every launch of the item kernels of the iteration
     const bool prof = c.opt.profile != 0;
     const char *tn = mixed ? "c64" : "c128";
     char names[3][32];
     std::snprintf(names[0], 32, "-");
-    std::snprintf(names[1], 32, "k_cocg_pa<%s>", tn);
-    std::snprintf(names[2], 32, "k_cocg_b<%s>", tn);
+    if (use_ring) {
+        std::snprintf(names[1], 32, "k_cocg_ring<%s>", tn);
+        std::snprintf(names[2], 32, "-");
+    } else {
+        std::snprintf(names[1], 32, "k_cocg_pa<%s>", tn);
+        std::snprintf(names[2], 32, "k_cocg_b<%s>", tn);
+    }
     const double csz = mixed ? 8.0 : 16.0, rsz = mixed ? 4.0 : 8.0;
     // algorithmic bytes per grid point: pa reads r, p_old, V and writes p_new, q; b reads x, r, p, q
-    // and writes x, r
-    const double bytes_per_point[3] = {0.0, 4 * csz + rsz, 6 * csz};
+    // and writes x, r; the fused kernel reads and writes x, r, p, q (V is read once per plane and
+    // block, not per system, and is not counted)
+    const double bytes_per_point[3] = {0.0, use_ring ? 8 * csz : 4 * csz + rsz, use_ring ? 0.0 : 6 * csz};
     if (prof) {
         RPA_CUDA(cudaMemsetAsync(c.d_prof_points, 0, sizeof(unsigned long long) * 3, st));
         P.prof = c.d_prof_points;
         for (int par = 0; par < 2; ++par) ia_pa[par].prof = ia_b[par].prof = c.d_prof_points;
+        for (auto &a : ra) a.prof = c.d_prof_points;
     }
     // Two graph instances of one epoch (alternating, so that the events of one can be read while
     // the other runs); without graphs the same launches go straight to the stream.
@@ -1655,6 +2133,18 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             if (capturing) RPA_CUDA(cudaEventRecordWithFlags(e, ss, cudaEventRecordExternal));
             else RPA_CUDA(cudaEventRecord(e, ss));
         };
+        if (use_ring) {
+            k_ring_list<<<1, 1024, 0, ss>>>(P);
+            for (int e = 0; e < kEpoch; ++e) {
+                rec(4 * e + 0);
+                ring_fn<<<ring_grid, ring_threads, ring_smem, ss>>>(ra[e & 3], (float2 *)xin, (float2 *)r,
+                                                                    (float2 *)p, (float2 *)q, c.vloc32, cf32);
+                rec(4 * e + 1);
+            }
+            RPA_LAUNCH("cocg iterations (fused)");
+            maintenance(ss);
+            return;
+        }
         for (int e = 0; e < kEpoch; ++e) {
             const int par = e & 1;
             const int t0 = 2 * e * 2;
@@ -1685,7 +2175,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         maintenance(ss);
     };
     const int per_maint = (mixed ? 8 : 5) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
-    const int per_epoch = 4 * kEpoch + per_maint;
+    const int per_epoch = (use_ring ? 1 + kEpoch : 4 * kEpoch) + per_maint;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     if (use_graph) {
@@ -1708,6 +2198,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         if (!prof) return;
         const int set = (int)(k & 1);
         for (int t = 0; t < kTimed; ++t) {
+            if (use_ring && (t & 1)) continue;      // the fused kernel: one timed launch per iteration
             float ms = 0.f;
             RPA_CUDA(cudaEventElapsedTime(&ms, evs[((size_t)set * kTimed + t) * 2], evs[((size_t)set * kTimed + t) * 2 + 1]));
             prof_ms[1 + t % 2] += ms;
@@ -1749,7 +2240,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     if (prof) {
         unsigned long long pts[3];
         RPA_CUDA(cudaMemcpy(pts, c.d_prof_points, sizeof pts, cudaMemcpyDeviceToHost));
-        for (int k = 1; k < 3; ++k) {
+        for (int k = 1; k < (use_ring ? 2 : 3); ++k) {
             const int sl = prof_slot(c, names[k]);
             c.stats.prof_ms[sl] += prof_ms[k];
             c.stats.prof_launches[sl] += prof_n[k];
@@ -1782,7 +2273,10 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
 
 // T[s][k] = u_k . rows[s] for nrows rows.
 void pc_coefficients(Ctx &c, const double *rows, int nrows, double *T, cudaStream_t st) {
-    gram(rows, nrows, c.psi64, c.ns, c.nd, T, st, c.dense_scratch);
+    if (use_tensor_cores(c))
+        tc_gemm(rows, c.nd, 1, c.psi64, c.nd, 1, nrows, c.ns, c.nd, T, st, c.dense_scratch, c.d_tc_err);
+    else
+        gram(rows, nrows, c.psi64, c.ns, c.nd, T, st, c.dense_scratch);
 }
 
 void check_orbitals(const Ctx &c, const int *orb, int nsys) {
@@ -1791,6 +2285,12 @@ void check_orbitals(const Ctx &c, const int *orb, int nsys) {
 }
 
 }  // namespace
+
+bool fused_kernel_applies(const Ctx &c) {
+    int smem_optin = 0;
+    RPA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
+    return ring_fits(c.nx, c.ny, (c.nx % 2) == 0 ? k_cocg_ring<true> : k_cocg_ring<false>, smem_optin);
+}
 
 int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
                       std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {

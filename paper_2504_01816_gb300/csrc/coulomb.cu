@@ -8,6 +8,8 @@
 // i.e. three per-axis transforms with Q^T, a pointwise scale, three transforms with Q.
 // The 1D eigendecompositions are computed once per context on the host (cyclic Jacobi in
 // FP64; n_a is at most a few hundred).
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -151,8 +153,7 @@ static void axis_pass(Ctx &c, int axis, const double *in, double *out, int ncols
     const long long inner = axis == 0 ? 1 : axis == 1 ? c.nx : (long long)c.nx * c.ny;
     const long long outer = (long long)ncols * c.nd / ((long long)n * inner);
     const size_t sh = sizeof(double) * ((size_t)n * n + (size_t)n * 33);
-    if (sh > 227 * 1024) fail(RPA_ERR_INVALID, "grid dimension %d too large for the Coulomb transform", n);
-    if (sh > 48 * 1024) RPA_CUDA(cudaFuncSetAttribute(k_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    allow_dynamic_smem((const void *)k_axis, sh);   // rejects grid dimensions above ~150
     const long long blocks = inner > 1 ? outer * ((inner + 31) / 32) : (outer + 31) / 32;
     k_axis<<<(unsigned)blocks, 256, sh, s>>>(in, out, c.Q[axis], n, inner, outer, forward, scale, c.nd);
     RPA_LAUNCH("coulomb axis transform");
@@ -180,6 +181,53 @@ void *static_scratch(int dev) {
     return g_scratch_addr[dev];
 }
 }  // namespace
+
+// The same per-axis transform as a batch of tensor-core contractions (tc_gemm_batched):
+//   axis x: one contraction, rows (o) of length n_x times M^T;
+//   axis y: one contraction per (column, z) slab, M (n_y x n_y) times the slab (n_y x n_x);
+//   axis z: one contraction per column, M (n_z x n_z) times the column (n_z x n_x n_y),
+// with M = Q^T (forward) or Q (back), Q[i*n+a] row-major.
+static void axis_pass_tc(Ctx &c, int axis, const double *in, double *out, int ncols, int forward,
+                         const double *scale, cudaStream_t s) {
+    const int n = axis == 0 ? c.nx : axis == 1 ? c.ny : c.nz;
+    const double *Q = c.Q[axis];
+    // M(a, b) = Q[b][a] (forward) or Q[a][b] (back): element strides of (a, b)
+    const long long ma = forward ? 1 : n, mb = forward ? n : 1;
+    if (axis == 0) {
+        const long long rows = (long long)ncols * c.nd / n;
+        if (rows > (long long)INT32_MAX) fail(RPA_ERR_INVALID, "too many rows for the tensor-core transform");
+        // D[o][a] = sum_b in[o][b] M(a, b): A = in (rows o, k = b), B(a, b) = M(a, b)
+        tc_gemm_batched(in, n, 1, 0, Q, ma, mb, 0, (int)rows, n, n, out, n, 1, 1, 1, scale, c.nd, s, c.d_tc_err);
+    } else if (axis == 1) {
+        const long long slab = (long long)n * c.nx;
+        const long long batch = (long long)ncols * c.nz;
+        // D_o[a][i] = sum_b M(a, b) in_o[b][i]: A(a, b) = M(a, b), B(i, b) = in_o[b][i]
+        for (long long z0 = 0; z0 < batch; z0 += 65535) {
+            const int nb = (int)std::min<long long>(65535, batch - z0);
+            tc_gemm_batched(Q, ma, mb, 0, in + z0 * slab, 1, c.nx, slab, n, c.nx, n, out + z0 * slab, c.nx, 1, slab,
+                            nb, scale, c.nd, s, c.d_tc_err);
+        }
+    } else {
+        const long long plane = (long long)c.nx * c.ny;
+        if (plane > (long long)INT32_MAX) fail(RPA_ERR_INVALID, "plane too large for the tensor-core transform");
+        if (ncols > 65535) fail(RPA_ERR_INVALID, "too many columns for the tensor-core transform");
+        tc_gemm_batched(Q, ma, mb, 0, in, 1, plane, c.nd, n, (int)plane, n, out, plane, 1, c.nd, ncols, scale, c.nd, s,
+                        c.d_tc_err);
+    }
+}
+
+static void coulomb_passes_tc(Ctx &c, double power, const double *in, double *out, int ncols, double *t1, double *t2,
+                              double *sc, cudaStream_t s) {
+    k_scale_grid<<<(unsigned)((c.nd + 255) / 256), 256, 0, s>>>(c.lam, sc, c.nd, power);
+    RPA_LAUNCH("coulomb scale");
+    count_launches(1);
+    axis_pass_tc(c, 0, in, t1, ncols, 1, nullptr, s);
+    axis_pass_tc(c, 1, t1, t2, ncols, 1, nullptr, s);
+    axis_pass_tc(c, 2, t2, t1, ncols, 1, sc, s);
+    axis_pass_tc(c, 2, t1, t2, ncols, 0, nullptr, s);
+    axis_pass_tc(c, 1, t2, t1, ncols, 0, nullptr, s);
+    axis_pass_tc(c, 0, t1, out, ncols, 0, nullptr, s);
+}
 
 static void coulomb_passes(Ctx &c, double power, const double *in, double *out, int ncols, double *t1, double *t2,
                            double *sc, cudaStream_t s) {
@@ -210,12 +258,15 @@ void coulomb_apply_noalloc(Ctx &c, double power, const double *in, double *out, 
     coulomb_passes(c, power, in, out, ncols, t1, t2, sc, s);
 }
 
-void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s) {
+void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s, bool tensor) {
     if (ncols <= 0) return;
     const size_t blk = sizeof(double) * (size_t)ncols * c.nd;
     char *base = (char *)c.coul_tmp.ensure(2 * blk + sizeof(double) * c.nd);
     double *t1 = (double *)base, *t2 = (double *)(base + blk), *sc = (double *)(base + 2 * blk);
-    coulomb_passes(c, power, in, out, ncols, t1, t2, sc, s);
+    if (tensor)
+        coulomb_passes_tc(c, power, in, out, ncols, t1, t2, sc, s);
+    else
+        coulomb_passes(c, power, in, out, ncols, t1, t2, sc, s);
 }
 
 }  // namespace rpa

@@ -414,7 +414,7 @@ void gram(const double *A, int na, const double *B, int nb, long long len, doubl
 
 void combine_rows(const double *S, int nc, int nk, const double *X, long long len, double *Y, cudaStream_t s) {
     const size_t sh = sizeof(double) * 16 * nk;
-    if (sh > 48 * 1024) RPA_CUDA(cudaFuncSetAttribute(k_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    allow_dynamic_smem((const void *)k_combine, sh);
     k_combine<<<dim3(std::min<unsigned>(cdiv(len, 256), 2048u), cdiv(nc, 16)), 256, sh, s>>>(S, nc, nk, X, len, Y);
     RPA_LAUNCH("combine_rows");
     count_launches(1);
@@ -440,7 +440,7 @@ void symmetrize(double *C, int n, cudaStream_t s) {
 
 void sq_trace(const double *C, int n, int n_o, double *part, double weight, double *e_out, cudaStream_t s) {
     const size_t sh = sizeof(double) * 3 * (size_t)n;
-    if (sh > 48 * 1024) RPA_CUDA(cudaFuncSetAttribute(k_sq_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    allow_dynamic_smem((const void *)k_sq_trace, sh);
     k_sq_trace<<<n, kSqThreads, sh, s>>>(C, n, n_o, part);
     k_sq_sum<<<1, 1, 0, s>>>(part, n, weight, e_out);
     RPA_LAUNCH("sq_trace");
@@ -450,8 +450,7 @@ void sq_trace(const double *C, int n, int n_o, double *part, double weight, doub
 void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out, cudaStream_t s) {
     const size_t sh = sizeof(double) * ((size_t)n * n + 3 * (size_t)n);
     const bool use_smem = sh <= 200 * 1024;
-    if (use_smem && sh > 48 * 1024)
-        RPA_CUDA(cudaFuncSetAttribute(k_sym_eigvals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    if (use_smem) allow_dynamic_smem((const void *)k_sym_eigvals, sh);
     k_sym_eigvals<<<1, kEigThreads, use_smem ? sh : 0, s>>>(C, n, lam, work, weight, e_out, use_smem ? 1 : 0);
     RPA_LAUNCH("sym_eigvals");
     count_launches(1);

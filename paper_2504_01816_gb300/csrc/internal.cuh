@@ -27,6 +27,11 @@ struct Error {
 
 [[noreturn]] void fail(rpa_status st, const char *fmt, ...);
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum (once; the value never
+// depends on the call, so contexts on different threads cannot lower each other's limit between
+// setting it and launching) and fail with RPA_ERR_INVALID if `need` bytes exceed that maximum.
+void allow_dynamic_smem(const void *kernel, size_t need);
+
 // Kernel launches issued by the library on this thread (reported in rpa_stats.launches).
 extern thread_local long long g_launches;
 inline void count_launches(long long n) { g_launches += n; }
@@ -110,7 +115,7 @@ struct Ctx {
     SysState *h_state = nullptr;  // pinned host mirror of the slot states
     size_t h_state_cap = 0;
     int *h_count = nullptr;       // pinned host counter
-    int *d_count = nullptr;
+    int *d_tc_err = nullptr;      // set by a tensor-core contraction that gave up waiting on its MMAs
 
     // per-call statistics
     rpa_stats stats{};
@@ -129,7 +134,14 @@ struct Ctx {
 // Operations (each enqueues work on `stream`)
 // ------------------------------------------------------------------------------------------
 // Kronecker Coulomb operator nu^power on ncols columns.
-void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s);
+void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s,
+                   bool tensor = false);
+// Whether the dense contractions of this context run on the tensor cores (rpa_options.contractions).
+inline bool use_tensor_cores(const Ctx &c) {
+    return c.opt.contractions == 2 || (c.opt.contractions == 0 && c.opt.prec == RPA_MIXED);
+}
+// Fails with RPA_ERR_CUDA if a tensor-core contraction reported a timed-out wait (synchronises s).
+void check_tensor_core_status(Ctx &c, cudaStream_t s);
 void coulomb_setup(Ctx &c);
 // Same operator with its scratch in the library's fixed device array (no allocation).
 void coulomb_apply_noalloc(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s);
@@ -152,6 +164,10 @@ int response_square(Ctx &c, double omega, const double *dv, const double *coef, 
 // Host symmetric eigendecomposition (cyclic Jacobi): A = Q diag(w) Q^T, Q[i*n+a] = component i of
 // eigenvector a; w ascending is not guaranteed.
 void jacobi_eigh(std::vector<double> A, int n, std::vector<double> &w, std::vector<double> &Q);
+
+// Whether the fused single-pass COCG kernel applies to this context's grid (a whole xy plane fits
+// its shared-memory ring); the mixed form then uses it by default.
+bool fused_kernel_applies(const Ctx &c);
 
 // Same as sternheimer_batch, with b replaced by P_c b first.
 int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
@@ -176,6 +192,18 @@ void sq_trace(const double *C, int n, int n_o, double *part, double weight, doub
 void sym_eigvals(double *C, int n, double *lam, double *work, double weight, double *e_out,
                  cudaStream_t s);
 void symmetrize(double *C, int n, cudaStream_t s);
+
+// D (M x N, row-major) = sum_k A(m, k) B(n, k) with A(m, k) = A[m a_m + k a_k] and B(n, k) =
+// B[n b_n + k b_k], on the tensor cores (tcgen05) as six products of BF16 splits accumulated in
+// FP32 (tc_gemm.cu).  *err_dev is set to 1 if the kernel gave up waiting on its MMAs.
+void tc_gemm(const double *A, long long a_m, long long a_k, const double *B, long long b_n, long long b_k, int M,
+             int N, long long K, double *D, cudaStream_t s, DevBuf &scratch, int *err_dev);
+// Batched form: for z < batch, D_z[m d_m + n d_n] = sum_k A_z(m, k) B_z(n, k), with the operands and
+// the output of member z offset by z a_z, z b_z, z d_z elements; optionally every output element e
+// (counted from D) is multiplied by scale[e % scale_n].
+void tc_gemm_batched(const double *A, long long a_m, long long a_k, long long a_z, const double *B, long long b_n,
+                     long long b_k, long long b_z, int M, int N, int K, double *D, long long d_m, long long d_n,
+                     long long d_z, int batch, const double *scale, long long scale_n, cudaStream_t s, int *err_dev);
 
 // Profiling helpers: register a kernel name in the stats table (returns its slot) and add
 // launches/time/points/bytes to it.

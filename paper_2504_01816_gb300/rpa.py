@@ -41,7 +41,8 @@ class rpa_options(ctypes.Structure):
                 ("fixed_subspace_iters", ctypes.c_int), ("n_atoms", ctypes.c_int),
                 ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int), ("project_solution", ctypes.c_int),
                 ("z_chunks", ctypes.c_int), ("stencil_shape", ctypes.c_int),
-                ("independent_frequencies", ctypes.c_int), ("sq_order", ctypes.c_int)]
+                ("independent_frequencies", ctypes.c_int), ("sq_order", ctypes.c_int),
+                ("contractions", ctypes.c_int)]
 
 
 PROF_SLOTS = 8
@@ -171,6 +172,7 @@ class Options:
     stencil_shape: int = 0
     independent_frequencies: int = 0
     sq_order: int = 0
+    contractions: int = 0
 
     def to_c(self) -> rpa_options:
         o = rpa_options()
@@ -288,22 +290,24 @@ class Context:
         _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
         return EcResult(float(ec[0]), float(ec[1]), ecm, lam, st, stats_dict(stats, nw))
 
-    AUTOTUNE_CANDIDATES = [f"stencil {shape}, {z} z chunk(s)"
+    AUTOTUNE_CANDIDATES = [f"split kernels, {shape}, {z} z chunk(s)"
                            for shape in ("1 column/thread <= 640 threads", "1 column/thread <= 320 threads x 2 blocks",
-                                         "2 columns/thread <= 384 threads") for z in (1, 2)]
+                                         "2 columns/thread <= 384 threads") for z in (1, 2)] + \
+                          ["fused single-pass kernel, whole planes in a shared-memory ring"]
 
     def autotune(self, omega: float, V, stream=None):
         """rpa_autotune: time the COCG kernel configurations on this workload, keep the fastest.
-        Returns (chosen index, candidate descriptions, times in ms)."""
+        Returns (chosen index, candidate descriptions, times in ms; -1 = not applicable)."""
         n_r = V.shape[0]
         _dev64(V, (n_r, self.n_d))
         chosen = ctypes.c_int(0)
-        times = (ctypes.c_double * 6)()
+        times = (ctypes.c_double * len(self.AUTOTUNE_CANDIDATES))()
         _check(_lib.rpa_autotune(self._h, float(omega), _ptr(V), n_r, ctypes.byref(chosen), times, _stream(stream)))
         # the autotuner sets stencil_shape and z_chunks; keep the Python-side options in step
-        self.options.stencil_shape = chosen.value // 2
-        self.options.z_chunks = chosen.value % 2 + 1
-        return chosen.value, self.AUTOTUNE_CANDIDATES, list(times)
+        i = chosen.value
+        self.options.stencil_shape = 4 if i == 6 else i // 2 + 1
+        self.options.z_chunks = 1 if i == 6 else i % 2 + 1
+        return i, self.AUTOTUNE_CANDIDATES, list(times)
 
     def ec_gradient(self, V0, want_subspace: bool = False, stream=None):
         """E_c and dE_c/dV_loc (N_d, float64 CUDA tensor) at fixed orbitals (rpa_ec_gradient);

@@ -44,6 +44,7 @@ def options(rpa, s):
     o.n_omega = 2
     o.fixed_subspace_iters = 1
     o.n_atoms = s.n_atoms
+    o.contractions = 1      # FP64 contractions: the oracle check below is held to 1e-7
     return o
 
 

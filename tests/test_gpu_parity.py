@@ -5,8 +5,17 @@ two solvers that both meet tol differ in x by at most ~2 tol cond(A), and chi0 i
 that bound through a sum of N_s solves.  The tests use tol = 1e-11..1e-12 so that the
 parity bound (1e-8 relative) is far above the solver error and far below any real
 mistake.  The mixed form reaches the same FP64 residual tolerance through refinement, so
-it is held to the same bounds.  Ritz values and energies are compared in absolute terms:
-1e-8 (FP64) and 1e-7 (mixed) for lambda_i, which the method's own target (1e-6) exceeds.
+it is held to the same bounds when its dense contractions run in FP64 (contractions = 1,
+which these tests pin).  Ritz values and energies are compared in absolute terms: 1e-8
+(FP64) and 1e-7 (mixed) for lambda_i, which the method's own target (1e-6) exceeds.
+
+Tensor-core contractions (contractions = 2, the mixed form's default) carry the error of
+their BF16 splits: six products of 8-bit pieces keep ~24 significant bits per product, and
+FP32 accumulation over k chunks of 64 adds ~4e-7 of a chunk's sum at worst, so each
+contraction is good to ~1e-6 of the norms it combines.  test_tensor_core_* compare them with
+the FP64 contractions (same COCG) at 1e-5 relative on R = nu^1/2 chi0 nu^1/2 V (six
+Kronecker transforms and the P_c coefficients in series) and with the oracle at the
+method's own target: every lambda_i within 1e-6, E_c within 1e-6 Ha per atom.
 """
 import math
 
@@ -158,7 +167,7 @@ def test_apply_nuchi0_matches_oracle(rpa, prec, tiny):
     V = synth.random_block(8, 6, s.n_d)
     tol = 1e-11
     p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
-    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=p)) as ctx:
+    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=p, contractions=1)) as ctx:
         for omega in (0.05, 1.7):
             R, code = ctx.apply_nuchi0(omega, cuda(V), symmetric=True)
             assert code == rpa.RPA_OK
@@ -180,34 +189,40 @@ def test_apply_nuchi0_small_batches_agree(rpa, ragged):
 
 @pytest.mark.parametrize("zc", [2, 3, 5])
 def test_z_chunked_stencil_items_agree(rpa, zc):
-    """Stencil work items split along z (with a 6-plane overlap) give the same result."""
+    """Stencil work items of the two-kernel form split along z (with a 6-plane overlap) give the
+    same result, and so does the fused kernel (which always marches whole columns)."""
     s = synth.small_system((13, 11, 17), h=0.5, n_s=3, n_wells=3, seed=33)
     V = synth.random_block(12, 5, s.n_d)
-    with rpa.Context.from_system(s, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED)) as ctx:
+    o = dict(tol=1e-12, prec=rpa.RPA_MIXED, contractions=1)
+    with rpa.Context.from_system(s, opts(rpa, stencil_shape=1, **o)) as ctx:
         Ra, _ = ctx.apply_nuchi0(0.6, cuda(V))
-        ctx.set_options(opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, z_chunks=zc, batch_systems=4))
+        ctx.set_options(opts(rpa, stencil_shape=1, z_chunks=zc, batch_systems=4, **o))
         Rb, _ = ctx.apply_nuchi0(0.6, cuda(V))
+        ctx.set_options(opts(rpa, stencil_shape=4, batch_systems=4, **o))
+        Rc, _ = ctx.apply_nuchi0(0.6, cuda(V))
     assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
+    assert relerr(Rc.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
 
 
-@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("shape", [2, 3, 4])
 def test_stencil_block_shapes_agree(rpa, shape):
-    """The stencil kernel's block-shape variants (other xy tiles, more blocks per SM)."""
+    """The stencil kernel's block-shape variants (other xy tiles, more blocks per SM) on a grid
+    whose planes are too large for the fused kernel (shape 4 then runs variant 1)."""
     s = synth.small_system((70, 31, 9), h=0.5, n_s=2, n_wells=3, seed=17)
     V = synth.random_block(13, 3, s.n_d)
-    with rpa.Context.from_system(s, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED)) as ctx:
+    with rpa.Context.from_system(s, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, contractions=1)) as ctx:
         Ra, _ = ctx.apply_nuchi0(0.7, cuda(V))
-        ctx.set_options(opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, stencil_shape=shape))
+        ctx.set_options(opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, stencil_shape=shape, contractions=1))
         Rb, _ = ctx.apply_nuchi0(0.7, cuda(V))
     assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
 
 
 def test_autotune_keeps_results(rpa, ragged):
     V = synth.random_block(14, 4, ragged.n_d)
-    with rpa.Context.from_system(ragged, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED)) as ctx:
+    with rpa.Context.from_system(ragged, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, contractions=1)) as ctx:
         Ra, _ = ctx.apply_nuchi0(0.5, cuda(V))
         chosen, names, times = ctx.autotune(0.5, cuda(V))
-        assert 0 <= chosen < 6 and all(t > 0 for t in times)
+        assert 0 <= chosen < 7 and all(t > 0 for t in times)   # the fused kernel applies on 13 x 11 planes
         Rb, _ = ctx.apply_nuchi0(0.5, cuda(V))
     assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
 
@@ -227,7 +242,7 @@ def test_ec_matches_oracle_fixed_iterations(rpa, prec, tiny):
     n_r, n_omega, iters, tol = 8, 4, 3, 1e-10
     V0 = synth.trial_vectors(0, n_r, s.n_d)
     p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
-    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms)
+    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms, contractions=1)
     with rpa.Context.from_system(s, o) as ctx:
         res = ctx.ec(cuda(V0))
     ref = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, n_omega, tol=tol, eps_c=0.0, fixed_iters=iters)
@@ -273,13 +288,13 @@ def test_mixed40_sampled_columns_match_oracle(rpa):
     s = w.system
     V = synth.trial_vectors(w.seed, w.n_r, s.n_d)
     omega = oracle.frequency_quadrature(w.n_omega)[0][2]
-    with rpa.Context.from_system(s, opts(rpa, prec=rpa.RPA_MIXED, tol=1e-10)) as ctx:
+    with rpa.Context.from_system(s, opts(rpa, prec=rpa.RPA_MIXED, tol=1e-10)) as ctx:   # tensor-core contractions
         R, code = ctx.apply_nuchi0(omega, cuda(V))
     assert code == rpa.RPA_OK
     R = R.cpu().numpy()
     cols = [0, 37]
     ref = oracle.Oracle.from_system(s).chi_tilde(V[cols], omega, 1e-10)
-    assert relerr(R[cols], ref) < 1e-7
+    assert relerr(R[cols], ref) < 1e-5
 
 
 @pytest.mark.slow
@@ -292,19 +307,21 @@ def test_lih72_sampled_column_matches_oracle(rpa):
     assert s.n_s == 64 and s.n_atoms == 64
     V = synth.trial_vectors(w.seed, 2, s.n_d)
     omega = oracle.frequency_quadrature(w.n_omega)[0][5]
-    with rpa.Context.from_system(s, opts(rpa, prec=rpa.RPA_MIXED, tol=1e-9)) as ctx:
+    with rpa.Context.from_system(s, opts(rpa, prec=rpa.RPA_MIXED, tol=1e-9)) as ctx:   # tensor-core contractions
         R, code = ctx.apply_nuchi0(omega, cuda(V))
     assert code == rpa.RPA_OK
     ref = oracle.Oracle.from_system(s).chi_tilde(V[:1], omega, 1e-9)
-    assert relerr(R.cpu().numpy()[:1], ref) < 1e-6
+    assert relerr(R.cpu().numpy()[:1], ref) < 1e-5
 
 
-@pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11)])
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11), (16, 5, 4)])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
 def test_stencil_variants_match_oracle(rpa, shape, grid):
     """(70, 3, 9): two x tiles with side halos and more halo elements per plane than twice the
-    block's threads (the kernels' fallback halo loop); (15, 13, 11): an odd nx, where the
-    two-column kernel holds a column past the box at zero."""
+    block's threads (the split kernels' fallback halo loop), and rows of 35 point pairs in the
+    fused kernel; (15, 13, 11): an odd nx, where the two-column kernels hold a point past the box
+    at zero; (16, 5, 4): fewer planes than the stencil's reach (nz < 6), even nx (16-byte pair
+    loads in the fused kernel)."""
     s = synth.small_system(grid, h=0.5, n_s=2, n_wells=2, seed=29)
     g = oracle.Grid(s.nx, s.ny, s.nz, s.h)
     rng = np.random.default_rng(8)
@@ -328,13 +345,15 @@ def test_ec_by_gauss_spectral_quadrature_matches_oracle(rpa, prec, tiny):
     n_r, n_omega, iters, tol = 8, 3, 2, 1e-10
     V0 = synth.trial_vectors(0, n_r, s.n_d)
     p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
-    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms, sq_order=3)
+    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms, sq_order=3,
+             contractions=1)
     with rpa.Context.from_system(s, o) as ctx:
         res3 = ctx.ec(cuda(V0))
         ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters,
-                             n_atoms=s.n_atoms, sq_order=n_r))
+                             n_atoms=s.n_atoms, sq_order=n_r, contractions=1))
         resn = ctx.ec(cuda(V0))
-        ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms))
+        ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms,
+                             contractions=1))
         rr = ctx.ec(cuda(V0))
         with pytest.raises(rpa.RpaError):
             ctx.set_options(opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters,
@@ -345,3 +364,37 @@ def test_ec_by_gauss_spectral_quadrature_matches_oracle(rpa, prec, tiny):
     assert np.max(np.abs(res3.e_c_per_omega - ref3.e_c_per_omega)) < 1e-8
     assert abs(res3.e_c - ref3.e_c) < 1e-8
     assert np.max(np.abs(resn.e_c_per_omega - rr.e_c_per_omega)) < 1e-11
+
+
+# ------------------------------------------------------------------------- tensor-core contractions
+@pytest.mark.parametrize("grid", [(15, 15, 15), (13, 11, 7), (150, 4, 3)])
+def test_tensor_core_contractions_match_fp64(rpa, grid):
+    """The chi0 application with its contractions (Kronecker transforms of nu^1/2 and the P_c
+    coefficients) on the tensor cores against the same with FP64 contractions: (150, 4, 3) has an
+    axis longer than the FP64 transform kernel's shared-memory limit would allow for 200+."""
+    s = synth.small_system(grid, h=0.5, n_s=2, n_wells=2, seed=41)
+    V = synth.random_block(15, 5, s.n_d)
+    with rpa.Context.from_system(s, opts(rpa, tol=1e-11, prec=rpa.RPA_MIXED, contractions=1)) as ctx:
+        Rf, code = ctx.apply_nuchi0(0.3, cuda(V))
+        assert code == rpa.RPA_OK
+        ctx.set_options(opts(rpa, tol=1e-11, prec=rpa.RPA_MIXED, contractions=2))
+        Rt, code = ctx.apply_nuchi0(0.3, cuda(V))
+        assert code == rpa.RPA_OK
+    err = relerr(Rt.cpu().numpy(), Rf.cpu().numpy())
+    assert 0 < err < 1e-5, err      # nonzero: the tensor-core path really ran
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tensor_core_ec_meets_the_method_target(rpa, prec, tiny):
+    """E_c and every Ritz value with tensor-core contractions (C = V^T R, P_c, nu^1/2) against the
+    oracle at the method's accuracy target: lambda_i within 1e-6, E_c within 1e-6 Ha per atom."""
+    s = tiny
+    n_r, n_omega, iters, tol = 8, 4, 3, 1e-10
+    V0 = synth.trial_vectors(0, n_r, s.n_d)
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    o = opts(rpa, tol=tol, prec=p, n_omega=n_omega, fixed_subspace_iters=iters, n_atoms=s.n_atoms, contractions=2)
+    with rpa.Context.from_system(s, o) as ctx:
+        res = ctx.ec(cuda(V0))
+    ref = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, n_omega, tol=tol, eps_c=0.0, fixed_iters=iters)
+    assert np.max(np.abs(res.lambdas - ref.lambdas)) < 1e-6
+    assert abs(res.e_c_per_atom - ref.e_c / s.n_atoms) < 1e-6
