@@ -127,7 +127,7 @@ void validate_options(const rpa_options &o) {
     if (o.z_chunks < 0 || o.z_chunks > 64) fail(RPA_ERR_INVALID, "z_chunks must be in [0, 64]");
     if (o.stencil_shape < 0 || o.stencil_shape > 4) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 4]");
     if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
-    if (o.contractions < 0 || o.contractions > 2) fail(RPA_ERR_INVALID, "contractions must be 0, 1 or 2");
+    if (o.contractions < 0 || o.contractions > 3) fail(RPA_ERR_INVALID, "contractions must be in [0, 3]");
 }
 
 // Gauss-Legendre nodes and weights on (-1, 1) by Newton iteration on P_n, then the map
@@ -203,7 +203,7 @@ int apply_nuchi0_impl(Ctx &c, double omega, const double *V, double *R, int ncol
     for (auto &x : e) RPA_CUDA(cudaEventCreate(&x));
     RPA_CUDA(cudaEventRecord(e[0], s));
     const double *dv = V;
-    const bool tc = use_tensor_cores(c);
+    const bool tc = use_tensor_cores_kronecker(c);
     if (symmetric) {
         coulomb_apply(c, 0.5, V, tmp1, ncols, s, tc);
         dv = tmp1;
@@ -217,7 +217,7 @@ int apply_nuchi0_impl(Ctx &c, double omega, const double *V, double *R, int ncol
     c.stats.ms_coulomb += ms_between(e[0], e[1]) + ms_between(e[2], e[3]);
     c.stats.ms_cocg += ms_between(e[1], e[2]);
     for (auto &x : e) cudaEventDestroy(x);
-    if (tc) check_tensor_core_status(c, s);
+    if (use_tensor_cores(c)) check_tensor_core_status(c, s);
     return worst;
 }
 

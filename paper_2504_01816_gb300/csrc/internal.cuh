@@ -136,8 +136,12 @@ struct Ctx {
 // Kronecker Coulomb operator nu^power on ncols columns.
 void coulomb_apply(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s,
                    bool tensor = false);
-// Whether the dense contractions of this context run on the tensor cores (rpa_options.contractions).
+// Whether the dense contractions of this context run on the tensor cores (rpa_options.contractions):
+// the P_c coefficients and C = V^T R, and the Kronecker transforms of nu^1/2.
 inline bool use_tensor_cores(const Ctx &c) {
+    return c.opt.contractions >= 2 || (c.opt.contractions == 0 && c.opt.prec == RPA_MIXED);
+}
+inline bool use_tensor_cores_kronecker(const Ctx &c) {
     return c.opt.contractions == 2 || (c.opt.contractions == 0 && c.opt.prec == RPA_MIXED);
 }
 // Fails with RPA_ERR_CUDA if a tensor-core contraction reported a timed-out wait (synchronises s).

@@ -2,30 +2,38 @@
 //
 //     D[m][n] = sum_k A(m, k) B(n, k),   A(m, k) = A[m * a_m + k * a_k],  B(n, k) = B[n * b_n + k * b_k]
 //
-// for FP64 operands, as products of BF16 splits accumulated in FP32.  Every operand value is
-// split as x = hi + mid + lo, hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid) (the
-// remainders are formed exactly), and the six products that reach the FP32 level,
-//     hi.hi + hi.mid + mid.hi + hi.lo + lo.hi + mid.mid,
-// are accumulated by tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator in tensor memory).
-// Each product of two BF16 numbers is exact in FP32, so a term carries ~24 significant bits.
+// for FP64 operands, as BF16 tensor-core products that are exact.  The scheme is the error-free
+// splitting of Ozaki, Ogita and Oishi (error-free transformation of matrix products into sums of
+// products of low-precision pieces) with per-chunk power-of-two scaling:
 //
-// Used for the projection C = V^T R of the Rayleigh-Ritz step (Algorithm 1) and the P_c
-// coefficients T_{k,(n,j)} = u_k . (u_n (.) nu^1/2 v_j) of the Sternheimer right-hand sides
-// (Eqs. 7-9) in the mixed-precision form; the plain FP64 form keeps the FP64 kernels.
+//   * k is walked in chunks of kTcK = 64.  Within a chunk every row m of A gets the power of two
+//     s_m = 2^(e_m + 1) above its largest |A(m, k)| (e_m its binary exponent), every row n of B
+//     likewise s_n, so that |A(m, k) / s_m| < 1.
+//   * x = A(m, k) / s_m * 2^7 is cut into four integer pieces of at most 8 bits,
+//       x = a1 + 2^-8 a2 + 2^-16 a3 + 2^-24 a4 + r,  |a_i| <= 128,  |r| < 2^-25,
+//     each exactly representable in BF16 (8 significant bits).  Same for B.
+//   * Products a_i b_j are integers below 2^14, so over one chunk (64 values of k) every partial
+//     sum the tensor core forms -- inside one MMA of 16 k values, or accumulated over the chunk's
+//     four MMAs -- is an integer below 2^24 and therefore exact in its FP32 accumulator, whatever
+//     the rounding of the hardware's additions.  The ten products of weight 2^0 .. 2^-24 go to four
+//     tensor-memory tiles by weight: L0 = a1.b1; L1 = a1.b2 + a2.b1; L2 = a1.b3 + a3.b1 + a2.b2;
+//     L3 = a1.b4 + a4.b1 + a2.b3 + a3.b2 (sums of up to 4 x 64 products: below 2^22).
+//   * After each chunk the tiles are read back (tcgen05.ld) and the chunk's contribution
+//     s_m s_n 2^-14 (L0 + 2^-8 L1 + 2^-16 L2 + 2^-24 L3) is added in FP64.
+// The only errors are the neglected pieces (weights 2^-32 and below, relative to s_m s_n) and the
+// FP64 additions: about 1e-9 of the chunk-row maxima, far below the FP32 level.
 //
-// Accumulation.  The tensor cores add the products of one MMA to the FP32 accumulator with a
-// relative error of up to ~2^-23 of the accumulator per instruction (measured: ~5e-6 relative
-// after a few hundred chained MMAs), so chains are kept short: the hi.hi products accumulate in
-// one tensor-memory tile and the five smaller cross products in a second, each over one k chunk
-// (4 and 20 MMAs), and after every chunk both tiles are read back and added in FP64 registers.
+// Used for the projection C = V^T R of the Rayleigh-Ritz step (Algorithm 1), the P_c coefficients
+// T_{k,(n,j)} = u_k . (u_n (.) nu^1/2 v_j) of the Sternheimer right-hand sides (Eqs. 7-9), and the
+// per-axis transforms of the Kronecker-product Coulomb operator (Eq. 5), in the mixed-precision form.
 //
 // Blocking.  A block computes one 128 x kTcN tile of D over one range of k (split-K, blockIdx.z) or
-// for one member of a batch (blockIdx.z with the batch strides); the range is walked in chunks of
-// kTcK.  Per chunk all threads read the FP64 operand tiles (coalesced along whichever index is
-// contiguous), split them and store the BF16 pieces into shared memory in the canonical K-major
-// layout without swizzle (8-row x 16-byte core matrices, 128 bytes each); one thread then issues
-// 4 (k slices of 16) x 6 (products) MMAs and commits them to an mbarrier, which every thread waits
-// on before the tiles are read back (tcgen05.ld) and the shared tiles rewritten.  The FP64 tile
+// for one member of a batch (blockIdx.z with the batch strides).  Per chunk all threads read the
+// FP64 operand tiles twice (coalesced along whichever index is contiguous): first for the row
+// exponents (shared-memory atomicMax), then to cut the pieces, which go to shared memory in the
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices, 128 bytes each).  One
+// thread issues 4 (k slices of 16) x 10 (products) MMAs and commits them to an mbarrier, which every
+// thread waits on before the tiles are read back and the shared tiles rewritten.  The FP64 tile
 // goes to the output (batched) or to a split-K partial; a second kernel adds the partials in a
 // fixed order (deterministic).
 //
@@ -46,13 +54,14 @@ constexpr int kTcM = 128;                // tile rows (MMA M)
 constexpr int kTcN = 64;                 // tile columns (MMA N)
 constexpr int kTcK = 64;                 // k chunk staged per round
 constexpr int kTcThreads = 256;
-constexpr int kTcSplits = 3;             // hi, mid, lo
+constexpr int kTcPieces = 4;             // integer pieces per operand value
+constexpr int kTcLevels = 4;             // product weights 2^0, 2^-8, 2^-16, 2^-24
 constexpr uint32_t kTcCoreBytes = 128;   // one 8 x 16-byte core matrix
 constexpr uint32_t kTcSbo = (kTcK / 8) * kTcCoreBytes;            // next 8-row group
 constexpr uint32_t kTcLbo = kTcCoreBytes;                         // next 8 k values
 constexpr uint32_t kTcTileA = kTcM * kTcK * 2;                    // bytes of one BF16 A tile
 constexpr uint32_t kTcTileB = kTcN * kTcK * 2;
-constexpr uint32_t kTcSmem = kTcSplits * (kTcTileA + kTcTileB) + 64;
+constexpr uint32_t kTcSmem = kTcPieces * (kTcTileA + kTcTileB) + 64;
 constexpr long long kTcWaitCycles = 2000000000LL;                 // ~1 s at 2 GHz
 
 struct TcArgs {
@@ -95,14 +104,27 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k) {
            (uint32_t)(k & 7) * 2u;
 }
 
-__device__ __forceinline__ void split3(double x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
-    const float f = (float)x;                       // x = f + e exactly enough (e below 2^-48 |x|)
-    const float e = (float)(x - (double)f);
-    h = __float2bfloat16_rn(f);
-    const float r1 = f - __bfloat162float(h);       // exact
-    m = __float2bfloat16_rn(r1);
-    const float r2 = (r1 - __bfloat162float(m)) + e;
-    l = __float2bfloat16_rn(r2);
+// Biased binary exponent field of |x| (0 for zero).
+__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+
+// x / 2^(e - 1022) * 2^7 (|result| < 128 when e is the exponent field of a value >= |x|) as four
+// integer pieces of at most 8 bits (exact BF16 values): x = a1 + a2 2^-8 + a3 2^-16 + a4 2^-24 + r.
+__device__ __forceinline__ void cut4(double x, int e, __nv_bfloat16 (&p)[4]) {
+    // power of two 2^(1029 - e), exact; a row of zeros (e = 0) gives zero pieces
+    const double t = e > 0 ? x * __hiloint2double((2052 - e) << 20, 0) : 0.0;
+    const float hi = (float)t;
+    const float lo = (float)(t - (double)hi);       // t = hi + lo to ~2^-48 |t|
+    const float a1 = rintf(hi);
+    float u = (hi - a1) * 256.f + lo * 256.f;       // hi - a1 exact; |u| <= 128
+    const float a2 = rintf(u);
+    u = (u - a2) * 256.f;                           // exact
+    const float a3 = rintf(u);
+    u = (u - a3) * 256.f;
+    const float a4 = rintf(u);
+    p[0] = __float2bfloat16_rn(a1);
+    p[1] = __float2bfloat16_rn(a2);
+    p[2] = __float2bfloat16_rn(a3);
+    p[3] = __float2bfloat16_rn(a4);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -119,13 +141,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char *tA = tsm;                                       // [3][kTcTileA]
-    unsigned char *tB = tsm + kTcSplits * kTcTileA;                // [3][kTcTileB]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tsm + kTcSplits * (kTcTileA + kTcTileB));
+    unsigned char *tA = tsm;                                       // [4][kTcTileA]
+    unsigned char *tB = tsm + kTcPieces * kTcTileA;                // [4][kTcTileB]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tsm + kTcPieces * (kTcTileA + kTcTileB));
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     __shared__ int abort_flag;
+    __shared__ int expA[kTcM], expB[kTcN];                         // row exponents of the chunk
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * kTcN;
     const bool batch = a.a_z != 0 || a.b_z != 0 || a.d_z != 0;
@@ -134,7 +164,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
     const long long k0 = batch ? 0 : (long long)blockIdx.z * a.kchunk;
     const long long k1 = min(a.K, k0 + a.kchunk);
     const uint32_t bar_addr = smem_u32(bar);
-    constexpr uint32_t kCols = 2 * kTcN;                          // hi.hi tile, cross-product tile
+    constexpr uint32_t kCols = kTcLevels * kTcN;                  // one accumulator tile per weight
 
     if (tid == 0) {
         abort_flag = 0;
@@ -155,8 +185,8 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
     // epilogue mapping: warp w reads tile rows 32 (w % 4) .. +31 (its tensor-memory lanes) and
     // columns 32 (w / 4) .. +31
     const int lane_base = 32 * (warp & 3), col0 = 32 * (warp >> 2);
-    const uint32_t t_hh = tmem + ((uint32_t)lane_base << 16) + (uint32_t)col0;
-    const uint32_t t_x = t_hh + kTcN;
+    const int my_row = lane_base + (tid & 31);
+    const uint32_t t_base = tmem + ((uint32_t)lane_base << 16) + (uint32_t)col0;
     double acc[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = 0.0;
@@ -164,19 +194,37 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
     uint32_t phase = 0;
     bool ok = true, pending = false;
     for (long long kb = k0; kb < k1; kb += kTcK) {
-        // operand tiles: FP64 -> three BF16 pieces, K-major core matrices
+        // 1. row exponents of the chunk
+        for (int e = tid; e < kTcM; e += kTcThreads) expA[e] = 0;
+        for (int e = tid; e < kTcN; e += kTcThreads) expB[e] = 0;
+        __syncthreads();
+        for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
+            const int row = a_kfast ? e / kTcK : e % kTcM;
+            const int kk = a_kfast ? e % kTcK : e / kTcM;
+            const int m = m0 + row;
+            const long long k = kb + kk;
+            if (m < a.M && k < k1) atomicMax(&expA[row], exp_field(Ab[(long long)m * a.a_m + k * a.a_k]));
+        }
+        for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
+            const int row = b_kfast ? e / kTcK : e % kTcN;
+            const int kk = b_kfast ? e % kTcK : e / kTcN;
+            const int n = n0 + row;
+            const long long k = kb + kk;
+            if (n < a.N && k < k1) atomicMax(&expB[row], exp_field(Bb[(long long)n * a.b_n + k * a.b_k]));
+        }
+        __syncthreads();
+        // 2. integer pieces into the K-major core-matrix tiles
         for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
             const int row = a_kfast ? e / kTcK : e % kTcM;
             const int kk = a_kfast ? e % kTcK : e / kTcM;
             const int m = m0 + row;
             const long long k = kb + kk;
             const double x = (m < a.M && k < k1) ? Ab[(long long)m * a.a_m + k * a.a_k] : 0.0;
-            __nv_bfloat16 h, md, l;
-            split3(x, h, md, l);
+            __nv_bfloat16 pc[4];
+            cut4(x, expA[row], pc);
             const uint32_t o = tc_off(row, kk);
-            *reinterpret_cast<__nv_bfloat16 *>(tA + o) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(tA + kTcTileA + o) = md;
-            *reinterpret_cast<__nv_bfloat16 *>(tA + 2 * kTcTileA + o) = l;
+#pragma unroll
+            for (int i = 0; i < kTcPieces; ++i) *reinterpret_cast<__nv_bfloat16 *>(tA + i * kTcTileA + o) = pc[i];
         }
         for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
             const int row = b_kfast ? e / kTcK : e % kTcN;
@@ -184,12 +232,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
             const int n = n0 + row;
             const long long k = kb + kk;
             const double x = (n < a.N && k < k1) ? Bb[(long long)n * a.b_n + k * a.b_k] : 0.0;
-            __nv_bfloat16 h, md, l;
-            split3(x, h, md, l);
+            __nv_bfloat16 pc[4];
+            cut4(x, expB[row], pc);
             const uint32_t o = tc_off(row, kk);
-            *reinterpret_cast<__nv_bfloat16 *>(tB + o) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(tB + kTcTileB + o) = md;
-            *reinterpret_cast<__nv_bfloat16 *>(tB + 2 * kTcTileB + o) = l;
+#pragma unroll
+            for (int i = 0; i < kTcPieces; ++i) *reinterpret_cast<__nv_bfloat16 *>(tB + i * kTcTileB + o) = pc[i];
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy stores -> tensor core
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -197,16 +244,21 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             constexpr uint32_t idesc = tc_idesc(kTcM, kTcN);
-            // (A piece, B piece) of the six products; product 0 (hi.hi) goes to its own tile
-            const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+            // (A piece, B piece, weight level) of the ten products a_i b_j with i + j <= 5
+            constexpr int np = 10;
+            const int pa[np] = {0, 0, 1, 0, 2, 1, 0, 3, 1, 2};
+            const int pb[np] = {0, 1, 0, 2, 0, 1, 3, 0, 2, 1};
+            const int lv[np] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 #pragma unroll
             for (int t = 0; t < kTcK / 16; ++t)
 #pragma unroll
-                for (int pr = 0; pr < 6; ++pr) {
+                for (int pr = 0; pr < np; ++pr) {
                     const uint64_t da = tc_desc(smem_u32(tA + pa[pr] * kTcTileA) + t * 2 * kTcCoreBytes);
                     const uint64_t db = tc_desc(smem_u32(tB + pb[pr] * kTcTileB) + t * 2 * kTcCoreBytes);
-                    const uint32_t d = pr == 0 ? tmem : tmem + kTcN;
-                    const uint32_t accum = (t > 0 || pr > 1) ? 1u : 0u;     // each chunk starts both tiles afresh
+                    const uint32_t d = tmem + (uint32_t)(lv[pr] * kTcN);
+                    // each chunk starts every level's tile afresh with its first product
+                    const bool first = t == 0 && (pr == 0 || pr == 1 || pr == 3 || pr == 6);
+                    const uint32_t accum = first ? 0u : 1u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
@@ -226,44 +278,43 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
         if (abort_flag) break;
         pending = false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // read both tiles back (16 columns at a time) and add them in FP64
+        // 3. read the four weight tiles back (8 columns at a time) and add the chunk in FP64
+        const int ea = expA[my_row];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t r[16], x[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(t_hh + 16 * h)
-                : "memory");
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
-                : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]),
-                  "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]), "=r"(x[15])
-                : "r"(t_x + 16 * h)
-                : "memory");
+        for (int h = 0; h < 4; ++h) {
+            uint32_t l0[8], l1[8], l2[8], l3[8];
+            tmem_ld8(t_base + 8 * h, l0);
+            tmem_ld8(t_base + kTcN + 8 * h, l1);
+            tmem_ld8(t_base + 2 * kTcN + 8 * h, l2);
+            tmem_ld8(t_base + 3 * kTcN + 8 * h, l3);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                acc[16 * h + c] += (double)__uint_as_float(r[c]) + (double)__uint_as_float(x[c]);
+            for (int c = 0; c < 8; ++c) {
+                const int eb = expB[col0 + 8 * h + c];
+                // s_m s_n 2^-14 = 2^(ea - 1022 + eb - 1022 - 14); zero rows have exponent field 0
+                const double sc = (ea == 0 || eb == 0) ? 0.0 : __hiloint2double((ea + eb - 2058 + 1023) << 20, 0);
+                const double v = (((double)__uint_as_float(l3[c]) * 0.00390625 + (double)__uint_as_float(l2[c])) *
+                                      0.00390625 +
+                                  (double)__uint_as_float(l1[c])) *
+                                     0.00390625 +
+                                 (double)__uint_as_float(l0[c]);
+                acc[8 * h + c] += sc * v;
+            }
         }
-        // the next chunk's MMAs rewrite tensor memory and its loads the shared tiles
+        // the next chunk's MMAs rewrite tensor memory and its loads the shared tiles and exponents
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
     if (ok && !abort_flag) {
-        const int m = m0 + lane_base + (tid & 31);
+        const int m = m0 + my_row;
         if (m < a.M) {
             if (batch) {
-                double *out = a.part + (long long)blockIdx.z * a.d_z + (long long)m * a.d_m;
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
                     const int n = n0 + col0 + c;
                     if (n < a.N) {
                         const long long off = (long long)blockIdx.z * a.d_z + (long long)m * a.d_m + (long long)n * a.d_n;
-                        out[(long long)n * a.d_n] = a.scale ? acc[c] * a.scale[off % a.scale_n] : acc[c];
+                        a.part[off] = a.scale ? acc[c] * a.scale[off % a.scale_n] : acc[c];
                     }
                 }
             } else {
