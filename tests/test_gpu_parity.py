@@ -298,6 +298,29 @@ def test_mixed40_sampled_columns_match_oracle(rpa):
 
 
 @pytest.mark.slow
+def test_mixed40_ritz_values_and_energy_match_oracle(rpa):
+    """40^3 benchmark system, mixed form at its defaults (tensor-core contractions, fused COCG
+    kernel), one subspace iteration at one frequency: every Ritz value lambda_i and E_c,m against
+    the oracle (the same iteration: 16 x 64 = 1024 Sternheimer solves on the host), at the
+    method's stated targets -- lambda_i within 1e-6, E_c within 1e-5 Ha per atom -- and at the
+    tighter bounds that the FP64 refinement to tol 1e-10 supports (1e-7 and 1e-8 Ha per atom)."""
+    w = synth.workload("mixed40")
+    s = w.system
+    V0 = synth.trial_vectors(w.seed, w.n_r, s.n_d)
+    tol = 1e-10
+    o = opts(rpa, prec=rpa.RPA_MIXED, tol=tol, n_omega=1, fixed_subspace_iters=1, n_atoms=s.n_atoms)
+    with rpa.Context.from_system(s, o) as ctx:
+        res = ctx.ec(cuda(V0))
+    assert res.status == rpa.RPA_OK
+    ref = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, 1, tol=tol, eps_c=0.0, fixed_iters=1)
+    dlam = np.max(np.abs(res.lambdas - ref.lambdas))
+    dec = abs(res.e_c - ref.e_c) / s.n_atoms
+    print(f"mixed40: max |d lambda| = {dlam:.2e}, |d E_c| = {dec:.2e} Ha/atom")
+    assert dlam < 1e-6 and dec < 1e-5              # the method's targets
+    assert dlam < 1e-7 and dec < 1e-8
+
+
+@pytest.mark.slow
 def test_lih72_sampled_column_matches_oracle(rpa):
     """LiH-shaped 72^3 cell (h=0.3, 32 Li-like + 32 H-like wells, 64 orbitals): one column of
     nu^1/2 chi0 nu^1/2 V at one frequency in the mixed form against the oracle (64 Sternheimer
