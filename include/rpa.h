@@ -110,6 +110,14 @@ typedef struct {
                                   FP32 accumulation over k chunks of 64, chunk sums in FP64; ~1e-7
                                   relative).  The overlap R^T R, the rotation V = R L^-T, Cholesky,
                                   the eigensolve and rpa_coulomb_apply always use FP64. */
+    int omega_first;           /* frequency range of this call (ascending index into the n_omega   */
+    int omega_count;           /* Gauss-Legendre nodes): rpa_ec / rpa_ec_gradient evaluate only the
+                                  frequencies omega_first .. omega_first + omega_count - 1 (count 0 =
+                                  all) and report zero for the others (lambdas, ec_per_omega; E_c sums
+                                  only the range).  With independent_frequencies set, the ranges of a
+                                  partition of the frequencies give, summed, exactly the E_c of one
+                                  call over all of them: frequency sharding across processes (the
+                                  paper's frequencies are independent but for the warm start). */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8
@@ -146,7 +154,7 @@ typedef struct {
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
  * profile 0, project_solution 0, z_chunks 0, stencil_shape 0 (automatic), independent_frequencies 0,
- * sq_order 0, contractions 0 (automatic). */
+ * sq_order 0, contractions 0 (automatic), omega_first 0, omega_count 0 (all frequencies). */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).

@@ -35,7 +35,7 @@ from __future__ import annotations
 import ctypes
 import math
 from dataclasses import dataclass, field
-from typing import List, Optional
+from typing import List, Optional, Sequence
 
 import numpy as np
 import scipy.linalg as sla
@@ -406,14 +406,17 @@ def gauss_sq_trace(C: np.ndarray, n_o: int, f) -> float:
 def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, omega0: float = 1.0,
            max_subspace_iters: int = 100, fixed_iters: Optional[int] = None, maxit: int = 100000,
            verbose: bool = False, project_solution: bool = False, keep_ritz: bool = False,
-           independent_frequencies: bool = False, sq_order: int = 0) -> EcResult:
+           independent_frequencies: bool = False, sq_order: int = 0,
+           omega_subset: Optional[Sequence[int]] = None) -> EcResult:
     """E_c by Algorithm 1 with Rayleigh-Ritz: frequencies from highest to lowest, the subspace
     carried over from each frequency to the next; at each frequency iterate
     R = chi~0 V, C = V^T R, lambda = eig(C), E_cm = (w_m/2pi) sum g(lambda), M = R^T R = L L^T,
     V = R L^{-T} while |E_cm - E_cm_old| > eps_c * N_atoms / N_omega (eps_c in Ha/atom), at least
     two iterations (E_cm starts at 0).  fixed_iters runs exactly that many iterations instead.
     sq_order > 0 evaluates E_cm = (w_m/2pi) Tr g(C) by Gauss spectral quadrature of that order
-    (gauss_sq_trace), the paper's choice; lambda are still the Ritz values."""
+    (gauss_sq_trace), the paper's choice; lambda are still the Ritz values.
+    omega_subset (indices into the ascending frequencies) evaluates only those frequencies and
+    leaves zeros for the others; the first one evaluated starts from V0."""
     omegas, weights = frequency_quadrature(n_omega, omega0)
     V = orthonormalize_cholesky(np.asarray(V0, dtype=np.float64))
     n_r = V.shape[0]
@@ -424,7 +427,10 @@ def rpa_ec(o: Oracle, V0: np.ndarray, n_omega: int, tol: float, eps_c: float, om
     thr = eps_c * o.n_atoms / n_omega
     ritz = [None] * n_omega
     V_start = V
+    selected = set(range(n_omega)) if omega_subset is None else set(int(m) for m in omega_subset)
     for m in range(n_omega - 1, -1, -1):
+        if m not in selected:
+            continue
         if independent_frequencies:
             V = V_start
         ecm = 0.0

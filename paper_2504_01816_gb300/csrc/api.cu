@@ -128,6 +128,9 @@ void validate_options(const rpa_options &o) {
     if (o.stencil_shape < 0 || o.stencil_shape > 4) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 4]");
     if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
     if (o.contractions < 0 || o.contractions > 3) fail(RPA_ERR_INVALID, "contractions must be in [0, 3]");
+    if (o.omega_count < 0 || o.omega_first < 0 || (o.omega_count > 0 && o.omega_first + o.omega_count > o.n_omega) ||
+        (o.omega_count == 0 && o.omega_first != 0))
+        fail(RPA_ERR_INVALID, "omega_first/omega_count must select a range of the n_omega frequencies");
 }
 
 // Gauss-Legendre nodes and weights on (-1, 1) by Newton iteration on P_n, then the map
@@ -250,6 +253,8 @@ void rpa_default_options(rpa_options *o) {
     o->independent_frequencies = 0;
     o->sq_order = 0;
     o->contractions = 0;
+    o->omega_first = 0;
+    o->omega_count = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }
@@ -531,9 +536,13 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
     double ec = 0.0;
     std::vector<double> ecm_all(nw, 0.0);
     const double thr = o.eps_c * o.n_atoms / nw;
-    for (int m = nw - 1; m >= 0; --m) {
+    // frequencies of this call (all, or the range omega_first .. +omega_count), highest first
+    const int m_lo = o.omega_count > 0 ? o.omega_first : 0;
+    const int m_hi = o.omega_count > 0 ? o.omega_first + o.omega_count - 1 : nw - 1;
+    if (lambdas_host) std::memset(lambdas_host, 0, sizeof(double) * (size_t)nw * n_r);
+    for (int m = m_hi; m >= m_lo; --m) {
         cur_m = -1;
-        if (o.independent_frequencies && m != nw - 1) orthonormalize(V0_dev, V);
+        if (o.independent_frequencies && m != m_hi) orthonormalize(V0_dev, V);
         cur_m = m;
         double ecm = 0.0;
         int it = 0;

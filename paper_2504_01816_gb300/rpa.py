@@ -42,7 +42,7 @@ class rpa_options(ctypes.Structure):
                 ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int), ("project_solution", ctypes.c_int),
                 ("z_chunks", ctypes.c_int), ("stencil_shape", ctypes.c_int),
                 ("independent_frequencies", ctypes.c_int), ("sq_order", ctypes.c_int),
-                ("contractions", ctypes.c_int)]
+                ("contractions", ctypes.c_int), ("omega_first", ctypes.c_int), ("omega_count", ctypes.c_int)]
 
 
 PROF_SLOTS = 8
@@ -173,6 +173,8 @@ class Options:
     independent_frequencies: int = 0
     sq_order: int = 0
     contractions: int = 0
+    omega_first: int = 0
+    omega_count: int = 0
 
     def to_c(self) -> rpa_options:
         o = rpa_options()

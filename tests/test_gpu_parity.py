@@ -421,3 +421,24 @@ def test_tensor_core_ec_meets_the_method_target(rpa, prec, tiny):
     ref = oracle.rpa_ec(oracle.Oracle.from_system(s), V0, n_omega, tol=tol, eps_c=0.0, fixed_iters=iters)
     assert np.max(np.abs(res.lambdas - ref.lambdas)) < 1e-6
     assert abs(res.e_c_per_atom - ref.e_c / s.n_atoms) < 1e-6
+
+
+def test_frequency_ranges_sum_to_the_full_quadrature(rpa, tiny):
+    """rpa_options.omega_first / omega_count with independent frequencies: the E_c of a partition
+    of the frequencies, summed, equals one call over all of them (frequency sharding), and the
+    per-frequency results are those of the full call."""
+    s = tiny
+    V0 = cuda(synth.trial_vectors(0, 6, s.n_d))
+    base = dict(tol=1e-10, n_omega=5, fixed_subspace_iters=2, n_atoms=s.n_atoms, independent_frequencies=1)
+    with rpa.Context.from_system(s, opts(rpa, **base)) as ctx:
+        full = ctx.ec(V0)
+        parts = []
+        for first, count in ((0, 3), (3, 2)):
+            ctx.set_options(opts(rpa, omega_first=first, omega_count=count, **base))
+            parts.append(ctx.ec(V0))
+        with pytest.raises(rpa.RpaError):
+            ctx.set_options(opts(rpa, omega_first=4, omega_count=2, **base))
+    assert abs(parts[0].e_c + parts[1].e_c - full.e_c) < 1e-14
+    assert np.array_equal(parts[0].e_c_per_omega[:3], full.e_c_per_omega[:3])
+    assert np.array_equal(parts[1].e_c_per_omega[3:], full.e_c_per_omega[3:])
+    assert np.all(parts[0].lambdas[3:] == 0) and np.array_equal(parts[1].lambdas[3:], full.lambdas[3:])
