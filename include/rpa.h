@@ -149,6 +149,9 @@ typedef struct {
     long long near_breakdowns;      /* mixed form: FP32 COCG steps at which r^T r or p^T A p fell to
                                        rounding level (the recurrence restarted or the inner solve
                                        ended early), summed over systems */
+    long long host_syncs;           /* host synchronisations of the call: with CUDA graphs and without
+                                       profile, one per subspace iteration (its read-back of the Ritz
+                                       values), plus the adjoint's per-frequency steps */
 } rpa_stats;
 
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,

@@ -11,6 +11,8 @@
 
 namespace rpa {
 
+constexpr size_t kReadBackBytes = 16384;   // pinned read-back block of a context
+
 static thread_local std::string g_last_error;
 thread_local long long g_launches = 0;
 
@@ -77,6 +79,11 @@ Ctx::~Ctx() {
     if (h_state) cudaFreeHost(h_state);
     if (h_count) cudaFreeHost(h_count);
     cudaFree(d_tc_err);
+    cudaFree(d_qstats);
+    cudaFree(d_loop);
+    if (h_rb) cudaFreeHost(h_rb);
+    for (cudaEvent_t e : ev_apply)
+        if (e) cudaEventDestroy(e);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -92,6 +99,24 @@ int prof_slot(Ctx &c, const char *name) {
     std::strncpy(c.stats.prof_name[i], name, 31);
     c.stats.prof_name[i][31] = 0;
     return i;
+}
+
+void sync_stream(Ctx &c, cudaStream_t s) {
+    RPA_CUDA(cudaStreamSynchronize(s));
+    c.host_syncs += 1;
+}
+
+int add_queue_stats(Ctx &c, const QueueStats &h) {
+    c.stats.sternheimer_solves += h.solves;
+    c.stats.cocg_iterations += h.iters;
+    c.stats.refinement_steps += h.refines;
+    c.stats.stencil_points += (h.iters + h.refines) * c.nd;
+    c.stats.near_breakdowns += h.nearb;
+    g_launches += h.launches;
+    int worst = h.worst;
+    if (h.unfinished) worst = std::max(worst, (int)RPA_ERR_NOT_CONVERGED);
+    c.stats.worst_status = std::max(c.stats.worst_status, worst);
+    return worst;
 }
 
 void check_tensor_core_status(Ctx &c, cudaStream_t s) {
@@ -199,11 +224,14 @@ float ms_between(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-// R = nu^1/2 chi0 nu^1/2 V (symmetric) or nu chi0 V.  tmp1, tmp2: ncols x nd scratch.
+// R = nu^1/2 chi0 nu^1/2 V (symmetric) or nu chi0 V.  tmp1, tmp2: ncols x nd scratch.  Enqueues
+// the work without waiting for it: the phase times (events) and the per-system statuses (device
+// statistics) are collected by finish_call after the caller's next synchronisation.
+// Returns the worst per-system status known on the host (queues run without graphs or with
+// profiling); device-driven queues report theirs through finish_call.
 int apply_nuchi0_impl(Ctx &c, double omega, const double *V, double *R, int ncols, int symmetric, double *tmp1,
                       double *tmp2, cudaStream_t s) {
-    cudaEvent_t e[4];
-    for (auto &x : e) RPA_CUDA(cudaEventCreate(&x));
+    cudaEvent_t *e = c.ev_apply;
     RPA_CUDA(cudaEventRecord(e[0], s));
     const double *dv = V;
     const bool tc = use_tensor_cores_kronecker(c);
@@ -216,12 +244,42 @@ int apply_nuchi0_impl(Ctx &c, double omega, const double *V, double *R, int ncol
     RPA_CUDA(cudaEventRecord(e[2], s));
     coulomb_apply(c, symmetric ? 0.5 : 1.0, tmp2, R, ncols, s, tc);
     RPA_CUDA(cudaEventRecord(e[3], s));
-    RPA_CUDA(cudaEventSynchronize(e[3]));
-    c.stats.ms_coulomb += ms_between(e[0], e[1]) + ms_between(e[2], e[3]);
-    c.stats.ms_cocg += ms_between(e[1], e[2]);
-    for (auto &x : e) cudaEventDestroy(x);
-    if (use_tensor_cores(c)) check_tensor_core_status(c, s);
+    c.apply_timed = true;
     return worst;
+}
+
+// Bytes of the pinned read-back block: Ritz values (up to 1024), two energies, two pivot flags, the
+// tensor-core flag and the queue statistics.
+constexpr size_t kReadBackLam = 1024 * sizeof(double);
+// offsets in the read-back block
+constexpr size_t kRbScal = kReadBackLam, kRbInfo = kRbScal + 2 * sizeof(double), kRbTc = kRbInfo + 2 * sizeof(int),
+                 kRbStats = (kRbTc + sizeof(int) + 15) / 16 * 16;
+
+// Enqueue the read-back of the device flags and statistics into the pinned block (the caller
+// synchronises once, then calls finish_call).
+void enqueue_status_readback(Ctx &c, cudaStream_t s) {
+    RPA_CUDA(cudaMemcpyAsync(c.h_rb + kRbTc, c.d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RPA_CUDA(cudaMemcpyAsync(c.h_rb + kRbStats, c.d_qstats, sizeof(QueueStats), cudaMemcpyDeviceToHost, s));
+    RPA_CUDA(cudaMemsetAsync(c.d_qstats, 0, sizeof(QueueStats), s));
+}
+
+// After the synchronisation that completed enqueue_status_readback: phase times, tensor-core flag
+// and queue statistics; returns the worst per-system status.
+int finish_call(Ctx &c, cudaStream_t s) {
+    if (c.apply_timed) {
+        c.stats.ms_coulomb += ms_between(c.ev_apply[0], c.ev_apply[1]) + ms_between(c.ev_apply[2], c.ev_apply[3]);
+        c.stats.ms_cocg += ms_between(c.ev_apply[1], c.ev_apply[2]);
+        c.apply_timed = false;
+    }
+    int tcerr = 0;
+    std::memcpy(&tcerr, c.h_rb + kRbTc, sizeof(int));
+    if (tcerr) {
+        RPA_CUDA(cudaMemsetAsync(c.d_tc_err, 0, sizeof(int), s));
+        fail(RPA_ERR_CUDA, "a tensor-core contraction timed out waiting for its MMAs");
+    }
+    QueueStats q;
+    std::memcpy(&q, c.h_rb + kRbStats, sizeof q);
+    return add_queue_stats(c, q);
 }
 
 }  // namespace
@@ -311,6 +369,11 @@ rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_ord
             RPA_CUDA(cudaMallocHost((void **)&c.h_count, 8 * sizeof(int)));
             RPA_CUDA(cudaMalloc(&c.d_tc_err, sizeof(int)));
             RPA_CUDA(cudaMemsetAsync(c.d_tc_err, 0, sizeof(int), s));
+            RPA_CUDA(cudaMalloc(&c.d_qstats, sizeof(QueueStats)));
+            RPA_CUDA(cudaMemsetAsync(c.d_qstats, 0, sizeof(QueueStats), s));
+            RPA_CUDA(cudaMalloc(&c.d_loop, sizeof(int)));
+            RPA_CUDA(cudaMallocHost((void **)&c.h_rb, kReadBackBytes));
+            for (auto &e : c.ev_apply) RPA_CUDA(cudaEventCreate(&e));
             RPA_CUDA(cudaMalloc(&c.d_prof_points, sizeof(unsigned long long) * RPA_PROF_SLOTS));
             RPA_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
             {
@@ -423,6 +486,9 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
+        enqueue_status_readback(c, s);
+        sync_stream(c, s);
+        finish_call(c, s);
         c.opt.stencil_shape = best_i == 6 ? 4 : best_i / 2 + 1;
         c.opt.z_chunks = best_i == 6 ? 1 : best_i % 2 + 1;
         if (chosen_host) *chosen_host = best_i;
@@ -444,7 +510,9 @@ rpa_status rpa_apply_nuchi0(rpa_ctx *ctx, double omega, const double *V_dev, dou
         double *t1 = (double *)c.blockA.ensure(blk);
         double *t2 = (double *)c.blockB.ensure(blk);
         worst = apply_nuchi0_impl(c, omega, V_dev, R_dev, n_r, symmetric, t1, t2, s);
-        RPA_CUDA(cudaStreamSynchronize(s));
+        enqueue_status_readback(c, s);
+        sync_stream(c, s);
+        worst = std::max(worst, finish_call(c, s));
     });
     if (st != RPA_OK) return st;
     if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
@@ -457,6 +525,12 @@ namespace rpa {
 namespace {
 
 // Algorithm 1 with Rayleigh-Ritz; with grad != nullptr also dE_c/dV_loc (see rpa_ec_gradient).
+//
+// A subspace iteration is enqueued without waiting: the chi0 application (its COCG queue replayed
+// by a device-side graph loop), the projection and eigenvalues, the orthonormalisation (the
+// Cholesky pivot check stays on the device) and the read-back of the Ritz values, energies, pivot
+// flags and statistics into pinned memory; the host then synchronises once per iteration to take
+// the stopping decision.
 int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double *ec_host, double *ec_per_omega_host,
             rpa_stats *stats, cudaStream_t s, double *grad, double *V_out) {
     int worst = 0;
@@ -464,6 +538,7 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
     if (n_r > 1024) fail(RPA_ERR_INVALID, "n_r above 1024 is not supported");
     std::memset(&c.stats, 0, sizeof c.stats);
     g_launches = 0;
+    c.host_syncs = 0;
     const rpa_options &o = c.opt;
     const int nw = o.n_omega;
     double om[kMaxOmega], wt[kMaxOmega];
@@ -488,72 +563,67 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
     double *lam = Sm + nn;
     double *work = lam + n_r;             // 3 n_r
     double *ecm_dev = work + 3 * (size_t)n_r;
-    int *info = (int *)(ecm_dev + 2);
-    std::vector<double> h_lam(n_r), h_scal(2);
-    int h_info = 0;
+    int *info = (int *)(ecm_dev + 2);     // [0]: starting block, [1]: the block A V
+    const double *h_lam = (const double *)c.h_rb;
+    const double *h_scal = (const double *)(c.h_rb + kRbScal);
+    const int *h_info = (const int *)(c.h_rb + kRbInfo);
     if (grad) RPA_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * c.nd, s));
+    RPA_CUDA(cudaMemsetAsync(info, 0, 2 * sizeof(int), s));
 
-    cudaEvent_t t0, t1;
+    cudaEvent_t t0, t1, a, b;
     RPA_CUDA(cudaEventCreate(&t0));
     RPA_CUDA(cudaEventCreate(&t1));
+    RPA_CUDA(cudaEventCreate(&a));
+    RPA_CUDA(cudaEventCreate(&b));
     RPA_CUDA(cudaEventRecord(t0, s));
 
-    // Y = X L^{-T}, L L^T = X^T X (rows: Y = L^{-1} X)
-    int cur_m = -1, cur_it = 0;
-    auto orthonormalize = [&](const double *X, double *Y) {
+    // Y = X L^{-T}, L L^T = X^T X (rows: Y = L^{-1} X); a failed pivot is recorded in *flag (the
+    // first failure is kept) and read with the iteration's other results.
+    auto orthonormalize = [&](const double *X, double *Y, int *flag) {
         gram(X, n_r, X, n_r, c.nd, Cm, s, c.dense_scratch);
         symmetrize(Cm, n_r, s);
-        cholesky(Cm, n_r, info, s);
-        RPA_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s));
-        RPA_CUDA(cudaStreamSynchronize(s));
-        if (h_info != 0) {
-            // the overlap again, for the message: its diagonal holds the squared row norms
-            gram(X, n_r, X, n_r, c.nd, Wm, s, c.dense_scratch);
-            std::vector<double> M(nn);
-            RPA_CUDA(cudaMemcpyAsync(M.data(), Wm, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
-            RPA_CUDA(cudaStreamSynchronize(s));
-            double dmin = 1e300, dmax = 0.0;
-            int bad = 0;
-            for (int i = 0; i < n_r; ++i) {
-                const double d = M[(size_t)i * n_r + i];
-                if (!std::isfinite(d)) ++bad;
-                else {
-                    dmin = std::min(dmin, d);
-                    dmax = std::max(dmax, d);
-                }
-            }
-            fail(RPA_ERR_NOT_SPD,
-                 "overlap matrix not positive definite (pivot %d) of %s (frequency %d, subspace iteration %d); "
-                 "recomputed overlap: diagonal in [%.3e, %.3e], %d non-finite, pivot entry %.3e",
-                 h_info - 1, cur_m < 0 ? "the starting block" : "the block A V", cur_m, cur_it, dmin, dmax, bad,
-                 M[(size_t)(h_info - 1) * n_r + (h_info - 1)]);
-        }
+        cholesky(Cm, n_r, flag, s);
         tri_inverse(Cm, n_r, Lm, s);
         combine_rows(Lm, n_r, n_r, X, c.nd, Y, s);
     };
-    orthonormalize(V0_dev, V);
+    // the overlap again, for the message of a failed orthonormalisation: its diagonal holds the
+    // squared row norms
+    auto fail_not_spd = [&](const double *X, int pivot, const char *what, int m, int it) {
+        gram(X, n_r, X, n_r, c.nd, Wm, s, c.dense_scratch);
+        std::vector<double> M(nn);
+        RPA_CUDA(cudaMemcpyAsync(M.data(), Wm, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+        sync_stream(c, s);
+        double dmin = 1e300, dmax = 0.0;
+        int bad = 0;
+        for (int i = 0; i < n_r; ++i) {
+            const double d = M[(size_t)i * n_r + i];
+            if (!std::isfinite(d)) ++bad;
+            else {
+                dmin = std::min(dmin, d);
+                dmax = std::max(dmax, d);
+            }
+        }
+        fail(RPA_ERR_NOT_SPD,
+             "overlap matrix not positive definite (pivot %d) of %s (frequency %d, subspace iteration %d); "
+             "recomputed overlap: diagonal in [%.3e, %.3e], %d non-finite, pivot entry %.3e",
+             pivot, what, m, it, dmin, dmax, bad, M[(size_t)pivot * n_r + pivot]);
+    };
+    orthonormalize(V0_dev, V, info);
 
     double ec = 0.0;
     std::vector<double> ecm_all(nw, 0.0);
+    if (lambdas_host) std::memset(lambdas_host, 0, sizeof(double) * (size_t)nw * n_r);
     const double thr = o.eps_c * o.n_atoms / nw;
     // frequencies of this call (all, or the range omega_first .. +omega_count), highest first
     const int m_lo = o.omega_count > 0 ? o.omega_first : 0;
     const int m_hi = o.omega_count > 0 ? o.omega_first + o.omega_count - 1 : nw - 1;
-    if (lambdas_host) std::memset(lambdas_host, 0, sizeof(double) * (size_t)nw * n_r);
     for (int m = m_hi; m >= m_lo; --m) {
-        cur_m = -1;
-        if (o.independent_frequencies && m != m_hi) orthonormalize(V0_dev, V);
-        cur_m = m;
+        if (o.independent_frequencies && m != m_hi) orthonormalize(V0_dev, V, info);
         double ecm = 0.0;
         int it = 0;
         for (;;) {
             const double ecm_old = ecm;
-            cur_it = it;
-            const int w = apply_nuchi0_impl(c, om[m], V, R, n_r, 1, T1, T2, s);
-            worst = std::max(worst, w);
-            cudaEvent_t a, b;
-            RPA_CUDA(cudaEventCreate(&a));
-            RPA_CUDA(cudaEventCreate(&b));
+            worst = std::max(worst, apply_nuchi0_impl(c, om[m], V, R, n_r, 1, T1, T2, s));
             RPA_CUDA(cudaEventRecord(a, s));
             // Rayleigh-Ritz: C = V^T R, eigenvalues, E_cm = (w_m / 2 pi) sum g(lambda)
             if (use_tensor_cores(c))
@@ -569,14 +639,18 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
             if (o.sq_order > 0) sq_trace(Wm, n_r, o.sq_order, work, wt[m] / (2.0 * M_PI), ecm_dev + 1, s);
             sym_eigvals(Wm, n_r, lam, work, wt[m] / (2.0 * M_PI), ecm_dev, s);
             // orthonormalisation: M = R^T R = L L^T, V = R L^{-T}
-            orthonormalize(R, V);
-            RPA_CUDA(cudaMemcpyAsync(h_lam.data(), lam, sizeof(double) * n_r, cudaMemcpyDeviceToHost, s));
-            RPA_CUDA(cudaMemcpyAsync(h_scal.data(), ecm_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            orthonormalize(R, V, info + 1);
             RPA_CUDA(cudaEventRecord(b, s));
-            RPA_CUDA(cudaEventSynchronize(b));
+            // the iteration's one read-back
+            RPA_CUDA(cudaMemcpyAsync(c.h_rb, lam, sizeof(double) * n_r, cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaMemcpyAsync(c.h_rb + kRbScal, ecm_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            RPA_CUDA(cudaMemcpyAsync(c.h_rb + kRbInfo, info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            enqueue_status_readback(c, s);
+            sync_stream(c, s);
+            worst = std::max(worst, finish_call(c, s));
+            if (h_info[0] != 0) fail_not_spd(V0_dev, h_info[0] - 1, "the starting block", -1, 0);
+            if (h_info[1] != 0) fail_not_spd(R, h_info[1] - 1, "the block A V", m, it);
             c.stats.ms_subspace += ms_between(a, b);
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
             ecm = o.sq_order > 0 ? h_scal[1] : h_scal[0];
             ++it;
             if (o.fixed_subspace_iters > 0) {
@@ -588,12 +662,12 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
         c.stats.subspace_iterations[m] = it;
         ecm_all[m] = ecm;
         ec += ecm;
-        if (lambdas_host) std::memcpy(lambdas_host + (size_t)m * n_r, h_lam.data(), sizeof(double) * n_r);
+        if (lambdas_host) std::memcpy(lambdas_host + (size_t)m * n_r, h_lam, sizeof(double) * n_r);
         if (grad) {
             // Ritz pairs of the last iteration: C = Q diag(lambda) Q^T, y_i = sum_k Q[k][i] v_k
             std::vector<double> Ch(nn), wv, Q;
             RPA_CUDA(cudaMemcpyAsync(Ch.data(), Cprev, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
-            RPA_CUDA(cudaStreamSynchronize(s));
+            sync_stream(c, s);
             jacobi_eigh(Ch, n_r, wv, Q);
             std::vector<double> S(nn), coef(n_r);
             for (int i = 0; i < n_r; ++i) {
@@ -603,7 +677,10 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
             RPA_CUDA(cudaMemcpyAsync(Sm, S.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
             combine_rows(Sm, n_r, n_r, Vprev, c.nd, T1, s);           // Ritz vectors
             coulomb_apply(c, 0.5, T1, T2, n_r, s);                    // nu^1/2 y_i
-            worst = std::max(worst, response_square(c, om[m], T2, coef.data(), grad, n_r, s));
+            worst = std::max(worst, response_square(c, om[m], T2, coef.data(), grad, n_r, s));   // synchronises
+            enqueue_status_readback(c, s);
+            sync_stream(c, s);
+            worst = std::max(worst, finish_call(c, s));
         }
     }
     if (V_out) RPA_CUDA(cudaMemcpyAsync(V_out, V, blk, cudaMemcpyDeviceToDevice, s));
@@ -611,8 +688,8 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
     RPA_CUDA(cudaEventSynchronize(t1));
     c.stats.ms_total = ms_between(t0, t1);
     c.stats.launches = g_launches;
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    c.stats.host_syncs = c.host_syncs;
+    for (cudaEvent_t e : {t0, t1, a, b}) cudaEventDestroy(e);
     if (ec_host) {
         ec_host[0] = ec;
         ec_host[1] = ec / o.n_atoms;

@@ -1803,6 +1803,68 @@ __global__ void k_pair_rows(const double *__restrict__ psi, const double *__rest
         rows[(long long)j * nd + idx] = psi[(long long)n * nd + idx] * dv[(long long)j * nd + idx];
 }
 
+// (n, j) of the pair systems q = n * ncols + j (chi0 and the adjoint's response).
+__global__ void k_pair_index(int *__restrict__ sys_n, int *__restrict__ sys_j, int nsys, int ncols) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nsys) {
+        sys_n[q] = q / ncols;
+        sys_j[q] = q % ncols;
+    }
+}
+
+// Add a finished queue's per-system outputs to the device statistics (one block; integer sums).
+__global__ void k_queue_stats(const int *__restrict__ sys_out, int nsys, const int *__restrict__ count,
+                              QueueStats *__restrict__ qs, long long launches) {
+    __shared__ long long red[3][8];
+    __shared__ int wred[8];
+    long long it = 0, rf = 0, nb = 0;
+    int worst = 0;
+    for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
+        it += sys_out[i];
+        worst = max(worst, sys_out[nsys + i]);
+        rf += sys_out[2 * nsys + i];
+        nb += sys_out[3 * nsys + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        it += __shfl_down_sync(0xffffffffu, it, o);
+        rf += __shfl_down_sync(0xffffffffu, rf, o);
+        nb += __shfl_down_sync(0xffffffffu, nb, o);
+        worst = max(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = it;
+        red[1][w] = rf;
+        red[2][w] = nb;
+        wred[w] = worst;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            it += red[0][k];
+            rf += red[1][k];
+            nb += red[2][k];
+            worst = max(worst, wred[k]);
+        }
+        qs->solves += nsys;
+        qs->iters += it;
+        qs->refines += rf;
+        qs->nearb += nb;
+        qs->launches += launches;
+        qs->worst = max(qs->worst, worst);
+        if (*count > 0) qs->unfinished = 1;
+    }
+}
+
+// End of an epoch of a device-driven queue: continue while systems are busy or waiting and the
+// epoch bound is not reached (the bound guarantees that the loop ends).
+__global__ void k_continue(cudaGraphConditionalHandle h, const int *__restrict__ count, int *__restrict__ epochs,
+                           long long max_epochs, QueueStats *__restrict__ qs, long long per_epoch) {
+    const int e = ++(*epochs);
+    qs->launches += per_epoch;
+    cudaGraphSetConditional(h, (*count > 0 && e < max_epochs) ? 1u : 0u);
+}
+
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
@@ -1822,7 +1884,9 @@ struct SolveSpec {
     const double *coef = nullptr;   // device, one per column j
     double sign = 1.0;
     double omega = 0.0;
-    std::vector<int> n, j;
+    std::vector<int> n, j;          // systems given on the host, or:
+    int pairs = 0;                  // > 0: the pair systems q = n * pairs + j (n < N_s, j < pairs)
+    int nsys = 0;
 };
 
 // xy tiles of the stencil kernel: at most 64 columns wide and at most max_threads grid columns
@@ -1873,7 +1937,7 @@ size_t slot_storage_bytes(bool mixed, long long nd, int S) {
 }
 
 int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
-    const int nsys = (int)sp.n.size();
+    const int nsys = sp.pairs > 0 ? sp.nsys : (int)sp.n.size();
     if (nsys == 0) return RPA_OK;
     const int S = choose_slots(c, nsys);
     const bool mixed = c.opt.prec == RPA_MIXED;
@@ -1930,8 +1994,13 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     int *sys_n = list + 4 * S, *sys_j = sys_n + nsys, *sys_out = sys_j + nsys;
     int *fin_cnt = sys_out + 4 * (size_t)nsys, *fin_list = fin_cnt + 1;
     RPA_CUDA(cudaMemsetAsync(qi, 0, sizeof(int) * nint, st));
-    RPA_CUDA(cudaMemcpyAsync(sys_n, sp.n.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-    RPA_CUDA(cudaMemcpyAsync(sys_j, sp.j.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+    if (sp.pairs > 0) {                 // generated on the device: no host copy, no synchronisation
+        k_pair_index<<<cdiv(nsys, 256), 256, 0, st>>>(sys_n, sys_j, nsys, sp.pairs);
+        RPA_LAUNCH("pair index");
+    } else {
+        RPA_CUDA(cudaMemcpyAsync(sys_n, sp.n.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        RPA_CUDA(cudaMemcpyAsync(sys_j, sp.j.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+    }
     k_init_slots<<<cdiv(S, 128), 128, 0, st>>>(slots, S);
     RPA_LAUNCH("init slots");
 
@@ -2177,8 +2246,10 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const int per_maint = (mixed ? 8 : 5) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
     const int per_epoch = (use_ring ? 1 + kEpoch : 4 * kEpoch) + per_maint;
 
+    // device-driven queue: CUDA graphs, no profiling, no per-system outputs wanted
+    const bool device_loop = use_graph && !prof && !iters_out && !status_out;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    if (use_graph) {
+    if (use_graph && !device_loop) {
         for (int g = 0; g < (prof ? 2 : 1); ++g) {
             cudaGraph_t graph;
             RPA_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -2208,14 +2279,58 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
 
     maintenance(st);   // first fill of the slots
     launches += per_maint;
+    const long long per_sys = (long long)c.opt.maxit * (mixed ? c.opt.max_refine : 1) / kEpoch + 3;
+    const long long max_epochs = ((long long)nsys + S - 1) / S * per_sys + 4;
+
+    // Device-driven queue (CUDA graphs, no profiling, no per-system outputs wanted): one graph whose
+    // conditional while node replays the epoch until no system is busy or waiting, so the host never
+    // waits on the queue; its statistics accumulate on the device for the caller's next read-back.
+    if (device_loop) {
+        cudaGraph_t parent = nullptr, body_end = nullptr;
+        cudaGraphExec_t loop = nullptr;
+        RPA_CUDA(cudaGraphCreate(&parent, 0));
+        try {
+            cudaGraphConditionalHandle h;
+            RPA_CUDA(cudaGraphConditionalHandleCreate(&h, parent, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            RPA_CUDA(cudaGraphAddNode(&cnode, parent, nullptr, nullptr, 0, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            RPA_CUDA(cudaStreamBeginCaptureToGraph(c.cap_stream, body, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal));
+            epoch(c.cap_stream, 0);
+            k_continue<<<1, 1, 0, c.cap_stream>>>(h, count, c.d_loop, max_epochs, c.d_qstats, per_epoch + 1);
+            RPA_LAUNCH("queue loop condition");
+            RPA_CUDA(cudaStreamEndCapture(c.cap_stream, &body_end));
+            RPA_CUDA(cudaGraphInstantiate(&loop, parent, 0));
+        } catch (...) {
+            cudaGraph_t dummy;
+            if (cudaStreamEndCapture(c.cap_stream, &dummy) == cudaSuccess && dummy) cudaGraphDestroy(dummy);
+            (void)cudaGetLastError();
+            cudaGraphDestroy(parent);
+            throw;
+        }
+        RPA_CUDA(cudaMemsetAsync(c.d_loop, 0, sizeof(int), st));
+        RPA_CUDA(cudaGraphLaunch(loop, st));
+        k_queue_stats<<<1, 256, 0, st>>>(sys_out, nsys, count, c.d_qstats, launches + 3);
+        RPA_LAUNCH("queue statistics");
+        cudaGraphExecDestroy(loop);     // freed once the launch completes
+        cudaGraphDestroy(parent);
+        for (auto &e : evs) cudaEventDestroy(e);
+        count_launches(2);
+        return RPA_OK;                  // per-system statuses arrive with the statistics
+    }
+
     // Epochs are enqueued up to two ahead of the host's check of the busy count.
     constexpr int kRing = 4;
     int *hc = c.h_count;
     cudaEvent_t ev[kRing];
     for (auto &e : ev) RPA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     long long issued = 0, checked = 0;
-    const long long per_sys = (long long)c.opt.maxit * (mixed ? c.opt.max_refine : 1) / kEpoch + 3;
-    const long long max_epochs = ((long long)nsys + S - 1) / S * per_sys + 4;
     bool done = false;
     while (!done) {
         while (issued - checked < 2 && issued < max_epochs) {
@@ -2226,11 +2341,12 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         }
         if (checked >= issued) break;
         RPA_CUDA(cudaEventSynchronize(ev[checked % kRing]));
+        c.host_syncs += 1;
         collect_epoch(checked);
         if (hc[checked % kRing] == 0) done = true;
         ++checked;
     }
-    RPA_CUDA(cudaStreamSynchronize(st));
+    sync_stream(c, st);
     while (checked < issued) collect_epoch(checked++);
     for (auto &e : ev) cudaEventDestroy(e);
     for (int g = 0; g < 2; ++g)
@@ -2348,15 +2464,10 @@ int response_square(Ctx &c, double omega, const double *dv, const double *coef, 
     sp.Tc = pair_coefficients(c, dv, ncols, s);
     sp.sign = -1.0;
     sp.omega = omega;
-    sp.n.resize(nsys);
-    sp.j.resize(nsys);
-    for (int n = 0; n < c.ns; ++n)
-        for (int j = 0; j < ncols; ++j) {
-            sp.n[n * ncols + j] = n;
-            sp.j[n * ncols + j] = j;
-        }
+    sp.pairs = ncols;
+    sp.nsys = nsys;
     const int w = run_queue(c, sp, s, nullptr, nullptr);
-    RPA_CUDA(cudaStreamSynchronize(s));   // coef (host) must outlive the copy
+    sync_stream(c, s);   // coef (host) must outlive the copy
     return w;
 }
 
@@ -2369,13 +2480,8 @@ int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, 
     sp.Tc = pair_coefficients(c, dv, ncols, s);   // T[(n, j)][k] = u_k . (u_n (.) dv_j)
     sp.sign = -1.0;
     sp.omega = omega;
-    sp.n.resize(nsys);
-    sp.j.resize(nsys);
-    for (int n = 0; n < c.ns; ++n)
-        for (int j = 0; j < ncols; ++j) {
-            sp.n[n * ncols + j] = n;
-            sp.j[n * ncols + j] = j;
-        }
+    sp.pairs = ncols;
+    sp.nsys = nsys;
     return run_queue(c, sp, s, nullptr, nullptr);
 }
 

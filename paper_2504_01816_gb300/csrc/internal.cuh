@@ -74,6 +74,14 @@ struct SysState {
     int status;
 };
 
+// Summary of the Sternheimer queues run since the last read-back, accumulated on the device (so
+// that a queue needs no host synchronisation) and added to rpa_stats at the next one.
+struct QueueStats {
+    long long solves, iters, refines, nearb, launches;
+    int worst;          // largest per-system status
+    int unfinished;     // a queue stopped at its epoch bound with systems left
+};
+
 // ------------------------------------------------------------------------------------------
 // Context
 // ------------------------------------------------------------------------------------------
@@ -116,6 +124,13 @@ struct Ctx {
     size_t h_state_cap = 0;
     int *h_count = nullptr;       // pinned host counter
     int *d_tc_err = nullptr;      // set by a tensor-core contraction that gave up waiting on its MMAs
+    QueueStats *d_qstats = nullptr;   // device accumulator of queue statistics
+    int *d_loop = nullptr;            // epoch counter of a device-driven queue
+    char *h_rb = nullptr;             // pinned read-back block (Ritz values, scalars, statistics)
+    long long host_syncs = 0;         // host synchronisations of the current call
+    // events of the last chi0 application (Coulomb / COCG phase times, read at the next sync)
+    cudaEvent_t ev_apply[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool apply_timed = false;
 
     // per-call statistics
     rpa_stats stats{};
@@ -149,6 +164,12 @@ void check_tensor_core_status(Ctx &c, cudaStream_t s);
 void coulomb_setup(Ctx &c);
 // Same operator with its scratch in the library's fixed device array (no allocation).
 void coulomb_apply_noalloc(Ctx &c, double power, const double *in, double *out, int ncols, cudaStream_t s);
+
+// Synchronise s and count it in the call's statistics.
+void sync_stream(Ctx &c, cudaStream_t s);
+// After a synchronisation: add the device queue statistics read back into h (pinned) to the
+// call's statistics and return the worst per-system status seen.
+int add_queue_stats(Ctx &c, const QueueStats &h);
 
 // Sternheimer solves for the systems given by (n, j) pairs with real right-hand sides b
 // (nsys x nd, row per system) -> complex solutions x (nsys x nd interleaved, FP64).

@@ -58,7 +58,8 @@ class rpa_stats(ctypes.Structure):
                 ("prof_count", ctypes.c_int), ("prof_name", (ctypes.c_char * 32) * PROF_SLOTS),
                 ("prof_launches", ctypes.c_longlong * PROF_SLOTS), ("prof_ms", ctypes.c_double * PROF_SLOTS),
                 ("prof_points", ctypes.c_double * PROF_SLOTS), ("prof_bytes", ctypes.c_double * PROF_SLOTS),
-                ("launches", ctypes.c_longlong), ("near_breakdowns", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("near_breakdowns", ctypes.c_longlong),
+                ("host_syncs", ctypes.c_longlong)]
 
 
 def stats_dict(stats: "rpa_stats", n_omega: int) -> dict:

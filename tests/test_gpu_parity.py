@@ -254,6 +254,8 @@ def test_ec_matches_oracle_fixed_iterations(rpa, prec, tiny):
     assert np.allclose(res.stats["weights"], ref.weights, rtol=1e-13)
     assert res.stats["subspace_iterations"] == [iters] * n_omega
     assert np.all(res.lambdas <= 1e-12) and res.e_c < 0
+    # the COCG queues run as device-side graph loops: one host synchronisation per subspace iteration
+    assert res.stats["host_syncs"] == iters * n_omega
 
 
 def test_ec_converged_mode_matches_oracle(rpa, ragged):
