@@ -68,6 +68,7 @@ void DevBuf::release() {
 Ctx::~Ctx() {
     cudaFree(vloc64);
     cudaFree(vloc32);
+    cudaFree(vloc_lo);
     cudaFree(psi64);
     cudaFree(psi32);
     cudaFree(eps_dev);
@@ -134,6 +135,12 @@ namespace {
 __global__ void k_to_float(const double *in, float *out, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
+}
+
+// lo = x - (float)x in FP32: x = hi + lo to ~2^-48 |x|
+__global__ void k_low_part(const double *in, float *out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)(in[i] - (double)(float)in[i]);
 }
 
 void validate_options(const rpa_options &o) {
@@ -357,6 +364,7 @@ rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_ord
             c.eps.assign(eps_host, eps_host + n_s);
             RPA_CUDA(cudaMalloc(&c.vloc64, sizeof(double) * nd));
             RPA_CUDA(cudaMalloc(&c.vloc32, sizeof(float) * nd));
+            RPA_CUDA(cudaMalloc(&c.vloc_lo, sizeof(float) * nd));
             RPA_CUDA(cudaMalloc(&c.psi64, sizeof(double) * nd * n_s));
             RPA_CUDA(cudaMalloc(&c.psi32, sizeof(float) * nd * n_s));
             RPA_CUDA(cudaMalloc(&c.eps_dev, sizeof(double) * n_s));
@@ -364,6 +372,7 @@ rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_ord
             RPA_CUDA(cudaMemcpyAsync(c.psi64, psi_dev, sizeof(double) * nd * n_s, cudaMemcpyDeviceToDevice, s));
             RPA_CUDA(cudaMemcpyAsync(c.eps_dev, eps_host, sizeof(double) * n_s, cudaMemcpyHostToDevice, s));
             k_to_float<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(c.vloc64, c.vloc32, nd);
+            k_low_part<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(c.vloc64, c.vloc_lo, nd);
             k_to_float<<<(unsigned)((nd * n_s + 255) / 256), 256, 0, s>>>(c.psi64, c.psi32, nd * n_s);
             RPA_LAUNCH("setup");
             RPA_CUDA(cudaMallocHost((void **)&c.h_count, 8 * sizeof(int)));

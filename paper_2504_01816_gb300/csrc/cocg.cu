@@ -201,33 +201,6 @@ __device__ __forceinline__ void coords(long long idx, const Grid3 &g, int &i, in
     i = (int)(rem - (long long)j * g.nx);
 }
 
-// (H + sigma) p at one point: diagonal (3 a0 + V + sigma) plus 6 x radius neighbours, zero
-// outside the box.
-template <typename T, typename C>
-__device__ __forceinline__ C stencil_at(const C *__restrict__ p, long long idx, int i, int j, int k,
-                                        const Grid3 &g, const Coef<T> &cf, T dre, T dim) {
-    const C c = p[idx];
-    T re = dre * c.x - dim * c.y;
-    T im = dre * c.y + dim * c.x;
-    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-#pragma unroll
-    for (int s = 1; s <= kRadius; ++s) {
-        T ar = 0, ai = 0;
-        if (i - s >= 0) { C u = p[idx - s]; ar += u.x; ai += u.y; }
-        if (i + s < g.nx) { C u = p[idx + s]; ar += u.x; ai += u.y; }
-        if (j - s >= 0) { C u = p[idx - s * sy]; ar += u.x; ai += u.y; }
-        if (j + s < g.ny) { C u = p[idx + s * sy]; ar += u.x; ai += u.y; }
-        if (k - s >= 0) { C u = p[idx - s * sz]; ar += u.x; ai += u.y; }
-        if (k + s < g.nz) { C u = p[idx + s * sz]; ar += u.x; ai += u.y; }
-        re += cf.a[s] * ar;
-        im += cf.a[s] * ai;
-    }
-    C out;
-    out.x = re;
-    out.y = im;
-    return out;
-}
-
 // ---------------------------------------------------------------------------------------------
 // COCG iteration: two per-slot scalar kernels (one warp per slot, the only writers of the slot
 // state during the iteration) and three kernels over the active (slot, chunk) items.
@@ -1258,71 +1231,156 @@ __device__ __forceinline__ double next_scale(const Slot &sl) {
     return sl.scale / fmax(rn, 1e-12 * sl.ref_norm);
 }
 
-// Mixed form, slots whose inner solve ended: x64 += d / scale, d projected first when
-// P.cproject (dropped if the inner solve went non-finite).
-__global__ void __launch_bounds__(kThreads) k_refine_x(Params P, double2 *__restrict__ x64, const float2 *__restrict__ d) {
+// Mixed form, slots whose inner solve ended: the correction d' = d (projected first when
+// P.cproject) goes into x64 += d' / scale and, for the residual update, into dq (the idle q
+// buffer); d is cleared for the next inner solve.  A correction that went non-finite is dropped:
+// only d is cleared.
+__global__ void __launch_bounds__(kThreads) k_refine_x(Params P, double2 *__restrict__ x64, float2 *__restrict__ d,
+                                                       float2 *__restrict__ dq) {
     const long long items = (long long)P.S * P.nblk;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
         const Slot &sl = P.slots[s];
-        if (sl.phase != kInnerDone || sl.discard) continue;
+        if (sl.phase != kInnerDone) continue;
+        const bool keep = !sl.discard;
         const double inv = 1.0 / sl.scale;
         const long long off = (long long)s * P.g.nd;
         const float *tp = P.Tp32 + (long long)s * P.ns * 2;
         for (int t = 0; t < kPPT; ++t) {
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
             if (idx < P.g.nd) {
-                double2 xv = x64[off + idx];
-                float2 dv = d[off + idx];
-                if (P.cproject)
-                    for (int k = 0; k < P.ns; ++k) {
-                        const float u = P.psi32[(long long)k * P.g.nd + idx];
-                        dv.x -= tp[2 * k] * u;
-                        dv.y -= tp[2 * k + 1] * u;
-                    }
-                xv.x += (double)dv.x * inv;
-                xv.y += (double)dv.y * inv;
-                x64[off + idx] = xv;
+                if (keep) {
+                    double2 xv = x64[off + idx];
+                    float2 dv = d[off + idx];
+                    if (P.cproject)
+                        for (int k = 0; k < P.ns; ++k) {
+                            const float u = P.psi32[(long long)k * P.g.nd + idx];
+                            dv.x -= tp[2 * k] * u;
+                            dv.y -= tp[2 * k + 1] * u;
+                        }
+                    xv.x += (double)dv.x * inv;
+                    xv.y += (double)dv.y * inv;
+                    x64[off + idx] = xv;
+                    dq[off + idx] = dv;
+                }
+                d[off + idx] = make_float2(0.f, 0.f);
             }
         }
     }
 }
 
-// Mixed form: r64 = b - (H + sigma) x64 in FP64 (x64 has absorbed the FP32 correction d); the
-// next inner solve starts from d = 0, r32 = scale * r64 (scale = next_scale), p = 0.  Partials
-// (into partB): r32^T r32 and ||scale * r64||^2.  (Continuing the FP32 recurrence with the replaced residual instead of restarting
-// was measured to lose convergence: the FP32 recursive residual can be far below the true one.)
-__global__ void __launch_bounds__(kThreads) k_residual64(Params P, const double *__restrict__ b,
-                                                         const double2 *__restrict__ x64, float2 *__restrict__ d,
-                                                         float2 *__restrict__ r32, float2 *__restrict__ p32,
-                                                         const double *__restrict__ vloc, Coef<double> cf) {
+// Error-free transformations on FP32 (Knuth's TwoSum; the product error from one fma), the
+// building blocks of double-float ("float-float") arithmetic: a value is an unevaluated sum
+// hi + lo of two FP32 numbers, ~48 significant bits (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005, use the same transformations).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (S, E) += (hi, lo) * x for an FP32 x: the product's rounding error is exact through fma.
+__device__ __forceinline__ void df_mad(float hi, float lo, float x, float &S, float &E) {
+    const float p = __fmul_rn(hi, x);
+    const float pe = __fmaf_rn(hi, x, -p);
+    float t;
+    two_sum(S, p, S, t);
+    E += t + pe + lo * x;
+}
+
+// (H + sigma) v at one point in double-float arithmetic for an FP32 complex v: the six
+// neighbours at each distance are summed exactly (TwoSum), multiplied by the split coefficient
+// (hi + lo) and accumulated with their rounding errors.  Zero outside the box.
+__device__ __forceinline__ void df_stencil(const float2 *__restrict__ v, long long idx, int i, int j, int k,
+                                           const Grid3 &g, const Coef<float> &ch, const Coef<float> &cl, float dh,
+                                           float dl, float oh, float ol, float (&re)[2], float (&im)[2]) {
+    const float2 c = v[idx];
+    float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
+    df_mad(dh, dl, c.x, Sr, Er);          // (3 a0 + V + sigma_re) c
+    df_mad(dh, dl, c.y, Si, Ei);
+    df_mad(-oh, -ol, c.y, Sr, Er);        // i sigma_im c
+    df_mad(oh, ol, c.x, Si, Ei);
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+#pragma unroll
+    for (int s = 1; s <= kRadius; ++s) {
+        float ar = 0.f, er = 0.f, ai = 0.f, ei = 0.f, t;
+        auto add = [&](float2 u) {
+            two_sum(ar, u.x, ar, t);
+            er += t;
+            two_sum(ai, u.y, ai, t);
+            ei += t;
+        };
+        if (i - s >= 0) add(v[idx - s]);
+        if (i + s < g.nx) add(v[idx + s]);
+        if (j - s >= 0) add(v[idx - s * sy]);
+        if (j + s < g.ny) add(v[idx + s * sy]);
+        if (k - s >= 0) add(v[idx - s * sz]);
+        if (k + s < g.nz) add(v[idx + s * sz]);
+        // a_s (ar + er): the sum's low part times the coefficient's high part joins the error term
+        df_mad(ch.a[s], cl.a[s], ar, Sr, Er);
+        Er += ch.a[s] * er;
+        df_mad(ch.a[s], cl.a[s], ai, Si, Ei);
+        Ei += ch.a[s] * ei;
+    }
+    re[0] = Sr;
+    re[1] = Er;
+    im[0] = Si;
+    im[1] = Ei;
+}
+
+// Mixed form: the FP64 residual of the slots whose inner solve ended, updated with their
+// correction, r64 -= (H + sigma) d' / scale, where (H + sigma) d' is evaluated in double-float
+// arithmetic on the FP32 pipes from the FP32 correction d' (the coefficients and V_loc split into
+// FP32 pairs).  It agrees with recomputing b - (H + sigma) x64 in FP64 to ~2^-48 of the update,
+// without the ~90 FP64 operations per point that GB300's FP64 rate makes the bottleneck.  The next
+// inner solve starts from r32 = scale * r64 (scale = next_scale) with p = 0 (d was cleared by
+// k_refine_x).  Partials (into partB): r32^T r32 and ||scale * r64||^2, summed in FP32 per thread.
+// (Continuing the FP32 recurrence with the replaced residual instead of restarting was measured
+// to lose convergence: the FP32 recursive residual can be far below the true one.)
+__global__ void __launch_bounds__(kThreads) k_residual_df(Params P, double2 *__restrict__ r64,
+                                                          const float2 *__restrict__ dq, float2 *__restrict__ r32,
+                                                          float2 *__restrict__ p32, const float *__restrict__ vhi,
+                                                          const float *__restrict__ vlo, Coef<float> ch,
+                                                          Coef<float> cl, double a0x3) {
     const long long items = (long long)P.S * P.nblk;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int s = (int)(it / P.nblk), chunk = (int)(it % P.nblk);
         const Slot &sl = P.slots[s];
         if (sl.phase != kInnerDone) continue;
-        const double sre = sl.shift_re, sim = sl.shift_im;
-        const double sc = next_scale(sl);
+        const bool upd = !sl.discard;
+        const double sc = next_scale(sl), inv = 1.0 / sl.scale;
+        // 3 a0 + sigma_re and sigma_im as FP32 pairs
+        const double d0 = a0x3 + sl.shift_re;
+        const float d0h = (float)d0, d0l = (float)(d0 - (double)d0h);
+        const float oh = (float)sl.shift_im, ol = (float)(sl.shift_im - (double)oh);
         const long long off = (long long)s * P.g.nd;
-        double v[3] = {0.0, 0.0, 0.0};
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
         for (int t = 0; t < kPPT; ++t) {
             const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
             if (idx < P.g.nd) {
-                int i, j, k;
-                coords(idx, P.g, i, j, k);
-                const double dre = 3.0 * cf.a[0] + vloc[idx] + sre;
-                const double2 ax = stencil_at<double, double2>(x64 + off, idx, i, j, k, P.g, cf, dre, sim);
-                const double rr = (b[off + idx] - ax.x) * sc, ri = -ax.y * sc;
-                const float2 rf = make_float2((float)rr, (float)ri);
+                double2 rv = r64[off + idx];
+                if (upd) {
+                    int i, j, k;
+                    coords(idx, P.g, i, j, k);
+                    float dh, dl, e;                      // 3 a0 + V + sigma_re as a pair
+                    two_sum(d0h, vhi[idx], dh, e);
+                    dl = e + d0l + vlo[idx];
+                    float re[2], im[2];
+                    df_stencil(dq + off, idx, i, j, k, P.g, ch, cl, dh, dl, oh, ol, re, im);
+                    rv.x = fma(-((double)re[0] + (double)re[1]), inv, rv.x);
+                    rv.y = fma(-((double)im[0] + (double)im[1]), inv, rv.y);
+                    r64[off + idx] = rv;
+                }
+                const float2 rf = make_float2((float)(rv.x * sc), (float)(rv.y * sc));
                 r32[off + idx] = rf;
-                d[off + idx] = make_float2(0.f, 0.f);
                 p32[off + idx] = make_float2(0.f, 0.f);         // direction buffer of iteration 0
-                v[0] += (double)rf.x * rf.x - (double)rf.y * rf.y;
-                v[1] += 2.0 * (double)rf.x * rf.y;
-                v[2] += rr * rr + ri * ri;
+                v0 += rf.x * rf.x - rf.y * rf.y;
+                v1 += 2.f * rf.x * rf.y;
+                v2 += rf.x * rf.x + rf.y * rf.y;
             }
         }
-        block_sum<3>(v);
+        const float vf[3] = {v0, v1, v2};
+        double v[3];
+        block_sum_t<float, 3>(vf, v);
         if (threadIdx.x == 0) {
             double *o = P.partB + ((long long)s * P.nblk + chunk) * 3;
             o[0] = v[0];
@@ -1734,11 +1792,12 @@ __global__ void __launch_bounds__(1024) k_refill(Params P, const int *__restrict
 
 // Load the right-hand side of every loading slot:
 //   b = sign * (base - sum_k T[sys][k] u_k),  base = u_n (.) vt_j (pair) or rhs[sys]
-// then x64 = 0 and the inner vectors start from r = b, x = 0, p = 0.  Partials: r^T r, ||b||^2.
+// then x64 = 0, the FP64 residual r64 = b (mixed form), and the inner vectors start from r = b,
+// x = 0, p = 0.  Partials: r^T r, ||b||^2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_load(Params P, const double *__restrict__ psi, int ns,
                                                    const double *__restrict__ vt, const double *__restrict__ rhs,
-                                                   const double *__restrict__ Tc, double sign, double *__restrict__ b,
+                                                   const double *__restrict__ Tc, double sign, double2 *__restrict__ b,
                                                    double2 *__restrict__ x64, typename Cx<T>::t *__restrict__ xin,
                                                    typename Cx<T>::t *__restrict__ r, typename Cx<T>::t *__restrict__ p,
                                                    long long pstride) {
@@ -1759,7 +1818,7 @@ __global__ void __launch_bounds__(kThreads) k_load(Params P, const double *__res
                 if (tc)
                     for (int k = 0; k < ns; ++k) base -= tc[k] * psi[(long long)k * P.g.nd + idx];
                 const double bv = sign * base;
-                b[off + idx] = bv;
+                b[off + idx] = make_double2(bv, 0.0);     // the FP64 residual of x64 = 0
                 x64[off + idx] = make_double2(0.0, 0.0);
                 C z;
                 z.x = (T)0;
@@ -1914,7 +1973,7 @@ int choose_slots(const Ctx &c, int nsys) {
     if (c.opt.batch_systems > 0) return std::max(1, std::min(nsys, c.opt.batch_systems));
     // All systems of a call in flight when they fit in 8 GB of slot storage; otherwise as many
     // as fit (the queue refills the slots).
-    const double slot_bytes = (double)c.nd * (c.opt.prec == RPA_MIXED ? 64.0 : 88.0);
+    const double slot_bytes = (double)c.nd * (c.opt.prec == RPA_MIXED ? 72.0 : 96.0);
     long long S = std::max(1LL, (long long)(8.0e9 / slot_bytes));
     return (int)std::min<long long>(S, nsys);
 }
@@ -1933,7 +1992,7 @@ struct Carver {
 
 size_t slot_storage_bytes(bool mixed, long long nd, int S) {
     const size_t n = (size_t)nd * S;
-    return 16 * n + 8 * n + (mixed ? 5 * 8 * n : 4 * 16 * n) + 8 * 256;
+    return 16 * n + 16 * n + (mixed ? 5 * 8 * n : 4 * 16 * n) + 8 * 256;
 }
 
 int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
@@ -1948,7 +2007,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     // slot storage: x64, b, then the inner vectors x, r, p, q (FP32 complex, or FP64 sharing x64)
     Carver cv{(char *)c.cocg_state.ensure(slot_storage_bytes(mixed, nd, S))};
     double2 *x64 = cv.take<double2>(n);
-    double *b = cv.take<double>(n);
+    double2 *b = cv.take<double2>(n);      // right-hand side; the mixed form's FP64 residual r64
     void *xin, *r, *p, *q;           // p: two direction buffers, pstride elements apart
     if (mixed) {
         xin = cv.take<float2>(n);
@@ -2082,6 +2141,11 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         1, std::min<long long>((long long)S * ntiles, (long long)dev_sms * std::max(1, pa_per_sm)));
     const Coef<float> cf32 = cast_coef<float>(c.coef);
     const Coef<double> cf64 = cast_coef<double>(c.coef);
+    Coef<float> cf_hi, cf_lo;              // the coefficients as FP32 pairs (double-float residual)
+    for (int k = 0; k <= kRadius; ++k) {
+        cf_hi.a[k] = (float)c.coef.a[k];
+        cf_lo.a[k] = (float)(c.coef.a[k] - (double)cf_hi.a[k]);
+    }
     const double scale = 4.0 / (c.h * c.h * c.h);
 
     // the fused kernel: one block per system, four rotating active lists
@@ -2163,9 +2227,9 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
                 k_cproj_dots<<<grid, kThreads, 0, ss>>>(P, (const float2 *)xin);
                 k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P, kInnerDone);
             }
-            k_refine_x<<<grid, kThreads, 0, ss>>>(P, x64, (const float2 *)xin);
-            k_residual64<<<grid, kThreads, 0, ss>>>(P, b, x64, (float2 *)xin, (float2 *)r, (float2 *)p, c.vloc64,
-                                                    cf64);   // p = direction buffer 0
+            k_refine_x<<<grid, kThreads, 0, ss>>>(P, x64, (float2 *)xin, (float2 *)q);
+            k_residual_df<<<grid, kThreads, 0, ss>>>(P, b, (const float2 *)q, (float2 *)r, (float2 *)p, c.vloc32,
+                                                     c.vloc_lo, cf_hi, cf_lo, 3.0 * c.coef.a[0]);   // p = direction buffer 0
             if (P.cproject) {
                 k_cproj_dots<<<grid, kThreads, 0, ss>>>(P, (const float2 *)r);
                 k_proj_sum<<<wgrid, kThreads, 0, ss>>>(P, kInnerDone);

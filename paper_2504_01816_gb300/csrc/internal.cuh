@@ -96,6 +96,7 @@ struct Ctx {
     // inputs (device copies)
     double *vloc64 = nullptr;
     float *vloc32 = nullptr;
+    float *vloc_lo = nullptr;     // V_loc - vloc32 in FP32: V_loc as an FP32 pair
     double *psi64 = nullptr;      // ns x nd (row s = orbital s)
     float *psi32 = nullptr;       // FP32 copy (projection of the mixed form's FP32 residuals)
     std::vector<double> eps;

@@ -9,19 +9,21 @@
 //   * k is walked in chunks of kTcK = 64.  Within a chunk every row m of A gets the power of two
 //     s_m = 2^(e_m + 1) above its largest |A(m, k)| (e_m its binary exponent), every row n of B
 //     likewise s_n, so that |A(m, k) / s_m| < 1.
-//   * x = A(m, k) / s_m * 2^7 is cut into four integer pieces of at most 8 bits,
-//       x = a1 + 2^-8 a2 + 2^-16 a3 + 2^-24 a4 + r,  |a_i| <= 128,  |r| < 2^-25,
-//     each exactly representable in BF16 (8 significant bits).  Same for B.
-//   * Products a_i b_j are integers below 2^14, so over one chunk (64 values of k) every partial
-//     sum the tensor core forms -- inside one MMA of 16 k values, or accumulated over the chunk's
-//     four MMAs -- is an integer below 2^24 and therefore exact in its FP32 accumulator, whatever
-//     the rounding of the hardware's additions.  The ten products of weight 2^0 .. 2^-24 go to four
-//     tensor-memory tiles by weight: L0 = a1.b1; L1 = a1.b2 + a2.b1; L2 = a1.b3 + a3.b1 + a2.b2;
-//     L3 = a1.b4 + a4.b1 + a2.b3 + a3.b2 (sums of up to 4 x 64 products: below 2^22).
-//   * After each chunk the tiles are read back (tcgen05.ld) and the chunk's contribution
-//     s_m s_n 2^-14 (L0 + 2^-8 L1 + 2^-16 L2 + 2^-24 L3) is added in FP64.
-// The only errors are the neglected pieces (weights 2^-32 and below, relative to s_m s_n) and the
-// FP64 additions: about 1e-9 of the chunk-row maxima, far below the FP32 level.
+//   * |x| = |A(m, k)| / s_m * 2^7 <= 128 is rounded to 2^-24 and cut into four balanced integer
+//     digits, read off the bits of the FP64 significand with integer instructions:
+//       |x| = a1 + 2^-8 a2 + 2^-16 a3 + 2^-24 a4 + r,  0 <= a1 <= 128, |a2..a4| <= 128, |r| <= 2^-25,
+//     each times the sign of A(m, k) and exactly representable in BF16 (8 significant bits).
+//   * Products a_i b_j are integers of magnitude at most 2^14, so over one chunk (64 values of k)
+//     every partial sum the tensor core forms -- inside one MMA of 16 k values, or accumulated over
+//     the chunk's four MMAs -- is an integer below 2^24 (the largest tile, L3, sums at most 256
+//     products: below 2^22) and therefore exact in its FP32 accumulator, whatever the rounding of
+//     the hardware's additions.  The ten products of weight 2^0 .. 2^-24 go to four tensor-memory tiles by weight:
+//     L0 = a1.b1; L1 = a1.b2 + a2.b1; L2 = a1.b3 + a3.b1 + a2.b2; L3 = a1.b4 + a4.b1 + a2.b3 + a3.b2.
+//   * After each chunk the tiles are read back (tcgen05.ld), combined exactly in 64-bit integers
+//     as 2^24 L0 + 2^16 L1 + 2^8 L2 + L3, and the chunk's contribution s_m s_n 2^-38 times that
+//     integer is added in FP64 (one conversion and one multiply-add per output and chunk).
+// The only errors are the truncated remainders and the neglected products (weights 2^-31 and
+// below, relative to s_m s_n) and the FP64 additions: about 1e-9 of the chunk-row maxima.
 //
 // Used for the projection C = V^T R of the Rayleigh-Ritz step (Algorithm 1), the P_c coefficients
 // T_{k,(n,j)} = u_k . (u_n (.) nu^1/2 v_j) of the Sternheimer right-hand sides (Eqs. 7-9), and the
@@ -107,24 +109,34 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k) {
 // Biased binary exponent field of |x| (0 for zero).
 __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
 
-// x / 2^(e - 1022) * 2^7 (|result| < 128 when e is the exponent field of a value >= |x|) as four
-// integer pieces of at most 8 bits (exact BF16 values): x = a1 + a2 2^-8 + a3 2^-16 + a4 2^-24 + r.
+// The four BF16 pieces of x for the row exponent field e (see above), from the significand bits:
+// I = round(|x| / 2^(e - 1022) * 2^31) = round(significand / 2^(22 + e - e_x)), then balanced base-256
+// digits I = a1 2^24 + a2 2^16 + a3 2^8 + a4 with a2..a4 in [-128, 127] and 0 <= a1 <= 128 (balanced
+// digits keep the neglected products unbiased).  An integer of magnitude <= 256 converts to FP32
+// exactly with no bits below the top 8 of its significand, so the upper half of its FP32 pattern
+// is the same value in BF16.
 __device__ __forceinline__ void cut4(double x, int e, __nv_bfloat16 (&p)[4]) {
-    // power of two 2^(1029 - e), exact; a row of zeros (e = 0) gives zero pieces
-    const double t = e > 0 ? x * __hiloint2double((2052 - e) << 20, 0) : 0.0;
-    const float hi = (float)t;
-    const float lo = (float)(t - (double)hi);       // t = hi + lo to ~2^-48 |t|
-    const float a1 = rintf(hi);
-    float u = (hi - a1) * 256.f + lo * 256.f;       // hi - a1 exact; |u| <= 128
-    const float a2 = rintf(u);
-    u = (u - a2) * 256.f;                           // exact
-    const float a3 = rintf(u);
-    u = (u - a3) * 256.f;
-    const float a4 = rintf(u);
-    p[0] = __float2bfloat16_rn(a1);
-    p[1] = __float2bfloat16_rn(a2);
-    p[2] = __float2bfloat16_rn(a3);
-    p[3] = __float2bfloat16_rn(a4);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    const int sh = 22 + e - ex;
+    long long I = 0;
+    if (ex > 0 && sh < 64)
+        I = (long long)((((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << (sh - 1))) >> sh);
+    int dg[4];
+#pragma unroll
+    for (int i = 3; i >= 1; --i) {
+        dg[i] = (int)(((I + 128) & 255) - 128);
+        I = (I - dg[i]) >> 8;
+    }
+    dg[0] = (int)I;
+    const unsigned short sx = (unsigned short)((bits >> 48) & 0x8000u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const unsigned int v = (unsigned int)abs(dg[i]);
+        const unsigned short h = (unsigned short)(__float_as_uint(__uint2float_rn(v)) >> 16);
+        const unsigned short sg = dg[i] < 0 ? (unsigned short)(sx ^ 0x8000u) : sx;
+        p[i] = __ushort_as_bfloat16(v ? (unsigned short)(h | sg) : (unsigned short)0);
+    }
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -148,7 +160,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_tc_gemm(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char *tA = tsm;                                       // [4][kTcTileA]
     unsigned char *tB = tsm + kTcPieces * kTcTileA;                // [4][kTcTileB]
@@ -291,14 +303,16 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int eb = expB[col0 + 8 * h + c];
-                // s_m s_n 2^-14 = 2^(ea - 1022 + eb - 1022 - 14); zero rows have exponent field 0
-                const double sc = (ea == 0 || eb == 0) ? 0.0 : __hiloint2double((ea + eb - 2058 + 1023) << 20, 0);
-                const double v = (((double)__uint_as_float(l3[c]) * 0.00390625 + (double)__uint_as_float(l2[c])) *
-                                      0.00390625 +
-                                  (double)__uint_as_float(l1[c])) *
-                                     0.00390625 +
-                                 (double)__uint_as_float(l0[c]);
-                acc[8 * h + c] += sc * v;
+                // the tiles hold integers below 2^24: exact in int64 as 2^24 L0 + 2^16 L1 + 2^8 L2 + L3
+                const long long v = ((long long)__float2int_rn(__uint_as_float(l0[c])) << 24) +
+                                    ((long long)__float2int_rn(__uint_as_float(l1[c])) << 16) +
+                                    ((long long)__float2int_rn(__uint_as_float(l2[c])) << 8) +
+                                    (long long)__float2int_rn(__uint_as_float(l3[c]));
+                // s_m s_n 2^-38 = 2^(ea - 1022 + eb - 1022 - 38); zero rows have exponent field 0
+                // (a scale below the normal range -- rows of magnitude ~1e-150 -- counts as zero)
+                const double sc = (ea == 0 || eb == 0 || ea + eb < 1060) ? 0.0
+                                                                          : __hiloint2double((ea + eb - 1059) << 20, 0);
+                acc[8 * h + c] = fma(sc, (double)v, acc[8 * h + c]);
             }
         }
         // the next chunk's MMAs rewrite tensor memory and its loads the shared tiles and exponents
