@@ -90,8 +90,11 @@ typedef struct {
                                   SM; 3 = two columns per thread, up to 384 threads.  4 = one fused
                                   kernel per iteration, one block per system with whole xy planes in
                                   a shared-memory ring (grids whose nx*ny plane fits, about 2000
-                                  points; else as 1).  0 = automatic: 4 where it fits, else 1.
-                                  rpa_autotune sets it.  The plain FP64 form always uses 1. */
+                                  points; else as 1).  5 = the fused kernel warp-specialised: producer
+                                  threads form the next plane while consumer threads apply the
+                                  stencil (planes of up to ~416 blocks of 2 x 2 points; else as 4).
+                                  0 = automatic: 4 where it fits, else 1.  rpa_autotune sets it.  The
+                                  plain FP64 form always uses 1. */
     int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
@@ -250,14 +253,15 @@ rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *i
                                      int ncols, void *stream);
 
 /* Number of configurations rpa_autotune times. */
-#define RPA_AUTOTUNE_CANDIDATES 7
+#define RPA_AUTOTUNE_CANDIDATES 8
 
 /* Autotuner: times one application of nu^1/2 chi0(i omega) nu^1/2 to the n_r columns of V_dev
  * for each candidate configuration of the COCG kernels and keeps the fastest for this context by
  * setting its stencil_shape and z_chunks options.  Candidates 0..5: the two-kernel variants
  * stencil_shape = 1, 2, 3 (columns per thread and threads per block, i.e. the xy tile shape)
  * crossed with one or two z chunks per column, index 2 (stencil_shape - 1) + (z_chunks - 1);
- * candidate 6: the fused single-pass kernel (stencil_shape 4).  The plain FP64 form has one
+ * candidate 6: the fused single-pass kernel (stencil_shape 4); candidate 7: its warp-specialised
+ * form (stencil_shape 5).  The plain FP64 form has one
  * configuration (candidate 0).  times_ms_host (may be NULL) receives RPA_AUTOTUNE_CANDIDATES
  * timings, -1 for a candidate that does not apply; *chosen_host (may be NULL) the index of the
  * chosen one.  The context's results do not depend on the choice beyond rounding. */

@@ -157,7 +157,7 @@ void validate_options(const rpa_options &o) {
     if (o.n_atoms < 1) fail(RPA_ERR_INVALID, "n_atoms must be >= 1");
     if (o.batch_systems < 0) fail(RPA_ERR_INVALID, "batch_systems must be >= 0");
     if (o.z_chunks < 0 || o.z_chunks > 64) fail(RPA_ERR_INVALID, "z_chunks must be in [0, 64]");
-    if (o.stencil_shape < 0 || o.stencil_shape > 4) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 4]");
+    if (o.stencil_shape < 0 || o.stencil_shape > 5) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 5]");
     if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
     if (o.contractions < 0 || o.contractions > 3) fail(RPA_ERR_INVALID, "contractions must be in [0, 3]");
     if (o.omega_count < 0 || o.omega_first < 0 || (o.omega_count > 0 && o.omega_first + o.omega_count > o.n_omega) ||
@@ -467,20 +467,22 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         double *t2 = (double *)c.blockB.ensure(blk);
         double *R = (double *)c.blockC.ensure(blk);
         // candidates 0..5: split kernel variant v (stencil_shape v + 1) with z chunks z + 1, index
-        // 2 v + z; candidate 6: the fused single-pass kernel (stencil_shape 4), where a plane fits
+        // 2 v + z; candidate 6: the fused single-pass kernel (stencil_shape 4), candidate 7 its
+        // warp-specialised form (stencil_shape 5), where a plane fits
         const bool mixed = c.opt.prec == RPA_MIXED;
         const bool fused_ok = mixed && fused_kernel_applies(c);
+        const bool ws_ok = mixed && fused_kernel_applies(c, true);
         double best = 1e300;
         int best_i = 0;
         cudaEvent_t a, b;
         RPA_CUDA(cudaEventCreate(&a));
         RPA_CUDA(cudaEventCreate(&b));
         for (int i = 0; i < RPA_AUTOTUNE_CANDIDATES; ++i) {
-            const bool run = i == 6 ? fused_ok : (mixed || i == 0);
+            const bool run = i == 7 ? ws_ok : i == 6 ? fused_ok : (mixed || i == 0);
             double ms = -1.0;
             if (run) {
-                c.opt.stencil_shape = i == 6 ? 4 : i / 2 + 1;
-                c.opt.z_chunks = i == 6 ? 1 : i % 2 + 1;
+                c.opt.stencil_shape = i >= 6 ? i - 2 : i / 2 + 1;
+                c.opt.z_chunks = i >= 6 ? 1 : i % 2 + 1;
                 RPA_CUDA(cudaEventRecord(a, s));
                 apply_nuchi0_impl(c, omega, V_dev, R, n_r, 1, t1, t2, s);
                 RPA_CUDA(cudaEventRecord(b, s));
@@ -498,8 +500,8 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         enqueue_status_readback(c, s);
         sync_stream(c, s);
         finish_call(c, s);
-        c.opt.stencil_shape = best_i == 6 ? 4 : best_i / 2 + 1;
-        c.opt.z_chunks = best_i == 6 ? 1 : best_i % 2 + 1;
+        c.opt.stencil_shape = best_i >= 6 ? best_i - 2 : best_i / 2 + 1;
+        c.opt.z_chunks = best_i >= 6 ? 1 : best_i % 2 + 1;
         if (chosen_host) *chosen_host = best_i;
     });
 }

@@ -818,6 +818,7 @@ __global__ void __launch_bounds__(MAXT, 1)
 constexpr int kRingPlanes = 14;
 constexpr int kRingPad = 6;
 constexpr int kRingMaxThreads = 512;
+constexpr int kRingWsMaxThreads = 672;     // consumers + producers (planes of up to 416 units)
 
 struct RingArgs {
     Slot *slots;
@@ -925,6 +926,211 @@ __device__ __forceinline__ void ring_pair(const unsigned char *addr, float2 &a, 
     b = make_float2(t.z, t.w);
 }
 
+// A unit of the fused kernels: the 2 x 2 points (x, x+1; y, y+1) of a plane, x and y even.
+struct RingUnit {
+    bool own, hasb, row1;          // a unit of the plane; point x+1 and row y+1 inside the box
+    int gy, col0, col1;            // row; in-plane indices of (x, y) and (x, y+1)
+    int rb0, rb1, rb1z;            // ring byte offsets of rows y and y+1 (rb1z: 0 if row y+1 is outside)
+};
+
+__device__ __forceinline__ RingUnit ring_unit(int u, const RingArgs &A) {
+    RingUnit r;
+    r.own = u >= 0 && u < A.hw * A.hh;
+    const int by = r.own ? u / A.hw : 0;
+    const int gx = r.own ? 2 * (u - by * A.hw) : 0;
+    r.gy = 2 * by;
+    r.hasb = r.own && gx + 1 < A.nx;
+    r.row1 = r.own && r.gy + 1 < A.ny;
+    r.col0 = r.gy * A.nx + gx;
+    r.col1 = r.col0 + A.nx;
+    r.rb0 = r.gy * A.rs * 8 + (kRingPad + gx) * 8;
+    r.rb1 = r.rb0 + A.rs * 8;
+    r.rb1z = r.row1 ? r.rb1 : 0;
+    return r;
+}
+
+// Raw values of a unit at a front plane: x, r, p, q of its four points (points outside the box
+// stay zero; x, p, q are not needed at the first pass).
+struct RingFront {
+    float2 x[4], r[4], p[4], q[4];
+};
+
+template <bool EVEN>
+__device__ __forceinline__ void ring_load_front(const RingUnit &U, int g0, bool first, const float2 *xs,
+                                                const float2 *rsv, const float2 *psv, const float2 *qs,
+                                                RingFront &F) {
+    const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) F.x[i] = F.r[i] = F.p[i] = F.q[i] = zero;
+    const int g1 = g0 + (U.col1 - U.col0);
+    ld_pair<EVEN>(rsv, g0, U.hasb, F.r[0], F.r[1]);
+    if (U.row1) ld_pair<EVEN>(rsv, g1, U.hasb, F.r[2], F.r[3]);
+    if (!first) {
+        ld_pair<EVEN>(xs, g0, U.hasb, F.x[0], F.x[1]);
+        ld_pair<EVEN>(psv, g0, U.hasb, F.p[0], F.p[1]);
+        ld_pair<EVEN>(qs, g0, U.hasb, F.q[0], F.q[1]);
+        if (U.row1) {
+            ld_pair<EVEN>(xs, g1, U.hasb, F.x[2], F.x[3]);
+            ld_pair<EVEN>(psv, g1, U.hasb, F.p[2], F.p[3]);
+            ld_pair<EVEN>(qs, g1, U.hasb, F.q[2], F.q[3]);
+        }
+    }
+}
+
+// Front plane f of a unit: x_k, r_k, p_k from the raw values, written back, and p_k into the ring
+// slot at `slot` (zeros for planes past the box); sums rho = r_k^T r_k and ||r_k||^2 (acc[0..2]).
+template <bool EVEN>
+__device__ __forceinline__ void ring_front(const RingUnit &U, int f, int nz, int plane, bool first, float alr,
+                                           float ali, float ber, float bei, const RingFront &F, float2 *xs,
+                                           float2 *rsv, float2 *psv, unsigned char *slot, float (&acc)[3]) {
+    const float2 zero = make_float2(0.f, 0.f);
+    float2 pk[4] = {zero, zero, zero, zero};
+    if (f < nz) {
+        const int g0 = f * plane + U.col0, g1 = f * plane + U.col1;
+        float2 rr[4];
+        if (first) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) rr[i] = pk[i] = F.r[i];
+        } else {
+            const float2 A1 = make_float2(alr, alr), A2 = make_float2(-ali, ali);
+            const float2 N1 = make_float2(-alr, -alr), N2 = make_float2(ali, -ali);
+            const float2 B1 = make_float2(ber, ber), B2 = make_float2(-bei, bei);
+            float2 xx[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                xx[i] = cax(F.x[i], A1, A2, F.p[i]);
+                rr[i] = cax(F.r[i], N1, N2, F.q[i]);
+                pk[i] = cax(rr[i], B1, B2, F.p[i]);
+            }
+            st_pair<EVEN>(xs, g0, U.hasb, xx[0], xx[1]);
+            st_pair<EVEN>(rsv, g0, U.hasb, rr[0], rr[1]);
+            if (U.row1) {
+                st_pair<EVEN>(xs, g1, U.hasb, xx[2], xx[3]);
+                st_pair<EVEN>(rsv, g1, U.hasb, rr[2], rr[3]);
+            }
+        }
+        if (!U.hasb) pk[1] = pk[3] = zero;
+        if (!U.row1) pk[2] = pk[3] = zero;
+        st_pair<EVEN>(psv, g0, U.hasb, pk[0], pk[1]);
+        if (U.row1) st_pair<EVEN>(psv, g1, U.hasb, pk[2], pk[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool in = (i & 1 ? U.hasb : true) && (i & 2 ? U.row1 : true);
+            if (in) {
+                cdot(acc[0], acc[1], rr[i], rr[i]);
+                acc[2] = fmaf(rr[i].x, rr[i].x, fmaf(rr[i].y, rr[i].y, acc[2]));
+            }
+        }
+    }
+    *reinterpret_cast<float4 *>(slot + U.rb0) = make_float4(pk[0].x, pk[0].y, pk[1].x, pk[1].y);
+    if (U.row1) *reinterpret_cast<float4 *>(slot + U.rb1) = make_float4(pk[2].x, pk[2].y, pk[3].x, pk[3].y);
+}
+
+// r_k and V of a unit at plane z (r_k written at the step that formed plane z).
+template <bool EVEN>
+__device__ __forceinline__ void ring_load_rv(const RingUnit &U, int g0, const float2 *rsv, const float *vloc,
+                                             float2 (&rk)[4], float (&vv)[4]) {
+    const int g1 = g0 + (U.col1 - U.col0);
+    ld_pair<EVEN>(rsv, g0, U.hasb, rk[0], rk[1]);
+    vv[0] = vloc[g0];
+    vv[1] = U.hasb ? vloc[g0 + 1] : 0.f;
+    if (U.row1) {
+        ld_pair<EVEN>(rsv, g1, U.hasb, rk[2], rk[3]);
+        vv[2] = vloc[g1];
+        vv[3] = U.hasb ? vloc[g1 + 1] : 0.f;
+    }
+}
+
+// q_k = (H + sigma) p_k on plane z for a unit, from the ring (cz: the ring slot of plane z), stored;
+// sums pi = p_k^T q_k, tau = r_k^T q_k, theta = q_k^T q_k (acc[0..5]).
+template <bool EVEN>
+__device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned char *ring, int psb, int rsb, int ny,
+                                             int cz, int gq0, const float2 (&rk)[4], const float (&vv)[4], float shr,
+                                             float shi, const Coef<float> &cf, float2 *qs, float (&acc)[6]) {
+    const float2 zero = make_float2(0.f, 0.f);
+    const unsigned char *const pz = ring + cz * psb;
+    const float2 c0 = make_float2(3.f * cf.a[0], 3.f * cf.a[0]);
+    const float2 SH = make_float2(shr, shr), SI = make_float2(-shi, shi);
+    // centre and x neighbours of one row: 7 16-byte loads (positions x-6 .. x+7)
+    auto xrow = [&](const unsigned char *pr, float va, float vb, float2 &ca, float2 &cb, float2 &qa, float2 &qb) {
+        float4 X[7];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) X[m] = *reinterpret_cast<const float4 *>(pr - 48 + 16 * m);
+        auto xat = [&](int o) -> float2 {
+            const float4 t = X[(o + 6) >> 1];
+            return ((o + 6) & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
+        };
+        ca = xat(0);
+        cb = xat(1);
+        qa = __ffma2_rn(SI, swp(ca), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(va, va))), ca));
+        qb = __ffma2_rn(SI, swp(cb), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(vb, vb))), cb));
+#pragma unroll
+        for (int d = 1; d <= kRadius; ++d) {
+            const float2 cd = make_float2(cf.a[d], cf.a[d]);
+            qa = __ffma2_rn(cd, __fadd2_rn(xat(-d), xat(d)), qa);
+            qb = __ffma2_rn(cd, __fadd2_rn(xat(1 - d), xat(1 + d)), qb);
+        }
+    };
+    float2 c0_, c1_, c2_, c3_, q0, q1, q2, q3;
+    xrow(pz + U.rb0, vv[0], vv[1], c0_, c1_, q0, q1);
+    // row y+1 outside the box (odd ny): its values are zero neighbours of row y, and its own q is
+    // discarded (the loads repeat row y, an address inside the plane)
+    xrow(pz + (U.row1 ? U.rb1 : U.rb0), vv[2], vv[3], c2_, c3_, q2, q3);
+    if (!U.row1) c2_ = c3_ = zero;
+    // y neighbours: rows y-6 .. y-1 and y+2 .. y+7 from the ring (the plane's first 16 bytes are
+    // padding, i.e. zero, and stand for rows outside the box); rows y and y+1 are the centres
+#pragma unroll
+    for (int d = 1; d <= kRadius; ++d) {
+        float2 u0, u1, l0, l1;              // rows y-d and y+1+d
+        ring_pair(pz + (U.gy - d >= 0 ? U.rb0 - d * rsb : 0), u0, u1);
+        ring_pair(pz + (U.gy + 1 + d < ny ? U.rb1 + d * rsb : 0), l0, l1);
+        float2 dn0, dn1, up0, up1;          // row y+d (for row y), row y+1-d (for row y+1)
+        if (d == 1) {
+            dn0 = c2_;
+            dn1 = c3_;
+            up0 = c0_;
+            up1 = c1_;
+        } else {
+            ring_pair(pz + (U.gy + d < ny ? U.rb0 + d * rsb : 0), dn0, dn1);
+            ring_pair(pz + (U.gy + 1 - d >= 0 ? U.rb1 - d * rsb : 0), up0, up1);
+        }
+        const int sm = cz >= d ? cz - d : cz + kRingPlanes - d;
+        const int sp = cz + d < kRingPlanes ? cz + d : cz + d - kRingPlanes;
+        float2 zm0, zm1, zm2, zm3, zp0, zp1, zp2, zp3;
+        ring_pair(ring + sm * psb + U.rb0, zm0, zm1);
+        ring_pair(ring + sp * psb + U.rb0, zp0, zp1);
+        ring_pair(ring + sm * psb + U.rb1z, zm2, zm3);   // row y+1 outside the box: padding
+        ring_pair(ring + sp * psb + U.rb1z, zp2, zp3);
+        const float2 cd = make_float2(cf.a[d], cf.a[d]);
+        q0 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u0, dn0), __fadd2_rn(zm0, zp0)), q0);
+        q1 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u1, dn1), __fadd2_rn(zm1, zp1)), q1);
+        q2 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up0, l0), __fadd2_rn(zm2, zp2)), q2);
+        q3 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up1, l1), __fadd2_rn(zm3, zp3)), q3);
+    }
+    st_pair<EVEN>(qs, gq0, U.hasb, q0, q1);
+    if (U.row1) st_pair<EVEN>(qs, gq0 + (U.col1 - U.col0), U.hasb, q2, q3);
+    cdot(acc[0], acc[1], c0_, q0);
+    cdot(acc[2], acc[3], rk[0], q0);
+    cdot(acc[4], acc[5], q0, q0);
+    if (U.hasb) {
+        cdot(acc[0], acc[1], c1_, q1);
+        cdot(acc[2], acc[3], rk[1], q1);
+        cdot(acc[4], acc[5], q1, q1);
+    }
+    if (U.row1) {
+        cdot(acc[0], acc[1], c2_, q2);
+        cdot(acc[2], acc[3], rk[2], q2);
+        cdot(acc[4], acc[5], q2, q2);
+        if (U.hasb) {
+            cdot(acc[0], acc[1], c3_, q3);
+            cdot(acc[2], acc[3], rk[3], q3);
+            cdot(acc[4], acc[5], q3, q3);
+        }
+    }
+}
+
+// The fused kernel: every thread takes one unit through both phases of a step (front, then the
+// stencil six planes behind), the front's loads for the next plane in flight during the stencil.
 template <bool EVEN>
 __global__ void __launch_bounds__(kRingMaxThreads, 1)
     k_cocg_ring(RingArgs A, float2 *__restrict__ xg, float2 *__restrict__ rg, float2 *__restrict__ pg,
@@ -932,23 +1138,12 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
     extern __shared__ float4 ring4[];
     unsigned char *const ring = reinterpret_cast<unsigned char *>(ring4);
     const int tid = threadIdx.x;
-    const int nx = A.nx, ny = A.ny, nz = A.nz, hw = A.hw;
-    const int plane = nx * ny;                     // grid functions have < 2^31 points
+    const int nz = A.nz, plane = A.nx * A.ny;      // grid functions have < 2^31 points
     const int rsb = A.rs * 8, psb = A.ps * 8;      // ring row / plane strides in bytes
-    const bool own = tid < hw * A.hh;
-    const int by = own ? tid / hw : 0;
-    const int gx = own ? 2 * (tid - by * hw) : 0, gy = 2 * by;
-    const bool hasb = own && gx + 1 < nx;          // point (x+1) lies in the box (odd nx)
-    const bool row1 = own && gy + 1 < ny;          // row y+1 lies in the box (odd ny)
-    const int col0 = gy * nx + gx, col1 = col0 + nx;          // in-plane index of (x, y), (x, y+1)
-    const int rb0 = gy * rsb + (kRingPad + gx) * 8;           // ring byte offsets of the two pairs
-    const int rb1 = rb0 + rsb;
-    const int rb1z = row1 ? rb1 : 0;               // row y+1, or the (zero) start of the plane
-    const float2 zero = make_float2(0.f, 0.f);
+    const RingUnit U = ring_unit(tid, A);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (blockIdx.x == 0 && tid == 0) *A.cnt_clear = 0;
     for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
-    const float2 c0 = make_float2(3.f * cf.a[0], 3.f * cf.a[0]);
     const int n_items = *A.cnt_in;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int s = A.list_in[it];
@@ -963,198 +1158,123 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
         float2 *const psv = pg + off;
         float2 *const qs = qg + off;
         __syncthreads();                           // the previous item's ring readers are done
-        if (own) {                                 // planes -6 .. -1 (ring slots 8 .. 13) are zero
+        if (U.own) {                               // planes -6 .. -1 (ring slots 8 .. 13) are zero
 #pragma unroll
             for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
-                *reinterpret_cast<float4 *>(ring + m * psb + rb0) = zero4;
-                if (row1) *reinterpret_cast<float4 *>(ring + m * psb + rb1) = zero4;
+                *reinterpret_cast<float4 *>(ring + m * psb + U.rb0) = zero4;
+                if (U.row1) *reinterpret_cast<float4 *>(ring + m * psb + U.rb1) = zero4;
             }
         }
-        // raw front of plane 0 (x, r, p, q of rows y and y+1)
-        float2 fx[4], fr[4], fp[4], fq[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) fx[i] = fr[i] = fp[i] = fq[i] = zero;
-        if (own) {
-            ld_pair<EVEN>(rsv, col0, hasb, fr[0], fr[1]);
-            if (row1) ld_pair<EVEN>(rsv, col1, hasb, fr[2], fr[3]);
-            if (!first) {
-                ld_pair<EVEN>(xs, col0, hasb, fx[0], fx[1]);
-                ld_pair<EVEN>(psv, col0, hasb, fp[0], fp[1]);
-                ld_pair<EVEN>(qs, col0, hasb, fq[0], fq[1]);
-                if (row1) {
-                    ld_pair<EVEN>(xs, col1, hasb, fx[2], fx[3]);
-                    ld_pair<EVEN>(psv, col1, hasb, fp[2], fp[3]);
-                    ld_pair<EVEN>(qs, col1, hasb, fq[2], fq[3]);
-                }
-            }
-        }
-        float a_rho_r = 0.f, a_rho_i = 0.f, a_nr = 0.f, a_pi_r = 0.f, a_pi_i = 0.f;
-        float a_tau_r = 0.f, a_tau_i = 0.f, a_th_r = 0.f, a_th_i = 0.f;
+        RingFront F;
+        if (U.own) ring_load_front<EVEN>(U, U.col0, first, xs, rsv, psv, qs, F);   // front plane 0
+        float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const int nsteps = nz + kRadius;
         // rolled loop: unrolled over the ring (compile-time slots) it needs far more registers
         for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
-            // r_k and V of the stencil's plane z = f - 6 (r_k written at step z), in flight during the
-            // front and the barrier
+            // r_k and V of the stencil's plane z = f - 6, in flight during the front and the barrier
             const int z = f - kRadius;
-            float2 rk[4] = {zero, zero, zero, zero};
+            float2 rk[4] = {};
             float vv[4] = {0.f, 0.f, 0.f, 0.f};
-            if (own && z >= 0) {
-                const int g0 = z * plane + col0, g1 = g0 + nx;
-                ld_pair<EVEN>(rsv, g0, hasb, rk[0], rk[1]);
-                vv[0] = vloc[g0];
-                vv[1] = hasb ? vloc[g0 + 1] : 0.f;
-                if (row1) {
-                    ld_pair<EVEN>(rsv, g1, hasb, rk[2], rk[3]);
-                    vv[2] = vloc[g1];
-                    vv[3] = hasb ? vloc[g1 + 1] : 0.f;
-                }
-            }
-            // 1. front plane f: x_k, r_k, p_k of the 2 x 2 points, p_k into ring slot u
-            float2 pk[4] = {zero, zero, zero, zero};
-            if (own && f < nz) {
-                float2 rr[4];
-                if (first) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) rr[i] = pk[i] = fr[i];
-                } else {
-                    const float2 A1 = make_float2(alr, alr), A2 = make_float2(-ali, ali);
-                    const float2 N1 = make_float2(-alr, -alr), N2 = make_float2(ali, -ali);
-                    const float2 B1 = make_float2(ber, ber), B2 = make_float2(-bei, bei);
-                    float2 xx[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        xx[i] = cax(fx[i], A1, A2, fp[i]);
-                        rr[i] = cax(fr[i], N1, N2, fq[i]);
-                        pk[i] = cax(rr[i], B1, B2, fp[i]);
-                    }
-                    st_pair<EVEN>(xs, f * plane + col0, hasb, xx[0], xx[1]);
-                    st_pair<EVEN>(rsv, f * plane + col0, hasb, rr[0], rr[1]);
-                    if (row1) {
-                        st_pair<EVEN>(xs, f * plane + col1, hasb, xx[2], xx[3]);
-                        st_pair<EVEN>(rsv, f * plane + col1, hasb, rr[2], rr[3]);
-                    }
-                }
-                if (!hasb) pk[1] = pk[3] = zero;
-                if (!row1) pk[2] = pk[3] = zero;
-                st_pair<EVEN>(psv, f * plane + col0, hasb, pk[0], pk[1]);
-                if (row1) st_pair<EVEN>(psv, f * plane + col1, hasb, pk[2], pk[3]);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const bool in = (i & 1 ? hasb : true) && (i & 2 ? row1 : true);
-                    if (in) {
-                        cdot(a_rho_r, a_rho_i, rr[i], rr[i]);
-                        a_nr = fmaf(rr[i].x, rr[i].x, fmaf(rr[i].y, rr[i].y, a_nr));
-                    }
-                }
-            }
-            if (own) {
-                *reinterpret_cast<float4 *>(ring + u * psb + rb0) = make_float4(pk[0].x, pk[0].y, pk[1].x, pk[1].y);
-                if (row1) *reinterpret_cast<float4 *>(ring + u * psb + rb1) = make_float4(pk[2].x, pk[2].y, pk[3].x, pk[3].y);
-            }
+            if (U.own && z >= 0) ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
+            // 1. front plane f, p_k into ring slot u
+            if (U.own) ring_front<EVEN>(U, f, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring + u * psb, fa);
             // 2. the next front plane, in flight during the stencil below
-            if (own) {
-                if (f + 1 < nz) {
-                    const int g0 = (f + 1) * plane + col0, g1 = g0 + nx;
-                    ld_pair<EVEN>(rsv, g0, hasb, fr[0], fr[1]);
-                    if (row1) ld_pair<EVEN>(rsv, g1, hasb, fr[2], fr[3]);
-                    if (!first) {
-                        ld_pair<EVEN>(xs, g0, hasb, fx[0], fx[1]);
-                        ld_pair<EVEN>(psv, g0, hasb, fp[0], fp[1]);
-                        ld_pair<EVEN>(qs, g0, hasb, fq[0], fq[1]);
-                        if (row1) {
-                            ld_pair<EVEN>(xs, g1, hasb, fx[2], fx[3]);
-                            ld_pair<EVEN>(psv, g1, hasb, fp[2], fp[3]);
-                            ld_pair<EVEN>(qs, g1, hasb, fq[2], fq[3]);
-                        }
+            if (U.own && f + 1 < nz) ring_load_front<EVEN>(U, (f + 1) * plane + U.col0, first, xs, rsv, psv, qs, F);
+            __syncthreads();
+            // 3. q_k on plane z, its 6 neighbour planes from the ring
+            if (U.own && z >= 0) {
+                const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
+                ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs, sa);
+            }
+        }
+        double v[9] = {fa[0], fa[1], fa[2], sa[0], sa[1], sa[2], sa[3], sa[4], sa[5]};
+        block_sum_any<9>(v);
+        if (tid == 0) {
+            ring_scalar_step(A, sl, s, v);
+            if (A.prof) atomicAdd(A.prof + 1, (unsigned long long)A.nd);
+        }
+    }
+}
+
+// Warp-specialised form of the fused kernel: the first threads (consumers, one unit each) apply
+// the stencil to plane f-6 while the threads after them (producers, two units each, one after the
+// other) form plane f+1, so the front's global-memory latency and the stencil's shared-memory work
+// overlap.  The producers
+// write the ring slot of plane f-13 during step f, which no consumer reads at that step (they
+// read f-12 .. f), and one barrier per step hands the planes over.
+template <bool EVEN>
+__global__ void __maxnreg__(96)
+    k_cocg_ring_ws(RingArgs A, float2 *__restrict__ xg, float2 *__restrict__ rg, float2 *__restrict__ pg,
+                   float2 *__restrict__ qg, const float *__restrict__ vloc, Coef<float> cf) {
+    extern __shared__ float4 ring4[];
+    unsigned char *const ring = reinterpret_cast<unsigned char *>(ring4);
+    const int tid = threadIdx.x;
+    const int nz = A.nz, plane = A.nx * A.ny;
+    const int rsb = A.rs * 8, psb = A.ps * 8;
+    const int nunits = A.hw * A.hh;
+    const int ncons = (nunits + 31) / 32 * 32;     // consumer threads; the rest produce
+    const int nprod = ((nunits + 1) / 2 + 31) / 32 * 32;
+    const bool producer = tid >= ncons;
+    const int pt = tid - ncons;                    // producer index: units pt and pt + nprod
+    const RingUnit U = ring_unit(producer ? -1 : tid, A);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (blockIdx.x == 0 && tid == 0) *A.cnt_clear = 0;
+    for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
+    const int n_items = *A.cnt_in;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int s = A.list_in[it];
+        Slot &sl = A.slots[s];
+        const bool first = sl.iters == 0;
+        const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
+        const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
+        const float shr = (float)sl.shift_re, shi = (float)sl.shift_im;
+        const long long off = (long long)s * A.nd;
+        float2 *const xs = xg + off;
+        float2 *const rsv = rg + off;
+        float2 *const psv = pg + off;
+        float2 *const qs = qg + off;
+        float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        __syncthreads();                           // the previous item's ring readers are done
+        if (producer)                              // planes -6 .. -1 (ring slots 8 .. 13) are zero; plane 0
+            for (int pu = pt; pu < nunits; pu += nprod) {
+                const RingUnit P = ring_unit(pu, A);
+#pragma unroll
+                for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                    *reinterpret_cast<float4 *>(ring + m * psb + P.rb0) = zero4;
+                    if (P.row1) *reinterpret_cast<float4 *>(ring + m * psb + P.rb1) = zero4;
+                }
+                RingFront F;
+                ring_load_front<EVEN>(P, P.col0, first, xs, rsv, psv, qs, F);
+                ring_front<EVEN>(P, 0, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring, fa);
+            }
+        __syncthreads();
+        const int nsteps = nz + kRadius;
+        for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
+            if (producer) {
+                // plane f + 1 into ring slot u + 1
+                if (f + 1 < nsteps) {
+                    const int un = u + 1 == kRingPlanes ? 0 : u + 1;
+                    for (int pu = pt; pu < nunits; pu += nprod) {
+                        const RingUnit P = ring_unit(pu, A);
+                        RingFront F;
+                        if (f + 1 < nz) ring_load_front<EVEN>(P, (f + 1) * plane + P.col0, first, xs, rsv, psv, qs, F);
+                        ring_front<EVEN>(P, f + 1, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv,
+                                         ring + un * psb, fa);
                     }
+                }
+            } else {
+                const int z = f - kRadius;
+                if (U.own && z >= 0) {
+                    float2 rk[4] = {};
+                    float vv[4] = {0.f, 0.f, 0.f, 0.f};
+                    ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
+                    const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;
+                    ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs, sa);
                 }
             }
             __syncthreads();
-            // 3. q_k = (H + sigma) p_k on plane z, its 6 neighbour planes from the ring
-            if (own && z >= 0) {
-                const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
-                const unsigned char *const pz = ring + cz * psb;
-                const float2 SH = make_float2(shr, shr), SI = make_float2(-shi, shi);
-                // centre and x neighbours of one row: 7 16-byte loads (positions x-6 .. x+7)
-                auto xrow = [&](const unsigned char *pr, float va, float vb, float2 &ca, float2 &cb, float2 &qa,
-                                float2 &qb) {
-                    float4 X[7];
-#pragma unroll
-                    for (int m = 0; m < 7; ++m) X[m] = *reinterpret_cast<const float4 *>(pr - 48 + 16 * m);
-                    auto xat = [&](int o) -> float2 {
-                        const float4 t = X[(o + 6) >> 1];
-                        return ((o + 6) & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
-                    };
-                    ca = xat(0);
-                    cb = xat(1);
-                    qa = __ffma2_rn(SI, swp(ca), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(va, va))), ca));
-                    qb = __ffma2_rn(SI, swp(cb), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(vb, vb))), cb));
-#pragma unroll
-                    for (int d = 1; d <= kRadius; ++d) {
-                        const float2 cd = make_float2(cf.a[d], cf.a[d]);
-                        qa = __ffma2_rn(cd, __fadd2_rn(xat(-d), xat(d)), qa);
-                        qb = __ffma2_rn(cd, __fadd2_rn(xat(1 - d), xat(1 + d)), qb);
-                    }
-                };
-                float2 c0_, c1_, c2_, c3_, q0, q1, q2, q3;
-                xrow(pz + rb0, vv[0], vv[1], c0_, c1_, q0, q1);
-                // row y+1 outside the box (odd ny): its values are zero neighbours of row y, and its
-                // own q is discarded (the loads repeat row y, an address inside the plane)
-                xrow(pz + (row1 ? rb1 : rb0), vv[2], vv[3], c2_, c3_, q2, q3);
-                if (!row1) c2_ = c3_ = zero;
-                // y neighbours: rows y-6 .. y-1 and y+2 .. y+7 from the ring (the plane's first 16
-                // bytes are padding, i.e. zero, and stand for rows outside the box); rows y and
-                // y+1 are the centres above
-#pragma unroll
-                for (int d = 1; d <= kRadius; ++d) {
-                    float2 u0, u1, l0, l1;              // rows y-d and y+1+d
-                    ring_pair(pz + (gy - d >= 0 ? rb0 - d * rsb : 0), u0, u1);
-                    ring_pair(pz + (gy + 1 + d < ny ? rb1 + d * rsb : 0), l0, l1);
-                    // row y at distance d: rows y-d and y+d; row y+1: rows y+1-d and y+1+d
-                    float2 dn0, dn1, up0, up1;          // row y+d (for row y), row y+1-d (for row y+1)
-                    if (d == 1) {
-                        dn0 = c2_; dn1 = c3_;         // row y+1
-                        up0 = c0_; up1 = c1_;         // row y
-                    } else {
-                        ring_pair(pz + (gy + d < ny ? rb0 + d * rsb : 0), dn0, dn1);
-                        ring_pair(pz + (gy + 1 - d >= 0 ? rb1 - d * rsb : 0), up0, up1);
-                    }
-                    const int sm = cz >= d ? cz - d : cz + kRingPlanes - d;
-                    const int sp = cz + d < kRingPlanes ? cz + d : cz + d - kRingPlanes;
-                    float2 zm0, zm1, zm2, zm3, zp0, zp1, zp2, zp3;
-                    ring_pair(ring + sm * psb + rb0, zm0, zm1);
-                    ring_pair(ring + sp * psb + rb0, zp0, zp1);
-                    ring_pair(ring + sm * psb + rb1z, zm2, zm3);  // row y+1 outside the box: padding
-                    ring_pair(ring + sp * psb + rb1z, zp2, zp3);
-                    const float2 cd = make_float2(cf.a[d], cf.a[d]);
-                    q0 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u0, dn0), __fadd2_rn(zm0, zp0)), q0);
-                    q1 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u1, dn1), __fadd2_rn(zm1, zp1)), q1);
-                    q2 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up0, l0), __fadd2_rn(zm2, zp2)), q2);
-                    q3 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up1, l1), __fadd2_rn(zm3, zp3)), q3);
-                }
-                st_pair<EVEN>(qs, z * plane + col0, hasb, q0, q1);
-                if (row1) st_pair<EVEN>(qs, z * plane + col1, hasb, q2, q3);
-                cdot(a_pi_r, a_pi_i, c0_, q0);
-                cdot(a_tau_r, a_tau_i, rk[0], q0);
-                cdot(a_th_r, a_th_i, q0, q0);
-                if (hasb) {
-                    cdot(a_pi_r, a_pi_i, c1_, q1);
-                    cdot(a_tau_r, a_tau_i, rk[1], q1);
-                    cdot(a_th_r, a_th_i, q1, q1);
-                }
-                if (row1) {
-                    cdot(a_pi_r, a_pi_i, c2_, q2);
-                    cdot(a_tau_r, a_tau_i, rk[2], q2);
-                    cdot(a_th_r, a_th_i, q2, q2);
-                    if (hasb) {
-                        cdot(a_pi_r, a_pi_i, c3_, q3);
-                        cdot(a_tau_r, a_tau_i, rk[3], q3);
-                        cdot(a_th_r, a_th_i, q3, q3);
-                    }
-                }
-            }
         }
-        double v[9] = {a_rho_r, a_rho_i, a_nr, a_pi_r, a_pi_i, a_tau_r, a_tau_i, a_th_r, a_th_i};
+        double v[9] = {fa[0], fa[1], fa[2], sa[0], sa[1], sa[2], sa[3], sa[4], sa[5]};
         block_sum_any<9>(v);
         if (tid == 0) {
             ring_scalar_step(A, sl, s, v);
@@ -1206,14 +1326,16 @@ using RingFn = void (*)(RingArgs, float2 *, float2 *, float2 *, float2 *, const 
 
 // The fused kernel applies when a plane's ring fits in a block's shared memory (beside the
 // kernel's static shared memory) and a plane has at most kRingMaxThreads blocks of 2 x 2 points.
-bool ring_fits(int nx, int ny, RingFn fn, int smem_optin) {
+bool ring_fits(int nx, int ny, RingFn fn, int smem_optin, bool ws = false) {
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    const long long blocks = (long long)((nx + 1) / 2) * ((ny + 1) / 2);
-    return blocks <= kRingMaxThreads && ring_bytes(nx, ny) + fa.sharedSizeBytes <= (size_t)smem_optin;
+    const long long units = (long long)((nx + 1) / 2) * ((ny + 1) / 2);
+    const long long threads = ws ? (units + 31) / 32 * 32 + ((units + 1) / 2 + 31) / 32 * 32 : units;
+    return threads <= (ws ? kRingWsMaxThreads : kRingMaxThreads) &&
+           ring_bytes(nx, ny) + fa.sharedSizeBytes <= (size_t)smem_optin;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2027,10 +2149,13 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     // rpa_options.stencil_shape: 0 = automatic (the fused kernel where a plane fits its ring, else
     // split variant 1), 1..3 = the split kernels' variants, 4 = the fused kernel (split variant 1
     // where a plane does not fit).  The plain FP64 form always runs the split kernels.
-    const int want = std::max(0, std::min(4, c.opt.stencil_shape));
+    const int want = std::max(0, std::min(5, c.opt.stencil_shape));
     const bool even_nx = (c.nx % 2) == 0;
-    const RingFn ring_fn = even_nx ? k_cocg_ring<true> : k_cocg_ring<false>;
-    const bool use_ring = mixed && (want == 0 || want == 4) && ring_fits(c.nx, c.ny, ring_fn, smem_optin);
+    const bool ws = want == 5 && ring_fits(c.nx, c.ny, even_nx ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>,
+                                           smem_optin, true);
+    const RingFn ring_fn = ws ? (even_nx ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>)
+                              : (even_nx ? k_cocg_ring<true> : k_cocg_ring<false>);
+    const bool use_ring = mixed && (want == 0 || want >= 4) && ring_fits(c.nx, c.ny, ring_fn, smem_optin, ws);
     const int variant = (want >= 1 && want <= 3) ? want - 1 : 0;
     const PaShape shape = mixed ? kPaShapes32[variant] : kPaShape64;
     Tiles tl = pick_tiles(c.nx, c.ny, shape.max_threads, shape.pairs != 0);
@@ -2176,7 +2301,11 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             ra[i] = a;
         }
         ring_smem = ring_bytes(c.nx, c.ny);
-        ring_threads = (unsigned)((hw * ((c.ny + 1) / 2) + 31) / 32 * 32);
+        {
+            const int units = hw * ((c.ny + 1) / 2);
+            ring_threads = (unsigned)((units + 31) / 32 * 32);
+            if (ws) ring_threads += (unsigned)(((units + 1) / 2 + 31) / 32 * 32);   // consumers + producers
+        }
         allow_dynamic_smem((const void *)ring_fn, ring_smem);
         int per_sm = 1;
         RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_fn, (int)ring_threads, ring_smem));
@@ -2189,7 +2318,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     char names[3][32];
     std::snprintf(names[0], 32, "-");
     if (use_ring) {
-        std::snprintf(names[1], 32, "k_cocg_ring<%s>", tn);
+        std::snprintf(names[1], 32, ws ? "k_cocg_ring_ws<%s>" : "k_cocg_ring<%s>", tn);
         std::snprintf(names[2], 32, "-");
     } else {
         std::snprintf(names[1], 32, "k_cocg_pa<%s>", tn);
@@ -2466,10 +2595,13 @@ void check_orbitals(const Ctx &c, const int *orb, int nsys) {
 
 }  // namespace
 
-bool fused_kernel_applies(const Ctx &c) {
+bool fused_kernel_applies(const Ctx &c, bool warp_specialised) {
     int smem_optin = 0;
     RPA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
-    return ring_fits(c.nx, c.ny, (c.nx % 2) == 0 ? k_cocg_ring<true> : k_cocg_ring<false>, smem_optin);
+    const bool even = (c.nx % 2) == 0;
+    if (warp_specialised)
+        return ring_fits(c.nx, c.ny, even ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>, smem_optin, true);
+    return ring_fits(c.nx, c.ny, even ? k_cocg_ring<true> : k_cocg_ring<false>, smem_optin);
 }
 
 int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

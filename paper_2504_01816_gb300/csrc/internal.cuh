@@ -193,7 +193,7 @@ void jacobi_eigh(std::vector<double> A, int n, std::vector<double> &w, std::vect
 
 // Whether the fused single-pass COCG kernel applies to this context's grid (a whole xy plane fits
 // its shared-memory ring); the mixed form then uses it by default.
-bool fused_kernel_applies(const Ctx &c);
+bool fused_kernel_applies(const Ctx &c, bool warp_specialised = false);
 
 // Same as sternheimer_batch, with b replaced by P_c b first.
 int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

@@ -296,7 +296,8 @@ class Context:
     AUTOTUNE_CANDIDATES = [f"split kernels, {shape}, {z} z chunk(s)"
                            for shape in ("1 column/thread <= 640 threads", "1 column/thread <= 320 threads x 2 blocks",
                                          "2 columns/thread <= 384 threads") for z in (1, 2)] + \
-                          ["fused single-pass kernel, whole planes in a shared-memory ring"]
+                          ["fused single-pass kernel, whole planes in a shared-memory ring",
+                           "fused single-pass kernel, warp-specialised (producer / consumer threads)"]
 
     def autotune(self, omega: float, V, stream=None):
         """rpa_autotune: time the COCG kernel configurations on this workload, keep the fastest.
@@ -308,8 +309,8 @@ class Context:
         _check(_lib.rpa_autotune(self._h, float(omega), _ptr(V), n_r, ctypes.byref(chosen), times, _stream(stream)))
         # the autotuner sets stencil_shape and z_chunks; keep the Python-side options in step
         i = chosen.value
-        self.options.stencil_shape = 4 if i == 6 else i // 2 + 1
-        self.options.z_chunks = 1 if i == 6 else i % 2 + 1
+        self.options.stencil_shape = i - 2 if i >= 6 else i // 2 + 1
+        self.options.z_chunks = 1 if i >= 6 else i % 2 + 1
         return i, self.AUTOTUNE_CANDIDATES, list(times)
 
     def ec_gradient(self, V0, want_subspace: bool = False, stream=None):

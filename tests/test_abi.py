@@ -84,7 +84,7 @@ def test_setup_rejects_bad_arguments_without_a_gpu(rpa):
     bad.n_omega = 0
     st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)
     assert st == rpa.RPA_ERR_INVALID and b"n_omega" in lib.rpa_last_error()
-    for field, value in (("sq_order", 33), ("stencil_shape", 5), ("z_chunks", -1), ("contractions", 4)):
+    for field, value in (("sq_order", 33), ("stencil_shape", 6), ("z_chunks", -1), ("contractions", 4)):
         lib.rpa_default_options(ctypes.byref(bad))
         setattr(bad, field, value)
         st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)

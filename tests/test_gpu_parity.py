@@ -200,8 +200,11 @@ def test_z_chunked_stencil_items_agree(rpa, zc):
         Rb, _ = ctx.apply_nuchi0(0.6, cuda(V))
         ctx.set_options(opts(rpa, stencil_shape=4, batch_systems=4, **o))
         Rc, _ = ctx.apply_nuchi0(0.6, cuda(V))
+        ctx.set_options(opts(rpa, stencil_shape=5, batch_systems=4, **o))
+        Rd, _ = ctx.apply_nuchi0(0.6, cuda(V))
     assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
     assert relerr(Rc.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
+    assert relerr(Rd.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
 
 
 @pytest.mark.parametrize("shape", [2, 3, 4])
@@ -222,7 +225,7 @@ def test_autotune_keeps_results(rpa, ragged):
     with rpa.Context.from_system(ragged, opts(rpa, tol=1e-12, prec=rpa.RPA_MIXED, contractions=1)) as ctx:
         Ra, _ = ctx.apply_nuchi0(0.5, cuda(V))
         chosen, names, times = ctx.autotune(0.5, cuda(V))
-        assert 0 <= chosen < 7 and all(t > 0 for t in times)   # the fused kernel applies on 13 x 11 planes
+        assert 0 <= chosen < 8 and all(t > 0 for t in times)   # the fused kernels apply on 13 x 11 planes
         Rb, _ = ctx.apply_nuchi0(0.5, cuda(V))
     assert relerr(Rb.cpu().numpy(), Ra.cpu().numpy()) < 1e-9
 
@@ -340,7 +343,7 @@ def test_lih72_sampled_column_matches_oracle(rpa):
 
 
 @pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11), (16, 5, 4)])
-@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
 def test_stencil_variants_match_oracle(rpa, shape, grid):
     """(70, 3, 9): two x tiles with side halos and more halo elements per plane than twice the
     block's threads (the split kernels' fallback halo loop), and rows of 35 point pairs in the
