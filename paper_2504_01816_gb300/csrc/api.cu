@@ -675,20 +675,14 @@ int ec_impl(Ctx &c, int n_r, const double *V0_dev, double *lambdas_host, double 
         ec += ecm;
         if (lambdas_host) std::memcpy(lambdas_host + (size_t)m * n_r, h_lam, sizeof(double) * n_r);
         if (grad) {
-            // Ritz pairs of the last iteration: C = Q diag(lambda) Q^T, y_i = sum_k Q[k][i] v_k
-            std::vector<double> Ch(nn), wv, Q;
-            RPA_CUDA(cudaMemcpyAsync(Ch.data(), Cprev, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
-            sync_stream(c, s);
-            jacobi_eigh(Ch, n_r, wv, Q);
-            std::vector<double> S(nn), coef(n_r);
-            for (int i = 0; i < n_r; ++i) {
-                coef[i] = wt[m] / (2.0 * M_PI) * (-wv[i] / (1.0 - wv[i]));   // (w_m / 2pi) g'(lambda_i)
-                for (int k = 0; k < n_r; ++k) S[(size_t)i * n_r + k] = Q[(size_t)k * n_r + i];
-            }
-            RPA_CUDA(cudaMemcpyAsync(Sm, S.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+            // Ritz pairs of the last iteration on the device: C = Q diag(lambda) Q^T (parallel Jacobi,
+            // C destroyed), y_i = sum_k Q[k][i] v_k, coef_i = (w_m / 2pi) g'(lambda_i)
+            double *coef = (double *)c.coef_buf.ensure(sizeof(double) * (4 * (size_t)n_r + 8));
+            jacobi_eigh_device(Cprev, n_r, Lm, work, coef + n_r, s);   // Q -> Lm, lambda -> work
+            ritz_rotation(Lm, work, n_r, wt[m] / (2.0 * M_PI), Sm, coef, s);
             combine_rows(Sm, n_r, n_r, Vprev, c.nd, T1, s);           // Ritz vectors
             coulomb_apply(c, 0.5, T1, T2, n_r, s);                    // nu^1/2 y_i
-            worst = std::max(worst, response_square(c, om[m], T2, coef.data(), grad, n_r, s));   // synchronises
+            worst = std::max(worst, response_square(c, om[m], T2, coef, grad, n_r, s));
             enqueue_status_readback(c, s);
             sync_stream(c, s);
             worst = std::max(worst, finish_call(c, s));

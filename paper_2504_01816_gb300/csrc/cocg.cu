@@ -2651,20 +2651,16 @@ static double *pair_coefficients(Ctx &c, const double *dv, int ncols, cudaStream
 int response_square(Ctx &c, double omega, const double *dv, const double *coef, double *grad, int ncols,
                     cudaStream_t s) {
     const int nsys = c.ns * ncols;
-    double *cd = (double *)c.coef_buf.ensure(sizeof(double) * (size_t)ncols);
-    RPA_CUDA(cudaMemcpyAsync(cd, coef, sizeof(double) * ncols, cudaMemcpyHostToDevice, s));
     SolveSpec sp;
     sp.vt = dv;
     sp.grad = grad;
-    sp.coef = cd;
+    sp.coef = coef;
     sp.Tc = pair_coefficients(c, dv, ncols, s);
     sp.sign = -1.0;
     sp.omega = omega;
     sp.pairs = ncols;
     sp.nsys = nsys;
-    const int w = run_queue(c, sp, s, nullptr, nullptr);
-    sync_stream(c, s);   // coef (host) must outlive the copy
-    return w;
+    return run_queue(c, sp, s, nullptr, nullptr);
 }
 
 int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {

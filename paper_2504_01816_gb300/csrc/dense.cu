@@ -394,9 +394,144 @@ __global__ void k_sq_sum(const double *__restrict__ part, int n, double weight, 
     *e_out = weight * s;
 }
 
+// Symmetric eigendecomposition A = Q diag(w) Q^T of an n x n matrix (row-major, destroyed) by the
+// cyclic Jacobi method in parallel (round-robin) order, one block: in each of the n' - 1 rounds of a
+// sweep (n' = n rounded up to even) the n'/2 disjoint index pairs of a round-robin tournament are
+// rotated together -- rotation angles from the current 2 x 2 blocks, then all column updates
+// A <- A J, Q <- Q J, then all row updates A <- J^T A.  Sweeps stop when the off-diagonal part falls
+// below 1e-30 of the whole (squared) or after 100 sweeps.  Q[i*n+a] = component i of eigenvector a;
+// w[a] = A[a][a].  work: 2 n' doubles (cosines, sines) and n' ints (the tournament).
+__global__ void __launch_bounds__(1024) k_jacobi_eigh(double *__restrict__ A, int n, double *__restrict__ Q,
+                                                      double *__restrict__ w, double *__restrict__ cs,
+                                                      int *__restrict__ perm) {
+    __shared__ double red[32];
+    __shared__ double tot_sh, off_sh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int m = n + (n & 1);                 // an odd n gets a dummy index n (no rotation)
+    const int half = m / 2;
+    double *sn = cs + half;
+    for (long long e = tid; e < (long long)n * n; e += nt) Q[e] = (e / n == e % n) ? 1.0 : 0.0;
+    for (int i = tid; i < m; i += nt) perm[i] = i;
+    __syncthreads();
+    auto block_sum2 = [&](double a, double b) {
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if ((tid & 31) == 0) {
+            red[tid >> 5] = a;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < (nt + 31) / 32; ++k) t += red[k];
+            tot_sh = t;
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = b;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < (nt + 31) / 32; ++k) t += red[k];
+            off_sh = t;
+        }
+        __syncthreads();
+    };
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double ta = 0.0, oa = 0.0;
+        for (long long e = tid; e < (long long)n * n; e += nt) {
+            const double a = A[e];
+            ta += a * a;
+            if (e / n != e % n) oa += a * a;
+        }
+        block_sum2(ta, oa);
+        if (!(off_sh > 1e-30 * tot_sh)) break;
+        for (int round = 0; round < m - 1; ++round) {
+            // pair k: (perm[k], perm[m - 1 - k])
+            for (int k = tid; k < half; k += nt) {
+                int p = perm[k], q = perm[m - 1 - k];
+                double c = 1.0, sg = 0.0;
+                if (p < n && q < n) {
+                    if (p > q) { const int t = p; p = q; q = t; }
+                    const double apq = A[(long long)p * n + q];
+                    if (apq != 0.0) {
+                        const double theta = (A[(long long)q * n + q] - A[(long long)p * n + p]) / (2.0 * apq);
+                        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sg = t * c;
+                    }
+                }
+                cs[k] = c;
+                sn[k] = sg;
+            }
+            __syncthreads();
+            // columns p, q of A and Q
+            for (long long e = tid; e < (long long)n * half; e += nt) {
+                const int row = (int)(e / half), k = (int)(e % half);
+                int p = perm[k], q = perm[m - 1 - k];
+                if (p >= n || q >= n) continue;
+                if (p > q) { const int t = p; p = q; q = t; }
+                const double c = cs[k], sg = sn[k];
+                const double akp = A[(long long)row * n + p], akq = A[(long long)row * n + q];
+                A[(long long)row * n + p] = c * akp - sg * akq;
+                A[(long long)row * n + q] = sg * akp + c * akq;
+                const double qkp = Q[(long long)row * n + p], qkq = Q[(long long)row * n + q];
+                Q[(long long)row * n + p] = c * qkp - sg * qkq;
+                Q[(long long)row * n + q] = sg * qkp + c * qkq;
+            }
+            __syncthreads();
+            // rows p, q of A
+            for (long long e = tid; e < (long long)n * half; e += nt) {
+                const int col = (int)(e / half), k = (int)(e % half);
+                int p = perm[k], q = perm[m - 1 - k];
+                if (p >= n || q >= n) continue;
+                if (p > q) { const int t = p; p = q; q = t; }
+                const double c = cs[k], sg = sn[k];
+                const double apk = A[(long long)p * n + col], aqk = A[(long long)q * n + col];
+                A[(long long)p * n + col] = c * apk - sg * aqk;
+                A[(long long)q * n + col] = sg * apk + c * aqk;
+            }
+            __syncthreads();
+            // next round of the tournament: index 0 stays, the others rotate by one place
+            if (tid == 0) {
+                const int last = perm[m - 1];
+                for (int i = m - 1; i > 1; --i) perm[i] = perm[i - 1];
+                perm[1] = last;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += nt) w[i] = A[(long long)i * n + i];
+}
+
+// The adjoint's rotation to Ritz vectors and weights: S[i][k] = Q[k][i] (row i of S combines the
+// basis into Ritz vector i) and coef[i] = weight * g'(lambda_i), g'(x) = -x / (1 - x).
+__global__ void k_ritz_rotation(const double *__restrict__ Q, const double *__restrict__ w, int n, double weight,
+                                double *__restrict__ S, double *__restrict__ coef) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), k = (int)(e % n);
+        S[e] = Q[(long long)k * n + i];
+        if (k == 0) coef[i] = weight * (-w[i] / (1.0 - w[i]));
+    }
+}
+
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
+
+void jacobi_eigh_device(double *A, int n, double *Q, double *w, double *work, cudaStream_t s) {
+    const int m = n + (n & 1);
+    k_jacobi_eigh<<<1, 1024, 0, s>>>(A, n, Q, w, work, (int *)(work + m));
+    RPA_LAUNCH("jacobi eigensolver");
+    count_launches(1);
+}
+
+void ritz_rotation(const double *Q, const double *w, int n, double weight, double *S, double *coef, cudaStream_t s) {
+    k_ritz_rotation<<<std::min<unsigned>(cdiv((long long)n * n, 256), 1024u), 256, 0, s>>>(Q, w, n, weight, S, coef);
+    RPA_LAUNCH("ritz rotation");
+    count_launches(1);
+}
 
 void gram(const double *A, int na, const double *B, int nb, long long len, double *G, cudaStream_t s,
           DevBuf &scratch) {

@@ -183,13 +183,18 @@ int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const doub
 int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s);
 
 // grad += sum_j coef[j] (4/h^3) Re sum_n (P_c x_{n,j})^2 for the projected Sternheimer solutions of
-// dV_j (ncols rows of dv); coef: ncols doubles on the host.  Returns the worst status.
+// dV_j (ncols rows of dv); coef: ncols doubles on the device.  Returns the worst status known on
+// the host (a device-driven queue reports through the device statistics).
 int response_square(Ctx &c, double omega, const double *dv, const double *coef, double *grad, int ncols,
                     cudaStream_t s);
 
 // Host symmetric eigendecomposition (cyclic Jacobi): A = Q diag(w) Q^T, Q[i*n+a] = component i of
-// eigenvector a; w ascending is not guaranteed.
+// eigenvector a; w ascending is not guaranteed.  (The 1D matrices of the Coulomb operator.)
 void jacobi_eigh(std::vector<double> A, int n, std::vector<double> &w, std::vector<double> &Q);
+// The same on the device (parallel cyclic Jacobi, one block; A destroyed); work: 3 (n + 1) doubles.
+void jacobi_eigh_device(double *A, int n, double *Q, double *w, double *work, cudaStream_t s);
+// S = Q^T and coef[i] = weight * g'(w_i), g'(x) = -x / (1 - x) (the adjoint's Ritz rotation, device).
+void ritz_rotation(const double *Q, const double *w, int n, double weight, double *S, double *coef, cudaStream_t s);
 
 // Whether the fused single-pass COCG kernel applies to this context's grid (a whole xy plane fits
 // its shared-memory ring); the mixed form then uses it by default.
