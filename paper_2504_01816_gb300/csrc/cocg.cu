@@ -15,7 +15,9 @@
 //   k_cocg_b:   x += alpha p, r -= alpha q, partial sums of r^T r and ||r||^2
 // Reductions are deterministic: every block writes its own partial sums; consumers add them in
 // block order.  Groups of iterations ("epochs") are replayed as CUDA graphs; between epochs
-// maintenance kernels refine, retire, refill and load slots.
+// maintenance kernels refine, retire, refill and load slots.  The mixed form's fused kernel
+// (k_cocg_ring, where a plane fits its shared-memory ring) replaces the four launches: one block
+// owns one system, so one launch per epoch runs every active inner solve to its end.
 //
 // Plain form:  complex FP64 COCG to ||r|| <= tol ||b||.
 // Mixed form:  FP64 iterative refinement around complex FP32 COCG: r64 = b - A x64 in FP64,
@@ -815,6 +817,13 @@ __global__ void __launch_bounds__(MAXT, 1)
 // per step suffices.  Each block handles whole systems, so the state is single-buffered: a
 // thread reads q at plane f six steps before it writes q there, and reads back r_k of plane
 // f-6 that it wrote itself.
+//
+// Because a block holds every sum of its system, it takes the scalar step itself and goes on
+// with the next sweep: one launch runs each system of the active list through its whole inner
+// solve.  Blocks take systems from a shared counter as they finish the previous one, so solves of
+// different lengths balance over the SMs and no launch waits on a partly filled last wave; the
+// list is taken from its end (it is in slot order, i.e. by orbital, and the highest orbitals,
+// nearest the unoccupied spectrum, need the most iterations: the longest solves start first).
 constexpr int kRingPlanes = 14;
 constexpr int kRingPad = 6;
 constexpr int kRingMaxThreads = 512;
@@ -822,12 +831,10 @@ constexpr int kRingWsMaxThreads = 672;     // consumers + producers (planes of u
 
 struct RingArgs {
     Slot *slots;
-    const int *list_in;            // active slots of this pass
+    const int *list_in;            // slots whose inner solve runs
     const int *cnt_in;
-    int *list_out;                 // slots that continue (next pass)
-    int *cnt_out;
-    int *cnt_clear;                // list counter of the pass after next, cleared here
-    unsigned long long *prof;      // grid points processed (nullptr = off)
+    int *grab;                     // systems taken so far (zero at the launch)
+    unsigned long long *prof;      // [1] grid points processed, [2] those of first sweeps (nullptr = off)
     long long nd;
     double tol, inner_tol;
     int maxit;
@@ -878,7 +885,8 @@ __device__ __forceinline__ void st_pair(float2 *base, int idx, bool hasb, float2
 
 // Scalar step of the fused iteration for one slot (thread 0 of its block).  v: rho (re, im),
 // ||r||^2, pi (re, im), tau (re, im), theta (re, im).  Same stopping rules as k_beta/k_alpha.
-__device__ void ring_scalar_step(const RingArgs &A, Slot &sl, int s, const double (&v)[9]) {
+// Returns whether the inner solve goes on.
+__device__ bool ring_scalar_step(const RingArgs &A, Slot &sl, const double (&v)[9]) {
     const int k = sl.iters;
     const double rn = sqrt(v[2]);
     const double thr = fmax(A.inner_tol * sl.ref_norm, 0.3 * A.tol * sl.bnorm * sl.scale);
@@ -896,14 +904,14 @@ __device__ void ring_scalar_step(const RingArgs &A, Slot &sl, int s, const doubl
         if (!conv && (nonfinite || (zero && k == 0))) sl.status = RPA_ERR_BREAKDOWN;
         if (!conv && !nonfinite && nearb) sl.nearbreak += 1;
         sl.phase = kInnerDone;
-        return;
+        return false;
     }
     const double den = v[3] * v[3] + v[4] * v[4];
     if (!(den > 0.0) || !isfinite(den)) {
         sl.status = RPA_ERR_BREAKDOWN;
         if (!isfinite(den)) sl.discard = 1;
         sl.phase = kInnerDone;
-        return;
+        return false;
     }
     const double ar = (v[0] * v[3] + v[1] * v[4]) / den;   // alpha_k = rho / pi
     const double ai = (v[1] * v[3] - v[0] * v[4]) / den;
@@ -915,8 +923,7 @@ __device__ void ring_scalar_step(const RingArgs &A, Slot &sl, int s, const doubl
     sl.alpha_im = ai;
     sl.beta_re = (nr_ * v[0] + ni_ * v[1]) / rr2;
     sl.beta_im = (ni_ * v[0] - nr_ * v[1]) / rr2;
-    const int pos = atomicAdd(A.cnt_out, 1);
-    A.list_out[pos] = s;
+    return true;
 }
 
 // Two x-adjacent points (x, x+1) of row y from a ring plane: one 16-byte shared load.
@@ -1129,6 +1136,34 @@ __device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned c
     }
 }
 
+// Next system of a fused-kernel block from the shared counter (index into the active list, taken
+// from its end), or -1 when the list is exhausted.  All threads of the block call it.
+__device__ __forceinline__ int ring_next_item(const RingArgs &A, int n_items) {
+    __shared__ int item;
+    if (threadIdx.x == 0) item = atomicAdd(A.grab, 1);
+    __syncthreads();
+    const int it = item;
+    return it < n_items ? A.list_in[n_items - 1 - it] : -1;
+}
+
+// End of a sweep of a fused-kernel block: block sums, scalar step by thread 0; returns (in every
+// thread) whether the system's inner solve goes on.
+__device__ __forceinline__ bool ring_end_sweep(const RingArgs &A, Slot &sl, bool first, const float (&fa)[3],
+                                               const float (&sa)[6]) {
+    __shared__ int more;
+    double v[9] = {fa[0], fa[1], fa[2], sa[0], sa[1], sa[2], sa[3], sa[4], sa[5]};
+    block_sum_any<9>(v);
+    if (threadIdx.x == 0) {
+        more = ring_scalar_step(A, sl, v) ? 1 : 0;
+        if (A.prof) {
+            atomicAdd(A.prof + 1, (unsigned long long)A.nd);
+            if (first) atomicAdd(A.prof + 2, (unsigned long long)A.nd);
+        }
+    }
+    __syncthreads();
+    return more != 0;
+}
+
 // The fused kernel: every thread takes one unit through both phases of a step (front, then the
 // stencil six planes behind), the front's loads for the next plane in flight during the stencil.
 template <bool EVEN>
@@ -1142,56 +1177,54 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
     const int rsb = A.rs * 8, psb = A.ps * 8;      // ring row / plane strides in bytes
     const RingUnit U = ring_unit(tid, A);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (blockIdx.x == 0 && tid == 0) *A.cnt_clear = 0;
     for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
     const int n_items = *A.cnt_in;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int s = A.list_in[it];
+    for (int s; (s = ring_next_item(A, n_items)) >= 0;) {
         Slot &sl = A.slots[s];
-        const bool first = sl.iters == 0;
-        const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
-        const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
         const float shr = (float)sl.shift_re, shi = (float)sl.shift_im;
         const long long off = (long long)s * A.nd;
         float2 *const xs = xg + off;
         float2 *const rsv = rg + off;
         float2 *const psv = pg + off;
         float2 *const qs = qg + off;
-        __syncthreads();                           // the previous item's ring readers are done
-        if (U.own) {                               // planes -6 .. -1 (ring slots 8 .. 13) are zero
+        bool more = true;
+        while (more) {                             // sweeps of this system (iterations of COCG)
+            const bool first = sl.iters == 0;
+            const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
+            const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
+            __syncthreads();                       // the previous sweep's ring readers are done
+            if (U.own) {                           // planes -6 .. -1 (ring slots 8 .. 13) are zero
 #pragma unroll
-            for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
-                *reinterpret_cast<float4 *>(ring + m * psb + U.rb0) = zero4;
-                if (U.row1) *reinterpret_cast<float4 *>(ring + m * psb + U.rb1) = zero4;
+                for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                    *reinterpret_cast<float4 *>(ring + m * psb + U.rb0) = zero4;
+                    if (U.row1) *reinterpret_cast<float4 *>(ring + m * psb + U.rb1) = zero4;
+                }
             }
-        }
-        RingFront F;
-        if (U.own) ring_load_front<EVEN>(U, U.col0, first, xs, rsv, psv, qs, F);   // front plane 0
-        float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int nsteps = nz + kRadius;
-        // rolled loop: unrolled over the ring (compile-time slots) it needs far more registers
-        for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
-            // r_k and V of the stencil's plane z = f - 6, in flight during the front and the barrier
-            const int z = f - kRadius;
-            float2 rk[4] = {};
-            float vv[4] = {0.f, 0.f, 0.f, 0.f};
-            if (U.own && z >= 0) ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
-            // 1. front plane f, p_k into ring slot u
-            if (U.own) ring_front<EVEN>(U, f, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring + u * psb, fa);
-            // 2. the next front plane, in flight during the stencil below
-            if (U.own && f + 1 < nz) ring_load_front<EVEN>(U, (f + 1) * plane + U.col0, first, xs, rsv, psv, qs, F);
-            __syncthreads();
-            // 3. q_k on plane z, its 6 neighbour planes from the ring
-            if (U.own && z >= 0) {
-                const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
-                ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs, sa);
+            RingFront F;
+            if (U.own) ring_load_front<EVEN>(U, U.col0, first, xs, rsv, psv, qs, F);   // front plane 0
+            float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int nsteps = nz + kRadius;
+            // rolled loop: unrolled over the ring (compile-time slots) it needs far more registers
+            for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
+                // r_k and V of the stencil's plane z = f - 6, in flight during the front and the barrier
+                const int z = f - kRadius;
+                float2 rk[4] = {};
+                float vv[4] = {0.f, 0.f, 0.f, 0.f};
+                if (U.own && z >= 0) ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
+                // 1. front plane f, p_k into ring slot u
+                if (U.own)
+                    ring_front<EVEN>(U, f, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring + u * psb, fa);
+                // 2. the next front plane, in flight during the stencil below
+                if (U.own && f + 1 < nz)
+                    ring_load_front<EVEN>(U, (f + 1) * plane + U.col0, first, xs, rsv, psv, qs, F);
+                __syncthreads();
+                // 3. q_k on plane z, its 6 neighbour planes from the ring
+                if (U.own && z >= 0) {
+                    const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
+                    ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs, sa);
+                }
             }
-        }
-        double v[9] = {fa[0], fa[1], fa[2], sa[0], sa[1], sa[2], sa[3], sa[4], sa[5]};
-        block_sum_any<9>(v);
-        if (tid == 0) {
-            ring_scalar_step(A, sl, s, v);
-            if (A.prof) atomicAdd(A.prof + 1, (unsigned long long)A.nd);
+            more = ring_end_sweep(A, sl, first, fa, sa);
         }
     }
 }
@@ -1218,72 +1251,70 @@ __global__ void __maxnreg__(96)
     const int pt = tid - ncons;                    // producer index: units pt and pt + nprod
     const RingUnit U = ring_unit(producer ? -1 : tid, A);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (blockIdx.x == 0 && tid == 0) *A.cnt_clear = 0;
     for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
     const int n_items = *A.cnt_in;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int s = A.list_in[it];
+    for (int s; (s = ring_next_item(A, n_items)) >= 0;) {
         Slot &sl = A.slots[s];
-        const bool first = sl.iters == 0;
-        const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
-        const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
         const float shr = (float)sl.shift_re, shi = (float)sl.shift_im;
         const long long off = (long long)s * A.nd;
         float2 *const xs = xg + off;
         float2 *const rsv = rg + off;
         float2 *const psv = pg + off;
         float2 *const qs = qg + off;
-        float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        __syncthreads();                           // the previous item's ring readers are done
-        if (producer)                              // planes -6 .. -1 (ring slots 8 .. 13) are zero; plane 0
-            for (int pu = pt; pu < nunits; pu += nprod) {
-                const RingUnit P = ring_unit(pu, A);
+        bool more = true;
+        while (more) {                             // sweeps of this system (iterations of COCG)
+            const bool first = sl.iters == 0;
+            const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
+            const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
+            float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            __syncthreads();                       // the previous sweep's ring readers are done
+            if (producer)                          // planes -6 .. -1 (ring slots 8 .. 13) are zero; plane 0
+                for (int pu = pt; pu < nunits; pu += nprod) {
+                    const RingUnit P = ring_unit(pu, A);
 #pragma unroll
-                for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
-                    *reinterpret_cast<float4 *>(ring + m * psb + P.rb0) = zero4;
-                    if (P.row1) *reinterpret_cast<float4 *>(ring + m * psb + P.rb1) = zero4;
+                    for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                        *reinterpret_cast<float4 *>(ring + m * psb + P.rb0) = zero4;
+                        if (P.row1) *reinterpret_cast<float4 *>(ring + m * psb + P.rb1) = zero4;
+                    }
+                    RingFront F;
+                    ring_load_front<EVEN>(P, P.col0, first, xs, rsv, psv, qs, F);
+                    ring_front<EVEN>(P, 0, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring, fa);
                 }
-                RingFront F;
-                ring_load_front<EVEN>(P, P.col0, first, xs, rsv, psv, qs, F);
-                ring_front<EVEN>(P, 0, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring, fa);
-            }
-        __syncthreads();
-        const int nsteps = nz + kRadius;
-        for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
-            if (producer) {
-                // plane f + 1 into ring slot u + 1
-                if (f + 1 < nsteps) {
-                    const int un = u + 1 == kRingPlanes ? 0 : u + 1;
-                    for (int pu = pt; pu < nunits; pu += nprod) {
-                        const RingUnit P = ring_unit(pu, A);
-                        RingFront F;
-                        if (f + 1 < nz) ring_load_front<EVEN>(P, (f + 1) * plane + P.col0, first, xs, rsv, psv, qs, F);
-                        ring_front<EVEN>(P, f + 1, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv,
-                                         ring + un * psb, fa);
+            __syncthreads();
+            const int nsteps = nz + kRadius;
+            for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
+                if (producer) {
+                    // plane f + 1 into ring slot u + 1
+                    if (f + 1 < nsteps) {
+                        const int un = u + 1 == kRingPlanes ? 0 : u + 1;
+                        for (int pu = pt; pu < nunits; pu += nprod) {
+                            const RingUnit P = ring_unit(pu, A);
+                            RingFront F;
+                            if (f + 1 < nz)
+                                ring_load_front<EVEN>(P, (f + 1) * plane + P.col0, first, xs, rsv, psv, qs, F);
+                            ring_front<EVEN>(P, f + 1, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv,
+                                             ring + un * psb, fa);
+                        }
+                    }
+                } else {
+                    const int z = f - kRadius;
+                    if (U.own && z >= 0) {
+                        float2 rk[4] = {};
+                        float vv[4] = {0.f, 0.f, 0.f, 0.f};
+                        ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
+                        const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;
+                        ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs,
+                                           sa);
                     }
                 }
-            } else {
-                const int z = f - kRadius;
-                if (U.own && z >= 0) {
-                    float2 rk[4] = {};
-                    float vv[4] = {0.f, 0.f, 0.f, 0.f};
-                    ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
-                    const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;
-                    ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs, sa);
-                }
+                __syncthreads();
             }
-            __syncthreads();
-        }
-        double v[9] = {fa[0], fa[1], fa[2], sa[0], sa[1], sa[2], sa[3], sa[4], sa[5]};
-        block_sum_any<9>(v);
-        if (tid == 0) {
-            ring_scalar_step(A, sl, s, v);
-            if (A.prof) atomicAdd(A.prof + 1, (unsigned long long)A.nd);
+            more = ring_end_sweep(A, sl, first, fa, sa);
         }
     }
 }
 
-// Active list of the first pass of an epoch: the slots whose inner solve runs, in slot order
+// Active list of the fused kernel's launch: the slots whose inner solve runs, in slot order
 // (block scan); clears the other list counters.  One block of 1024 threads.
 __global__ void __launch_bounds__(1024) k_ring_list(Params P) {
     __shared__ int wsum[32];
@@ -2171,7 +2202,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     Slot *slots = (Slot *)c.sys_state.ensure(sizeof(Slot) * S);
     // ints: head, count, cnt[4], list[4][S], then per system: n, j, iters, status, refines,
     // near-breakdowns; then the finished-slot count and list [S].  The split kernels use lists 0
-    // and 1 (by iteration parity), the fused kernel all four in rotation.
+    // and 1 (by iteration parity); the fused kernel list 0, with counter 1 as its work counter.
     const size_t nint = 6 + 4 * (size_t)S + 6 * (size_t)nsys + 1 + (size_t)S;
     int *qi = (int *)c.slot_idx.ensure(sizeof(int) * nint);
     int *head = qi, *count = qi + 1, *cnt = qi + 2, *list = qi + 6;
@@ -2273,33 +2304,27 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     }
     const double scale = 4.0 / (c.h * c.h * c.h);
 
-    // the fused kernel: one block per system, four rotating active lists
-    RingArgs ra[4];
+    // the fused kernel: one block per system at a time, each run through its inner solve
+    RingArgs ra{};
     unsigned ring_grid = 1, ring_threads = 32;
     size_t ring_smem = 0;
     if (use_ring) {
         const int hw = (c.nx + 1) / 2;
-        for (int i = 0; i < 4; ++i) {
-            RingArgs a{};
-            a.slots = slots;
-            a.list_in = list + i * S;
-            a.cnt_in = cnt + i;
-            a.list_out = list + ((i + 1) & 3) * S;
-            a.cnt_out = cnt + ((i + 1) & 3);
-            a.cnt_clear = cnt + ((i + 2) & 3);
-            a.nd = nd;
-            a.tol = c.opt.tol;
-            a.inner_tol = c.opt.inner_tol;
-            a.maxit = c.opt.maxit;
-            a.nx = c.nx;
-            a.ny = c.ny;
-            a.nz = c.nz;
-            a.hw = hw;
-            a.hh = (c.ny + 1) / 2;
-            a.rs = 2 * hw + kRingPad;
-            a.ps = c.ny * a.rs + kRingPad;
-            ra[i] = a;
-        }
+        ra.slots = slots;
+        ra.list_in = list;             // built by k_ring_list, which also clears the counter
+        ra.cnt_in = cnt;
+        ra.grab = cnt + 1;
+        ra.nd = nd;
+        ra.tol = c.opt.tol;
+        ra.inner_tol = c.opt.inner_tol;
+        ra.maxit = c.opt.maxit;
+        ra.nx = c.nx;
+        ra.ny = c.ny;
+        ra.nz = c.nz;
+        ra.hw = hw;
+        ra.hh = (c.ny + 1) / 2;
+        ra.rs = 2 * hw + kRingPad;
+        ra.ps = c.ny * ra.rs + kRingPad;
         ring_smem = ring_bytes(c.nx, c.ny);
         {
             const int units = hw * ((c.ny + 1) / 2);
@@ -2326,14 +2351,15 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     }
     const double csz = mixed ? 8.0 : 16.0, rsz = mixed ? 4.0 : 8.0;
     // algorithmic bytes per grid point: pa reads r, p_old, V and writes p_new, q; b reads x, r, p, q
-    // and writes x, r; the fused kernel reads and writes x, r, p, q (V is read once per plane and
-    // block, not per system, and is not counted)
+    // and writes x, r; the fused kernel reads and writes x, r, p, q, except in the first sweep of an
+    // inner solve, which reads r and writes p, q (V is read once per plane and block, not per system,
+    // and is not counted)
     const double bytes_per_point[3] = {0.0, use_ring ? 8 * csz : 4 * csz + rsz, use_ring ? 0.0 : 6 * csz};
     if (prof) {
         RPA_CUDA(cudaMemsetAsync(c.d_prof_points, 0, sizeof(unsigned long long) * 3, st));
         P.prof = c.d_prof_points;
         for (int par = 0; par < 2; ++par) ia_pa[par].prof = ia_b[par].prof = c.d_prof_points;
-        for (auto &a : ra) a.prof = c.d_prof_points;
+        ra.prof = c.d_prof_points;
     }
     // Two graph instances of one epoch (alternating, so that the events of one can be read while
     // the other runs); without graphs the same launches go straight to the stream.
@@ -2397,13 +2423,11 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         };
         if (use_ring) {
             k_ring_list<<<1, 1024, 0, ss>>>(P);
-            for (int e = 0; e < kEpoch; ++e) {
-                rec(4 * e + 0);
-                ring_fn<<<ring_grid, ring_threads, ring_smem, ss>>>(ra[e & 3], (float2 *)xin, (float2 *)r,
-                                                                    (float2 *)p, (float2 *)q, c.vloc32, cf32);
-                rec(4 * e + 1);
-            }
-            RPA_LAUNCH("cocg iterations (fused)");
+            rec(0);
+            ring_fn<<<ring_grid, ring_threads, ring_smem, ss>>>(ra, (float2 *)xin, (float2 *)r, (float2 *)p,
+                                                                (float2 *)q, c.vloc32, cf32);
+            rec(1);
+            RPA_LAUNCH("cocg inner solves (fused)");
             maintenance(ss);
             return;
         }
@@ -2437,7 +2461,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         maintenance(ss);
     };
     const int per_maint = (mixed ? 8 : 5) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
-    const int per_epoch = (use_ring ? 1 + kEpoch : 4 * kEpoch) + per_maint;
+    const int per_epoch = (use_ring ? 2 : 4 * kEpoch) + per_maint;
 
     // device-driven queue: CUDA graphs, no profiling, no per-system outputs wanted
     const bool device_loop = use_graph && !prof && !iters_out && !status_out;
@@ -2461,8 +2485,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     auto collect_epoch = [&](long long k) {
         if (!prof) return;
         const int set = (int)(k & 1);
-        for (int t = 0; t < kTimed; ++t) {
-            if (use_ring && (t & 1)) continue;      // the fused kernel: one timed launch per iteration
+        for (int t = 0; t < (use_ring ? 1 : kTimed); ++t) {   // the fused kernel: one timed launch
             float ms = 0.f;
             RPA_CUDA(cudaEventElapsedTime(&ms, evs[((size_t)set * kTimed + t) * 2], evs[((size_t)set * kTimed + t) * 2 + 1]));
             prof_ms[1 + t % 2] += ms;
@@ -2555,6 +2578,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             c.stats.prof_launches[sl] += prof_n[k];
             c.stats.prof_points[sl] += (double)pts[k];
             c.stats.prof_bytes[sl] += (double)pts[k] * bytes_per_point[k];
+            if (use_ring) c.stats.prof_bytes[sl] -= (double)pts[2] * 5 * csz;   // first sweeps: 3 streams
         }
     }
 
