@@ -11,8 +11,10 @@
  *   apply:  out = (H + sigma) in,  H = -1/2 L_h + diag(V_loc)
  *           L_h is the centred finite-difference Laplacian whose weights w[0..R]
  *           (already divided by h^2) are passed in; grid values outside the box are
- *           zero (Dirichlet), as in the real-space method of the paper (Section
- *           "Implementation": matrix-free high-order centred finite differences).
+ *           zero (Dirichlet) or, with `periodic`, those of the periodic continuation
+ *           of the grid function (the bulk cells of the paper's Section "Results"),
+ *           as in the real-space method of the paper (Section "Implementation":
+ *           matrix-free high-order centred finite differences).
  *   cocg:   COCG (van der Vorst & Melissen 1990), the conjugate-orthogonal CG the
  *           paper uses for the complex-symmetric Sternheimer systems
  *           (H - eps_n + i omega) x = b  (Section "Implementation", Sternheimer
@@ -51,8 +53,17 @@ void oracle_set_threads(int n) {
 #endif
 }
 
+/* Grid index a along an axis of n points: itself inside [0, n), its periodic image when
+ * `periodic`, else -1 (outside the box: a zero value). */
+static int tap(int a, int n, int periodic) {
+    if (a >= 0 && a < n) return a;
+    if (!periodic) return -1;
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
 /* out = (-1/2 L_h + V + sigma) in, for one complex grid function. */
-static void apply_shifted_h(int nx, int ny, int nz, int radius, const double *w,
+static void apply_shifted_h(int nx, int ny, int nz, int radius, const double *w, int periodic,
                             const double *vloc, double complex sigma,
                             const double complex *in, double complex *out) {
     for (int k = 0; k < nz; ++k)
@@ -61,20 +72,23 @@ static void apply_shifted_h(int nx, int ny, int nz, int radius, const double *w,
                 long idx = i + (long)nx * (j + (long)ny * k);
                 double complex lap = 3.0 * w[0] * in[idx];
                 for (int s = 1; s <= radius; ++s) {
-                    if (i - s >= 0) lap += w[s] * in[idx - s];
-                    if (i + s < nx) lap += w[s] * in[idx + s];
-                    if (j - s >= 0) lap += w[s] * in[idx - (long)s * nx];
-                    if (j + s < ny) lap += w[s] * in[idx + (long)s * nx];
-                    if (k - s >= 0) lap += w[s] * in[idx - (long)s * nx * ny];
-                    if (k + s < nz) lap += w[s] * in[idx + (long)s * nx * ny];
+                    for (int sg = -1; sg <= 1; sg += 2) {
+                        int a;
+                        if ((a = tap(i + sg * s, nx, periodic)) >= 0)
+                            lap += w[s] * in[a + (long)nx * (j + (long)ny * k)];
+                        if ((a = tap(j + sg * s, ny, periodic)) >= 0)
+                            lap += w[s] * in[i + (long)nx * (a + (long)ny * k)];
+                        if ((a = tap(k + sg * s, nz, periodic)) >= 0)
+                            lap += w[s] * in[i + (long)nx * (j + (long)ny * a)];
+                    }
                 }
                 out[idx] = -0.5 * lap + (vloc[idx] + sigma) * in[idx];
             }
 }
 
-void oracle_apply_h(int nx, int ny, int nz, int radius, const double *w, const double *vloc,
+void oracle_apply_h(int nx, int ny, int nz, int radius, const double *w, int periodic, const double *vloc,
                     double sigma_re, double sigma_im, const double *in, double *out) {
-    apply_shifted_h(nx, ny, nz, radius, w, vloc, sigma_re + I * sigma_im,
+    apply_shifted_h(nx, ny, nz, radius, w, periodic, vloc, sigma_re + I * sigma_im,
                     (const double complex *)in, (double complex *)out);
 }
 
@@ -92,7 +106,7 @@ static double norm2(long n, const double complex *x) {
 }
 
 /* One COCG solve.  Returns the status; *iters gets the iteration count. */
-static int cocg_one(int nx, int ny, int nz, int radius, const double *w, const double *vloc,
+static int cocg_one(int nx, int ny, int nz, int radius, const double *w, int periodic, const double *vloc,
                     double complex sigma, const double complex *b, double complex *x,
                     double tol, int maxit, int *iters) {
     long n = (long)nx * ny * nz;
@@ -111,7 +125,7 @@ static int cocg_one(int nx, int ny, int nz, int radius, const double *w, const d
     }
     double complex rho = dotu(n, r, r);
     for (it = 0; it < maxit;) {
-        apply_shifted_h(nx, ny, nz, radius, w, vloc, sigma, p, q);
+        apply_shifted_h(nx, ny, nz, radius, w, periodic, vloc, sigma, p, q);
         double complex mu = dotu(n, p, q);
         if (cabs(mu) == 0.0 || cabs(rho) == 0.0) {
             status = ORACLE_BREAKDOWN;
@@ -142,7 +156,7 @@ done:
 
 /* Solve nsys independent systems (H + sigma_s) x_s = b_s; systems run in parallel
  * over the host's threads. */
-void oracle_cocg_batch(int nx, int ny, int nz, int radius, const double *w, const double *vloc,
+void oracle_cocg_batch(int nx, int ny, int nz, int radius, const double *w, int periodic, const double *vloc,
                        int nsys, const double *sigma_re, const double *sigma_im, const double *b,
                        double *x, double tol, int maxit, int *iters, int *status) {
     long n = (long)nx * ny * nz;
@@ -150,7 +164,7 @@ void oracle_cocg_batch(int nx, int ny, int nz, int radius, const double *w, cons
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int s = 0; s < nsys; ++s) {
-        status[s] = cocg_one(nx, ny, nz, radius, w, vloc, sigma_re[s] + I * sigma_im[s],
+        status[s] = cocg_one(nx, ny, nz, radius, w, periodic, vloc, sigma_re[s] + I * sigma_im[s],
                              (const double complex *)(b + 2 * n * s), (double complex *)(x + 2 * n * s),
                              tol, maxit, &iters[s]);
     }

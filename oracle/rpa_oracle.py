@@ -18,11 +18,14 @@ and "trapezoidal rule", Section "Implementation"; these are the readings):
 * grid functions are vectors of length N_d = nx*ny*nz, point (i,j,k) at
   i + nx*(j + ny*k); a block of K of them is an array (K, N_d);
 * orbitals u_n are l2-orthonormal (u = psi h^{3/2});
-* L_h is the 12th-order centred Laplacian with zero values outside the box;
-  H = -1/2 L_h + diag(V_loc);
+* L_h is the 12th-order centred Laplacian with zero values outside the box
+  (Dirichlet) or, for a periodic grid, the values of the periodic continuation
+  (the bulk cells of Section "Results"); H = -1/2 L_h + diag(V_loc);
 * nu = 4 pi (-L_h)^{-1} (Poisson equation, Eq. 5); nu^p is applied through the
   eigendecompositions of the three 1D second-difference matrices (Kronecker
-  product formalism, Section "Implementation");
+  product formalism, Section "Implementation"); on a periodic grid -L_h is
+  singular on the constant function (the G = 0 mode), which nu^p maps to zero
+  (the neutralising background of a periodic cell);
 * chi0 dV = drho = (4/h^3) Re sum_n u_n (.) x_n with
   (H - eps_n + i omega) x_n = -P_c(u_n (.) dV),  P_c = I - U U^T   (Eqs. 7-9);
 * the correlation energy is E_c = (1/2pi) int_0^inf sum_i [log(1-lambda_i) +
@@ -54,9 +57,10 @@ def _lib():
     if _lib_handle is None:
         lib = ctypes.CDLL(_build.build())
         d, i = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-        lib.oracle_apply_h.argtypes = [ctypes.c_int] * 4 + [d, d, ctypes.c_double, ctypes.c_double, d, d]
+        lib.oracle_apply_h.argtypes = [ctypes.c_int] * 4 + [d, ctypes.c_int, d, ctypes.c_double, ctypes.c_double,
+                                                             d, d]
         lib.oracle_apply_h.restype = None
-        lib.oracle_cocg_batch.argtypes = ([ctypes.c_int] * 4 + [d, d, ctypes.c_int, d, d, d, d,
+        lib.oracle_cocg_batch.argtypes = ([ctypes.c_int] * 4 + [d, ctypes.c_int, d, ctypes.c_int, d, d, d, d,
                                           ctypes.c_double, ctypes.c_int, i, i])
         lib.oracle_cocg_batch.restype = None
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -105,6 +109,7 @@ class Grid:
     ny: int
     nz: int
     h: float
+    periodic: bool = False      # periodic continuation instead of zero values outside the box
 
     @property
     def n_d(self) -> int:
@@ -116,11 +121,12 @@ class Grid:
 
 
 def apply_h(grid: Grid, vloc: np.ndarray, vec: np.ndarray, sigma: complex = 0.0) -> np.ndarray:
-    """(H + sigma) vec for one complex grid function (matrix-free, Dirichlet)."""
+    """(H + sigma) vec for one complex grid function (matrix-free)."""
     w = fd_weights() / grid.h ** 2
     v = np.ascontiguousarray(vec, dtype=np.complex128)
     out = np.empty_like(v)
-    _lib().oracle_apply_h(grid.nx, grid.ny, grid.nz, RADIUS, _dp(w), _dp(np.ascontiguousarray(vloc)),
+    _lib().oracle_apply_h(grid.nx, grid.ny, grid.nz, RADIUS, _dp(w), int(grid.periodic),
+                          _dp(np.ascontiguousarray(vloc)),
                           float(np.real(sigma)), float(np.imag(sigma)),
                           _dp(v.view(np.float64)), _dp(out.view(np.float64)))
     return out
@@ -141,7 +147,8 @@ def cocg(grid: Grid, vloc: np.ndarray, sigma: np.ndarray, b: np.ndarray, tol: fl
     w = fd_weights() / grid.h ** 2
     sre = np.ascontiguousarray(sigma.real)
     sim = np.ascontiguousarray(sigma.imag)
-    _lib().oracle_cocg_batch(grid.nx, grid.ny, grid.nz, RADIUS, _dp(w), _dp(np.ascontiguousarray(vloc)), nsys,
+    _lib().oracle_cocg_batch(grid.nx, grid.ny, grid.nz, RADIUS, _dp(w), int(grid.periodic),
+                             _dp(np.ascontiguousarray(vloc)), nsys,
                              _dp(sre), _dp(sim), _dp(b.view(np.float64)), _dp(x.view(np.float64)),
                              float(tol), int(maxit), _ip(it), _ip(st))
     return x, it, st
@@ -150,29 +157,39 @@ def cocg(grid: Grid, vloc: np.ndarray, sigma: np.ndarray, b: np.ndarray, tol: fl
 # ------------------------------------------------------------------------------------
 # Coulomb operator by the Kronecker-product formalism (Section "Implementation")
 # ------------------------------------------------------------------------------------
-def second_difference_1d(n: int, h: float) -> np.ndarray:
-    """Dense 1D second-derivative matrix with zero boundary values (Toeplitz)."""
+def second_difference_1d(n: int, h: float, periodic: bool = False) -> np.ndarray:
+    """Dense 1D second-derivative matrix: zero boundary values (Toeplitz), or the periodic
+    continuation (circulant: every tap i +- k taken modulo n, so taps that wrap onto the same
+    point add up)."""
     w = fd_weights()
     D = np.zeros((n, n))
     for i in range(n):
-        for j in range(max(0, i - RADIUS), min(n, i + RADIUS + 1)):
-            D[i, j] = w[abs(i - j)] / h ** 2
+        D[i, i] += w[0] / h ** 2
+        for k in range(1, RADIUS + 1):
+            for j in (i - k, i + k):
+                if periodic:
+                    D[i, j % n] += w[k] / h ** 2
+                elif 0 <= j < n:
+                    D[i, j] += w[k] / h ** 2
     return D
 
 
 class Coulomb:
     """nu^p = (4 pi)^p (-L_h)^(-p) through -L_h = (Q_z x Q_y x Q_x) diag(mu_x+mu_y+mu_z) (...)^T,
-    with K_a = -D_a = Q_a diag(mu_a) Q_a^T the 1D eigendecompositions."""
+    with K_a = -D_a = Q_a diag(mu_a) Q_a^T the 1D eigendecompositions.  On a periodic grid the
+    one zero eigenvalue of -L_h (all three 1D constant modes) gets the factor 0."""
 
     def __init__(self, grid: Grid):
         self.grid = grid
         self.mu, self.Q = [], []
         for n in (grid.nx, grid.ny, grid.nz):
-            mu, Q = np.linalg.eigh(-second_difference_1d(n, grid.h))
+            mu, Q = np.linalg.eigh(-second_difference_1d(n, grid.h, grid.periodic))
             self.mu.append(mu)
             self.Q.append(Q)
         mx, my, mz = self.mu
         self.lam = mz[:, None, None] + my[None, :, None] + mx[None, None, :]
+        # the G = 0 mode: eigh returns the constant modes' zero eigenvalues to rounding
+        self.zero = self.lam <= 1e-9 * self.lam.max() if grid.periodic else np.zeros(self.lam.shape, bool)
 
     def apply(self, X: np.ndarray, power: float) -> np.ndarray:
         """nu^power applied to every row of X (K, N_d)."""
@@ -183,7 +200,8 @@ class Coulomb:
         Y = np.einsum("ia,kzyi->kzya", Qx, Y)
         Y = np.einsum("ja,kzjx->kzax", Qy, Y)
         Y = np.einsum("la,klyx->kayx", Qz, Y)
-        Y = Y * ((4.0 * math.pi) ** power * self.lam ** (-power))[None]
+        lam = np.where(self.zero, 1.0, self.lam)
+        Y = Y * np.where(self.zero, 0.0, (4.0 * math.pi) ** power * lam ** (-power))[None]
         # back: multiply by Q_a along each axis
         Y = np.einsum("ia,kzya->kzyi", Qx, Y)
         Y = np.einsum("ja,kzax->kzjx", Qy, Y)
@@ -212,8 +230,8 @@ class SolveStats:
 class Oracle:
     """One model system (grid, V_loc, occupied u_n and eps_n) and the method on it."""
 
-    def __init__(self, nx, ny, nz, h, vloc, psi, eps, n_atoms=1):
-        self.grid = Grid(int(nx), int(ny), int(nz), float(h))
+    def __init__(self, nx, ny, nz, h, vloc, psi, eps, n_atoms=1, periodic=False):
+        self.grid = Grid(int(nx), int(ny), int(nz), float(h), bool(periodic))
         self.vloc = np.ascontiguousarray(vloc, dtype=np.float64)
         self.psi = np.ascontiguousarray(psi, dtype=np.float64)   # (N_s, N_d)
         self.eps = np.asarray(eps, dtype=np.float64)
@@ -222,7 +240,7 @@ class Oracle:
 
     @classmethod
     def from_system(cls, s):
-        return cls(s.nx, s.ny, s.nz, s.h, s.vloc, s.psi, s.eps, s.n_atoms)
+        return cls(s.nx, s.ny, s.nz, s.h, s.vloc, s.psi, s.eps, s.n_atoms, getattr(s, "periodic", False))
 
     @property
     def n_s(self):

@@ -11,8 +11,8 @@ The paper computes its ground state with a full Kohn-Sham SCF (Section
 "Implementation": orbitals and eigenvalues are computed by the ground-state code,
 written to files and read back).  Pseudopotentials and SCF are outside the hot
 path, so the ground state here is the exact lowest eigenpairs of a model
-Hamiltonian  H = -1/2 L_h + diag(V_loc)  with Dirichlet (zero) boundary values and
-a 12th-order central finite-difference Laplacian L_h.  The finite-difference
+Hamiltonian  H = -1/2 L_h + diag(V_loc)  with Dirichlet (zero) boundary values, or
+periodic ones for a bulk cell, and a 12th-order central finite-difference Laplacian L_h.  The finite-difference
 weights are generated here by Fornberg's recursion (B. Fornberg, Math. Comp. 51
 (1988) 699), which is a different derivation from the closed form the oracle and
 the library use; a test checks that the orbitals produced here are eigenvectors
@@ -77,18 +77,29 @@ def fornberg_second_derivative(radius: int) -> np.ndarray:
     return w
 
 
-def _second_derivative_1d(n: int, h: float, w: np.ndarray) -> sp.csr_matrix:
+def _second_derivative_1d(n: int, h: float, w: np.ndarray, periodic: bool = False) -> sp.csr_matrix:
     radius = len(w) - 1
+    if periodic:
+        # circulant: entry (i, (i + o) mod n) for every offset o; wrapped taps that land on the
+        # same point are summed by the COO -> CSR conversion
+        rows, cols, vals = [], [], []
+        for o in range(-radius, radius + 1):
+            rows.append(np.arange(n))
+            cols.append((np.arange(n) + o) % n)
+            vals.append(np.full(n, w[abs(o)] / h ** 2))
+        return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(n, n)).tocsr()
     offsets = [o for o in range(-radius, radius + 1) if abs(o) < n]
     diags = [np.full(n - abs(o), w[abs(o)] / h ** 2) for o in offsets]
     return sp.diags(diags, offsets, shape=(n, n), format="csr")
 
 
-def _hamiltonian_sparse(nx: int, ny: int, nz: int, h: float, vloc: np.ndarray) -> sp.csr_matrix:
+def _hamiltonian_sparse(nx: int, ny: int, nz: int, h: float, vloc: np.ndarray,
+                        periodic: bool = False) -> sp.csr_matrix:
     w = fornberg_second_derivative(6)
-    dx = _second_derivative_1d(nx, h, w)
-    dy = _second_derivative_1d(ny, h, w)
-    dz = _second_derivative_1d(nz, h, w)
+    dx = _second_derivative_1d(nx, h, w, periodic)
+    dy = _second_derivative_1d(ny, h, w, periodic)
+    dz = _second_derivative_1d(nz, h, w, periodic)
     ix, iy, iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
     lap = (sp.kron(iz, sp.kron(iy, dx)) + sp.kron(iz, sp.kron(dy, ix))
            + sp.kron(dz, sp.kron(iy, ix)))
@@ -98,28 +109,37 @@ def _hamiltonian_sparse(nx: int, ny: int, nz: int, h: float, vloc: np.ndarray) -
 # --------------------------------------------------------------------------------------
 # Gaussian-well potentials
 # --------------------------------------------------------------------------------------
-def _grid_coords(n: int, h: float) -> np.ndarray:
-    # Interior points of the box [0, (n+1) h]; the walls carry the zero boundary values.
-    return (np.arange(n) + 1.0) * h
+def _grid_coords(n: int, h: float, periodic: bool = False) -> np.ndarray:
+    # Dirichlet: interior points of the box [0, (n+1) h], the walls carry the zero boundary
+    # values; periodic: the points of the cell [0, n h).
+    return np.arange(n) * h if periodic else (np.arange(n) + 1.0) * h
 
 
-def _potential(nx, ny, nz, h, centres, depths, widths) -> np.ndarray:
-    x, y, z = _grid_coords(nx, h), _grid_coords(ny, h), _grid_coords(nz, h)
+def _potential(nx, ny, nz, h, centres, depths, widths, periodic: bool = False) -> np.ndarray:
+    x, y, z = (_grid_coords(n, h, periodic) for n in (nx, ny, nz))
+    cell = (nx * h, ny * h, nz * h)
+    images = (-1, 0, 1) if periodic else (0,)
+
+    def gauss(t, c, s, length):
+        # a periodic cell sums the well's nearest images along the axis
+        return sum(np.exp(-((t - c - m * length) ** 2) / (2 * s * s)) for m in images)
+
     v = np.zeros((nz, ny, nx))
     for (cx, cy, cz), d, s in zip(centres, depths, widths):
-        gx = np.exp(-((x - cx) ** 2) / (2 * s * s))
-        gy = np.exp(-((y - cy) ** 2) / (2 * s * s))
-        gz = np.exp(-((z - cz) ** 2) / (2 * s * s))
+        gx, gy, gz = gauss(x, cx, s, cell[0]), gauss(y, cy, s, cell[1]), gauss(z, cz, s, cell[2])
         v -= d * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
     return v.reshape(-1)
 
 
-def _random_wells(rng, n_wells, box):
+def _random_wells(rng, n_wells, box, periodic: bool = False):
     depths = rng.uniform(1.0, 3.0, n_wells)
     widths = rng.uniform(0.8, 1.5, n_wells)
     centres = []
     for s in widths:
-        centres.append([rng.uniform(min(2.0 * s, 0.3 * b), b - min(2.0 * s, 0.3 * b)) for b in box])
+        if periodic:
+            centres.append([rng.uniform(0.0, b) for b in box])
+        else:
+            centres.append([rng.uniform(min(2.0 * s, 0.3 * b), b - min(2.0 * s, 0.3 * b)) for b in box])
     return np.array(centres), depths, widths
 
 
@@ -227,6 +247,7 @@ class System:
     psi: np.ndarray           # (N_s, N_d) float64, l2-orthonormal rows (u = psi_continuum h^{3/2})
     eps: np.ndarray           # (N_s,) float64, ascending, Hartree
     n_atoms: int
+    periodic: bool = False    # periodic cell (bulk) instead of zero boundary values
 
     @property
     def n_d(self) -> int:
@@ -261,33 +282,37 @@ _GEN_VERSION = "v2"
 
 
 def make_system(name: str, n: Sequence[int], h: float, n_s: int, seed: int, wells: str = "random",
-                n_wells: int = 4, gs_tol: float = 1e-8) -> System:
+                n_wells: int = 4, gs_tol: float = 1e-8, periodic: bool = False) -> System:
     """Build (or load from the on-disk cache) a seeded Gaussian-well system.
 
     wells="random": n_wells wells with depth U[1,3] Ha, width U[0.8,1.5] bohr and
     centres uniform in the box at least 2 widths from every wall.
     wells="rocksalt": 32 Li-like (3 Ha, 1.2 bohr) + 32 H-like (1.5 Ha, 0.9 bohr)
     wells on a 2x2x2 rock-salt lattice of constant 7.6 bohr, jittered by U[-0.1,0.1].
+    periodic: a periodic cell of n h per axis (wells summed over their nearest images, centres
+    uniform in the cell) instead of a box with zero boundary values.
     """
     nx, ny, nz = (int(v) for v in n)
     key = f"{_GEN_VERSION}|{name}|{nx},{ny},{nz}|{h!r}|{n_s}|{seed}|{wells}|{n_wells}|{gs_tol!r}"
+    if periodic:
+        key += "|periodic"
     digest = hashlib.sha1(key.encode()).hexdigest()[:16]
     cdir = _cache_dir()
     path = os.path.join(cdir, f"{name}_{digest}.npz") if cdir else None
     if path and os.path.exists(path):
         z = np.load(path)
-        return System(name, nx, ny, nz, h, z["vloc"], z["psi"], z["eps"], int(z["n_atoms"]))
+        return System(name, nx, ny, nz, h, z["vloc"], z["psi"], z["eps"], int(z["n_atoms"]), periodic)
 
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0]))
-    box = [(nx + 1) * h, (ny + 1) * h, (nz + 1) * h]
+    box = [nx * h, ny * h, nz * h] if periodic else [(nx + 1) * h, (ny + 1) * h, (nz + 1) * h]
     if wells == "random":
-        centres, depths, widths = _random_wells(rng, n_wells, box)
+        centres, depths, widths = _random_wells(rng, n_wells, box, periodic)
     elif wells == "rocksalt":
         centres, depths, widths = _rocksalt_wells(rng, box)
     else:
         raise ValueError(wells)
-    vloc = _potential(nx, ny, nz, h, centres, depths, widths)
-    H = _hamiltonian_sparse(nx, ny, nz, h, vloc)
+    vloc = _potential(nx, ny, nz, h, centres, depths, widths, periodic)
+    H = _hamiltonian_sparse(nx, ny, nz, h, vloc, periodic)
     if H.shape[0] <= 4096:
         eps, psi, gap = _dense_ground_state(H, n_s)
     else:
@@ -303,7 +328,7 @@ def make_system(name: str, n: Sequence[int], h: float, n_s: int, seed: int, well
         if psi[i, k] < 0:
             psi[i] = -psi[i]
     system = System(name, nx, ny, nz, h, vloc, np.ascontiguousarray(psi), np.asarray(eps, dtype=np.float64),
-                    len(depths))
+                    len(depths), periodic)
     if path:
         tmp = path + f".tmp{os.getpid()}"
         with open(tmp, "wb") as f:
@@ -315,12 +340,13 @@ def make_system(name: str, n: Sequence[int], h: float, n_s: int, seed: int, well
 def hamiltonian_matrix(system: System) -> sp.csr_matrix:
     """The model Hamiltonian that defines the ground-state problem, as a sparse matrix
     (assembled from Kronecker sums of 1D Fornberg-weight matrices)."""
-    return _hamiltonian_sparse(system.nx, system.ny, system.nz, system.h, system.vloc)
+    return _hamiltonian_sparse(system.nx, system.ny, system.nz, system.h, system.vloc, system.periodic)
 
 
-def laplacian_matrix(nx: int, ny: int, nz: int, h: float) -> sp.csr_matrix:
-    """The Dirichlet finite-difference Laplacian of the model problem, as a sparse matrix."""
-    return -2.0 * _hamiltonian_sparse(nx, ny, nz, h, np.zeros(nx * ny * nz))
+def laplacian_matrix(nx: int, ny: int, nz: int, h: float, periodic: bool = False) -> sp.csr_matrix:
+    """The finite-difference Laplacian of the model problem (Dirichlet or periodic), as a sparse
+    matrix."""
+    return -2.0 * _hamiltonian_sparse(nx, ny, nz, h, np.zeros(nx * ny * nz), periodic)
 
 
 def trial_vectors(seed: int, n_r: int, n_d: int) -> np.ndarray:
@@ -351,17 +377,23 @@ WORKLOADS = {
     # 32^3, h=0.45, 8 wells, 8 orbitals, N_r=32, N_omega=6 (adjoint)
     "adjoint32": dict(n=(32, 32, 32), h=0.45, n_s=8, n_wells=8, wells="random", n_r=32, n_omega=6,
                       tol=1e-8, eps_c=1e-7, seed=3),
+    # periodic 40^3 cell, h=0.4, 16 wells, 16 orbitals, N_r=64, N_omega=8 (mixed40's sizes, bulk
+    # boundary conditions)
+    "bulk40": dict(n=(40, 40, 40), h=0.4, n_s=16, n_wells=16, wells="random", n_r=64, n_omega=8,
+                   tol=1e-8, eps_c=1e-6, seed=4, periodic=True),
 }
 
 
 def workload(name: str, **overrides) -> Workload:
     p = dict(WORKLOADS[name])
     p.update(overrides)
-    sys_ = make_system(name, p["n"], p["h"], p["n_s"], p["seed"], wells=p["wells"], n_wells=p["n_wells"])
+    sys_ = make_system(name, p["n"], p["h"], p["n_s"], p["seed"], wells=p["wells"], n_wells=p["n_wells"],
+                       periodic=p.get("periodic", False))
     return Workload(sys_, p["n_r"], p["n_omega"], p["tol"], p["eps_c"], p["seed"])
 
 
 def small_system(n: Tuple[int, int, int] = (8, 8, 8), h: float = 0.5, n_s: int = 2, n_wells: int = 2,
-                 seed: int = 11) -> System:
+                 seed: int = 11, periodic: bool = False) -> System:
     """Tiny system for brute-force checks (dense diagonalisation is cheap)."""
-    return make_system(f"small{n[0]}x{n[1]}x{n[2]}", n, h, n_s, seed, wells="random", n_wells=n_wells)
+    return make_system(f"small{n[0]}x{n[1]}x{n[2]}", n, h, n_s, seed, wells="random", n_wells=n_wells,
+                       periodic=periodic)

@@ -16,8 +16,8 @@ def dense_h(system):
     return synth.hamiltonian_matrix(system).toarray()
 
 
-def dense_minus_laplacian(nx, ny, nz, h):
-    return -synth.laplacian_matrix(nx, ny, nz, h).toarray()
+def dense_minus_laplacian(nx, ny, nz, h, periodic=False):
+    return -synth.laplacian_matrix(nx, ny, nz, h, periodic).toarray()
 
 
 def full_spectrum(system):
@@ -42,14 +42,18 @@ def chi0_sum_over_states(system, omega):
     return (4.0 / system.h ** 3) * X
 
 
-def nu_power_dense(nx, ny, nz, h, power):
-    """(4 pi)^p (-L_h)^{-p} by a dense symmetric eigendecomposition."""
-    mu, Q = np.linalg.eigh(dense_minus_laplacian(nx, ny, nz, h))
-    return (Q * ((4.0 * math.pi) ** power * mu ** (-power))) @ Q.T
+def nu_power_dense(nx, ny, nz, h, power, periodic=False):
+    """(4 pi)^p (-L_h)^{-p} by a dense symmetric eigendecomposition; on a periodic grid the
+    pseudo-inverse power (the null space of -L_h, the constant function, maps to zero)."""
+    mu, Q = np.linalg.eigh(dense_minus_laplacian(nx, ny, nz, h, periodic))
+    keep = mu > 1e-9 * mu.max() if periodic else np.ones(mu.shape, bool)
+    f = np.zeros_like(mu)
+    f[keep] = (4.0 * math.pi) ** power * mu[keep] ** (-power)
+    return (Q * f) @ Q.T
 
 
 def chi_tilde_dense(system, omega):
-    nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5)
+    nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5, system.periodic)
     return nh @ chi0_sum_over_states(system, omega) @ nh
 
 
@@ -61,7 +65,7 @@ def chi0_projected_sos(system, vloc, omega):
     At the potential the orbitals belong to, this is the sum over states of Eq. 2."""
     import scipy.linalg as sla
     s2 = synth.System(system.name, system.nx, system.ny, system.nz, system.h, np.asarray(vloc),
-                      system.psi, system.eps, system.n_atoms)
+                      system.psi, system.eps, system.n_atoms, system.periodic)
     H = dense_h(s2)
     Q = sla.null_space(system.psi)
     e, Z = np.linalg.eigh(Q.T @ H @ Q)
@@ -78,7 +82,7 @@ def chi0_projected_sos(system, vloc, omega):
 def ec_projected_dense(system, vloc, n_r, omegas, weights):
     """E_c = (1/2pi) sum_m w_m sum_{i < n_r} g(lambda_i) over the n_r lowest eigenvalues of
     nu^1/2 chi0 nu^1/2, chi0 from chi0_projected_sos."""
-    nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5)
+    nh = nu_power_dense(system.nx, system.ny, system.nz, system.h, 0.5, system.periodic)
     e = 0.0
     for om, w in zip(omegas, weights):
         lam = np.linalg.eigvalsh(nh @ chi0_projected_sos(system, vloc, om) @ nh)[:n_r]
