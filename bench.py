@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mixed40")
+    ap.add_argument("--stencil-shape", type=int, default=-1,
+                    help="rpa_options.stencil_shape for the timed steps (-1: the autotuner's choice)")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -300,6 +302,7 @@ def run_ours(args):
     opts.fixed_subspace_iters = 1
     opts.n_atoms = s.n_atoms
     opts.profile = 0                           # the timed steps run without per-launch events
+    opts.periodic = int(getattr(s, "periodic", False))   # the system's boundary conditions
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = rpa.Context.from_system(s, opts)
@@ -323,7 +326,10 @@ def run_ours(args):
     # autotuner: choose the COCG kernel configuration on this workload (one chi~0 application
     # per candidate at a middle frequency), outside the timed region
     tune = None
-    if args.prec == "mixed" and not args.no_autotune:
+    if args.stencil_shape >= 0:                # a fixed kernel configuration (profiler captures)
+        opts.stencil_shape = args.stencil_shape
+        ctx.set_options(opts)
+    elif args.prec == "mixed" and not args.no_autotune:
         om_mid = ctx_omegas(w.n_omega)[w.n_omega // 2]
         chosen, names, times = ctx.autotune(om_mid, V0)
         opts.stencil_shape, opts.z_chunks = ctx.options.stencil_shape, ctx.options.z_chunks
@@ -378,7 +384,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "c64+f64 (mixed)" if args.prec == "mixed" else "c128 (f64)", "data": "synthetic",
-                "config": {"workload": f"{args.workload}: {s.nx}^3 Dirichlet grid h={s.h} bohr, "
+                "config": {"workload": f"{args.workload}: {s.nx}^3 {'periodic' if s.periodic else 'Dirichlet'} "
+                                       f"grid h={s.h} bohr, "
                                        f"{s.n_atoms} Gaussian wells, N_s={s.n_s}, N_r={w.n_r}, N_omega={w.n_omega}, "
                                        f"{args.prec}, COCG tol {args.tol:g}; step = 1 subspace iteration at every "
                                        f"frequency ({s.n_s * w.n_r * w.n_omega} Sternheimer solves)",
@@ -398,7 +405,7 @@ def run_ours(args):
                 "e_c_per_atom_last_step": res.e_c_per_atom}
     if not args.no_fp64 and rank == 0:
         o64 = rpa.default_options()
-        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms"):
+        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "periodic"):
             setattr(o64, k, getattr(opts, k))
         o64.prec = rpa.RPA_FP64
         r64, ms64 = timed_ec(o64)
@@ -414,7 +421,7 @@ def run_ours(args):
         tts = {}
         for name, prec in (("mixed", rpa.RPA_MIXED), ("fp64", rpa.RPA_FP64)):
             ot = rpa.default_options()
-            for k in ("tol", "n_omega", "n_atoms", "stencil_shape", "z_chunks"):
+            for k in ("tol", "n_omega", "n_atoms", "stencil_shape", "z_chunks", "periodic"):
                 setattr(ot, k, getattr(opts, k))
             ot.prec = prec
             ot.eps_c = 1e-5

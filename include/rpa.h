@@ -89,12 +89,17 @@ typedef struct {
                                   block; 2 = one column per thread, up to 320 threads, two blocks per
                                   SM; 3 = two columns per thread, up to 384 threads.  4 = one fused
                                   kernel per iteration, one block per system with whole xy planes in
-                                  a shared-memory ring (grids whose nx*ny plane fits, about 2000
-                                  points; else as 1).  5 = the fused kernel warp-specialised: producer
+                                  a shared-memory ring (grids whose nx*ny plane fits, about 1800
+                                  points); where a plane does not fit, its cluster form (below); where
+                                  neither fits, as 1.  5 = the fused kernel warp-specialised: producer
                                   threads form the next plane while consumer threads apply the
                                   stencil (planes of up to ~416 blocks of 2 x 2 points; else as 4).
-                                  0 = automatic: 4 where it fits, else 1.  rpa_autotune sets it.  The
-                                  plain FP64 form always uses 1. */
+                                  6 = the fused kernel's cluster form: the 2..8 blocks of a thread-
+                                  block cluster split every plane into bands of row pairs and read
+                                  the rows past their band from each other's shared memory, here
+                                  with rings small enough for two blocks per SM (else as 4).
+                                  0 = automatic: as 4.  rpa_autotune sets it.  The plain FP64 form
+                                  always uses 1; periodic grids run 4 (even nx) or 1. */
     int independent_frequencies; /* != 0: every frequency starts from V0 instead of the subspace of
                                   the next higher frequency (no warm start, Algorithm 1 carries it);
                                   with fixed_subspace_iters = 1 E_c is then the Rayleigh-Ritz energy
@@ -109,10 +114,13 @@ typedef struct {
                                   step -- the Kronecker per-axis transforms of nu^1/2, the P_c
                                   coefficients and C = V^T R: 0 = automatic (tensor cores in the mixed
                                   form, FP64 in the plain form); 1 = FP64 on CUDA cores; 2 = tensor
-                                  cores (tcgen05: six products of BF16 splits of the FP64 operands,
-                                  FP32 accumulation over k chunks of 64, chunk sums in FP64; ~1e-7
-                                  relative).  The overlap R^T R, the rotation V = R L^-T, Cholesky,
-                                  the eigensolve and rpa_coulomb_apply always use FP64. */
+                                  cores (tcgen05: in every k chunk of 64 each row of each operand is
+                                  scaled by a power of two and cut into four integer pieces of at most
+                                  8 bits; the ten products of pieces that matter accumulate exactly in
+                                  FP32 and are combined in FP64; ~1e-8 relative); 3 = tensor cores
+                                  except the Kronecker transforms.  The overlap R^T R, the rotation
+                                  V = R L^-T, Cholesky, the eigensolve and rpa_coulomb_apply always
+                                  use FP64. */
     int omega_first;           /* frequency range of this call (ascending index into the n_omega   */
     int omega_count;           /* Gauss-Legendre nodes): rpa_ec / rpa_ec_gradient evaluate only the
                                   frequencies omega_first .. omega_first + omega_count - 1 (count 0 =
@@ -121,6 +129,12 @@ typedef struct {
                                   partition of the frequencies give, summed, exactly the E_c of one
                                   call over all of them: frequency sharding across processes (the
                                   paper's frequencies are independent but for the warm start). */
+    int periodic;              /* boundary conditions, fixed at rpa_setup (rpa_set_options rejects a
+                                  change): 0 = zero values outside the box (Dirichlet); 1 = periodic
+                                  in x, y and z (a bulk cell, the paper's Section "Results"): the
+                                  stencil takes the periodic continuation of every grid function,
+                                  and nu^p acts with the G = 0 mode removed (the constant function
+                                  maps to zero: the neutralising background of a periodic cell). */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8
@@ -160,7 +174,7 @@ typedef struct {
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
  * profile 0, project_solution 0, z_chunks 0, stencil_shape 0 (automatic), independent_frequencies 0,
- * sq_order 0, contractions 0 (automatic), omega_first 0, omega_count 0 (all frequencies). */
+ * sq_order 0, contractions 0 (automatic), omega_first 0, omega_count 0 (all frequencies), periodic 0. */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).
@@ -253,7 +267,7 @@ rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *i
                                      int ncols, void *stream);
 
 /* Number of configurations rpa_autotune times. */
-#define RPA_AUTOTUNE_CANDIDATES 8
+#define RPA_AUTOTUNE_CANDIDATES 9
 
 /* Autotuner: times one application of nu^1/2 chi0(i omega) nu^1/2 to the n_r columns of V_dev
  * for each candidate configuration of the COCG kernels and keeps the fastest for this context by
@@ -261,8 +275,8 @@ rpa_status rpa_coulomb_apply_noalloc(rpa_ctx *ctx, double power, const double *i
  * stencil_shape = 1, 2, 3 (columns per thread and threads per block, i.e. the xy tile shape)
  * crossed with one or two z chunks per column, index 2 (stencil_shape - 1) + (z_chunks - 1);
  * candidate 6: the fused single-pass kernel (stencil_shape 4); candidate 7: its warp-specialised
- * form (stencil_shape 5).  The plain FP64 form has one
- * configuration (candidate 0).  times_ms_host (may be NULL) receives RPA_AUTOTUNE_CANDIDATES
+ * form (stencil_shape 5); candidate 8: its cluster form with two blocks per SM (stencil_shape 6).
+ * The plain FP64 form has one configuration (candidate 0).  times_ms_host (may be NULL) receives RPA_AUTOTUNE_CANDIDATES
  * timings, -1 for a candidate that does not apply; *chosen_host (may be NULL) the index of the
  * chosen one.  The context's results do not depend on the choice beyond rounding. */
 rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r, int *chosen_host,

@@ -157,9 +157,10 @@ void validate_options(const rpa_options &o) {
     if (o.n_atoms < 1) fail(RPA_ERR_INVALID, "n_atoms must be >= 1");
     if (o.batch_systems < 0) fail(RPA_ERR_INVALID, "batch_systems must be >= 0");
     if (o.z_chunks < 0 || o.z_chunks > 64) fail(RPA_ERR_INVALID, "z_chunks must be in [0, 64]");
-    if (o.stencil_shape < 0 || o.stencil_shape > 5) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 5]");
+    if (o.stencil_shape < 0 || o.stencil_shape > 6) fail(RPA_ERR_INVALID, "stencil_shape must be in [0, 6]");
     if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
     if (o.contractions < 0 || o.contractions > 3) fail(RPA_ERR_INVALID, "contractions must be in [0, 3]");
+    if (o.periodic != 0 && o.periodic != 1) fail(RPA_ERR_INVALID, "periodic must be 0 or 1");
     if (o.omega_count < 0 || o.omega_first < 0 || (o.omega_count > 0 && o.omega_first + o.omega_count > o.n_omega) ||
         (o.omega_count == 0 && o.omega_first != 0))
         fail(RPA_ERR_INVALID, "omega_first/omega_count must select a range of the n_omega frequencies");
@@ -320,6 +321,7 @@ void rpa_default_options(rpa_options *o) {
     o->contractions = 0;
     o->omega_first = 0;
     o->omega_count = 0;
+    o->periodic = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }
@@ -403,6 +405,8 @@ rpa_status rpa_set_options(rpa_ctx *ctx, const rpa_options *opt) {
     return guarded([&] {
         if (!ctx || !opt) fail(RPA_ERR_INVALID, "NULL argument");
         validate_options(*opt);
+        if (opt->periodic != ctx->impl.opt.periodic)
+            fail(RPA_ERR_INVALID, "periodic is fixed at rpa_setup (the Coulomb operator is built for it)");
         ctx->impl.opt = *opt;
     });
 }
@@ -468,17 +472,19 @@ rpa_status rpa_autotune(rpa_ctx *ctx, double omega, const double *V_dev, int n_r
         double *R = (double *)c.blockC.ensure(blk);
         // candidates 0..5: split kernel variant v (stencil_shape v + 1) with z chunks z + 1, index
         // 2 v + z; candidate 6: the fused single-pass kernel (stencil_shape 4), candidate 7 its
-        // warp-specialised form (stencil_shape 5), where a plane fits
+        // warp-specialised form (stencil_shape 5), where a plane fits; candidate 8 its cluster form
+        // with two blocks per SM (stencil_shape 6), where the plane's bands fit
         const bool mixed = c.opt.prec == RPA_MIXED;
         const bool fused_ok = mixed && fused_kernel_applies(c);
         const bool ws_ok = mixed && fused_kernel_applies(c, true);
+        const bool cl_ok = mixed && fused_kernel_applies(c, false, true);
         double best = 1e300;
         int best_i = 0;
         cudaEvent_t a, b;
         RPA_CUDA(cudaEventCreate(&a));
         RPA_CUDA(cudaEventCreate(&b));
         for (int i = 0; i < RPA_AUTOTUNE_CANDIDATES; ++i) {
-            const bool run = i == 7 ? ws_ok : i == 6 ? fused_ok : (mixed || i == 0);
+            const bool run = i == 8 ? cl_ok : i == 7 ? ws_ok : i == 6 ? fused_ok : (mixed || i == 0);
             double ms = -1.0;
             if (run) {
                 c.opt.stencil_shape = i >= 6 ? i - 2 : i / 2 + 1;

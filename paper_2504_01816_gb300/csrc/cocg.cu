@@ -27,6 +27,8 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 namespace rpa {
@@ -67,7 +69,14 @@ template <> struct Cx<double> { using t = double2; };
 struct Grid3 {
     int nx, ny, nz;
     long long nd;
+    int periodic;                  // 1: periodic continuation outside the box, 0: zero values
 };
+
+// Grid index a (any integer) along an axis of n points, taken into [0, n) (periodic grids).
+__device__ __forceinline__ int wrap_index(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
 
 template <typename T> struct Coef {
     T a[kRadius + 1];
@@ -123,6 +132,7 @@ struct IterArgs {
     long long nd;
     int nx, ny, nz;
     int nper;                      // work items per slot (stencil tiles, or chunks)
+    int periodic;                  // 1: periodic continuation outside the box, 0: zero values
 };
 
 // Sum N doubles over the block; the result is valid in thread 0.  Fixed order.
@@ -402,10 +412,14 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const long long items = (long long)*A.cnt * ntiles;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const int plane = nx * ny;                    // grid functions have < 2^31 points
-    // with one tile across x the left/right strips lie outside the box: zero, never loaded
-    const bool sides = tl.ntx > 1;
+    // with one tile across x the left/right strips lie outside the box: zero, never loaded (on a
+    // periodic grid they hold the wrapped columns)
+    const bool per = A.periodic != 0;
+    const bool sides = tl.ntx > 1 || per;
     const int nhalo = sides ? 2 * R * (tl.tx + tl.ty) : 2 * R * tl.tx;
     const C zero = {(T)0, (T)0};
+    // plane z of the column window: itself, its periodic image, or -1 (outside: zero)
+    auto zplane = [&](int z) -> int { return (z >= 0 && z < nz) ? z : (per ? wrap_index(z, nz) : -1); };
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int s = A.list[(int)(it / ntiles)], tile = (int)(it % ntiles);
         const Slot &sl = A.slots[s];
@@ -442,7 +456,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 hy = e2 - cc * tl.ty + R;
                 hx = cc < R ? cc : tl.tx + cc;
             }
-            const int ax = x0 + hx - R, ay = y0 + hy - R;
+            int ax = x0 + hx - R, ay = y0 + hy - R;
+            if (per) {
+                ax = wrap_index(ax, nx);
+                ay = wrap_index(ay, ny);
+            }
             foff = hy * W + hx;
             goff = (ax >= 0 && ax < nx && ay >= 0 && ay < ny) ? ay * nx + ax : -1;
         };
@@ -474,13 +492,13 @@ __global__ void __launch_bounds__(MAXT, MINB)
         C qv[2 * R + 1];
 #pragma unroll
         for (int m = 0; m < 2 * R + 1; ++m) {
-            const int z = zb + m - R;
-            qv[m] = (own && z >= 0 && z < nz) ? pnew(rs[col + z * plane], po[col + z * plane]) : zero;
+            const int z = zplane(zb + m - R);
+            qv[m] = (own && z >= 0) ? pnew(rs[col + z * plane], po[col + z * plane]) : zero;
         }
         C f1r = zero, f1p = zero;          // raw front of plane z+R+1, consumed at the end of step z
-        if (own && zb + R + 1 < nz) {
-            f1r = rs[col + (zb + R + 1) * plane];
-            f1p = po[col + (zb + R + 1) * plane];
+        if (own && zplane(zb + R + 1) >= 0) {
+            f1r = rs[col + zplane(zb + R + 1) * plane];
+            f1p = po[col + zplane(zb + R + 1) * plane];
         }
         T vnext = own ? vloc[col + zb * plane] : (T)0;  // potential of the next plane
         T acc0 = 0, acc1 = 0;              // per-thread sums in the working precision (FP64 is slow)
@@ -511,9 +529,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
                         }
                 }
                 C f2r = zero, f2p = zero;
-                if (own && z + R + 2 < nz) {
-                    f2r = rs[col + (z + R + 2) * plane];
-                    f2p = po[col + (z + R + 2) * plane];
+                if (own && zplane(z + R + 2) >= 0) {
+                    f2r = rs[col + zplane(z + R + 2) * plane];
+                    f2p = po[col + zplane(z + R + 2) * plane];
                 }
                 const T vz = vnext;                          // potential of plane z (loaded one plane ago)
                 if (own && z + 1 < ze) vnext = vloc[col + (z + 1) * plane];
@@ -542,7 +560,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
 
                 }
                 // the front loaded one plane ago takes the slot of plane z-6
-                qv[u] = (own && z + R + 1 < nz) ? pnew(f1r, f1p) : zero;
+                qv[u] = (own && zplane(z + R + 1) >= 0) ? pnew(f1r, f1p) : zero;
                 f1r = f2r;
                 f1p = f2p;
             }
@@ -809,14 +827,24 @@ __global__ void __launch_bounds__(MAXT, 1)
 // One block owns one system and marches along z.  At step f it forms x, r, p of plane f
 // ("front", loaded one plane ahead into registers), writes them back, and stores p_k of the
 // plane into a ring of kRingPlanes planes in shared memory; after one barrier it applies the
-// 12th-order stencil to plane f-6, whose 6 planes on either side are in the ring.  Rows of a
-// ring plane are padded with kRingPad zero columns, so x neighbours past the box read zeros;
-// y neighbours past the box are predicated off; ring planes outside [0, nz) hold zeros.  A
-// thread owns two x-adjacent points, so a ring access is one 16-byte load for both.  With 14
-// ring planes the plane written at step f+1 is the one read last at step f-1, so one barrier
-// per step suffices.  Each block handles whole systems, so the state is single-buffered: a
-// thread reads q at plane f six steps before it writes q there, and reads back r_k of plane
-// f-6 that it wrote itself.
+// 12th-order stencil to plane f-6, whose 6 planes on either side are in the ring.  A thread owns
+// 2 x 2 points (x, x+1; y, y+1), so a ring access is one 16-byte load for both x points, and rows
+// y and y+1 share their y neighbours.  Ring layout (complex elements): a 16-byte zero
+// word at the start of every plane, then its rows of 2 hw elements, each followed by a few unused
+// elements so that two rows span hw 16-byte words modulo 8 (for even hw): the 16-byte words of
+// consecutive units then fall in consecutive bank groups across row pairs, and a quarter warp's
+// 16-byte loads are free of bank conflicts.  Neighbours past the box in x or y are read from the
+// zero word (x: per-unit masks; y: predicated addresses); ring planes outside [0, nz) hold zeros.
+// With 14 ring planes the plane written at step f+1 is the one read last at step f-1, so one
+// barrier per step suffices.  Each block handles whole systems, so the state is single-buffered:
+// a thread reads q at plane f six steps before it writes q there, and reads back r_k of plane f-6
+// that it wrote itself.
+//
+// Periodic grids (PER; nx even, so that the point pairs wrap onto point pairs): x and y neighbours
+// are read at their periodic images in the ring; at the start of a sweep the ring slots of planes
+// -6 .. -1 receive p_k of planes nz-6 .. nz-1, formed from their old values as the front would form
+// them (not written back: the front forms them again at their own steps), and at steps f >= nz the
+// ring receives p_k of plane f - nz, read back from the direction this thread wrote at step f - nz.
 //
 // Because a block holds every sum of its system, it takes the scalar step itself and goes on
 // with the next sweep: one launch runs each system of the active list through its whole inner
@@ -825,7 +853,6 @@ __global__ void __launch_bounds__(MAXT, 1)
 // list is taken from its end (it is in slot order, i.e. by orbital, and the highest orbitals,
 // nearest the unoccupied spectrum, need the most iterations: the longest solves start first).
 constexpr int kRingPlanes = 14;
-constexpr int kRingPad = 6;
 constexpr int kRingMaxThreads = 512;
 constexpr int kRingWsMaxThreads = 672;     // consumers + producers (planes of up to 416 units)
 
@@ -841,14 +868,22 @@ struct RingArgs {
     int nx, ny, nz;
     int hw;                        // point pairs per row: ceil(nx / 2)
     int hh;                        // row pairs: ceil(ny / 2)
-    int rs;                        // ring row stride (complex elements): 2 hw + kRingPad
-    int ps;                        // ring plane stride (complex elements): ny rs + kRingPad
+    int rs;                        // ring row stride (complex elements): 2 hw + ring_row_pad(hw)
+    int ps;                        // ring plane stride: 2 + ny rs (the zero word, then the rows);
+                                   // cluster form: 2 + 2 bp rs (the block's band)
+    int bp;                        // cluster form: row pairs per band (the last band may hold fewer)
 };
 
+// Unused elements after each ring row: even, and for even hw the smallest that makes two rows span
+// hw 16-byte words modulo 8.
+inline int ring_row_pad(int hw) {
+    const int p = (8 - hw % 8) % 8;
+    return p + (p & 1);
+}
 // Shared-memory bytes of the ring for an nx x ny plane.
 inline size_t ring_bytes(int nx, int ny) {
-    const size_t hw = (size_t)(nx + 1) / 2;
-    return (size_t)kRingPlanes * ((size_t)ny * (2 * hw + kRingPad) + kRingPad) * sizeof(float2);
+    const int hw = (nx + 1) / 2;
+    return (size_t)kRingPlanes * (2 + (size_t)ny * (2 * hw + ring_row_pad(hw))) * sizeof(float2);
 }
 
 __device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
@@ -938,21 +973,27 @@ struct RingUnit {
     bool own, hasb, row1;          // a unit of the plane; point x+1 and row y+1 inside the box
     int gy, col0, col1;            // row; in-plane indices of (x, y) and (x, y+1)
     int rb0, rb1, rb1z;            // ring byte offsets of rows y and y+1 (rb1z: 0 if row y+1 is outside)
+    int xm;                        // bit m: x load m (point pair x/2 - 3 + m) lies inside the row
+    int bx;                        // point pair of the unit in its row: x / 2
 };
 
-__device__ __forceinline__ RingUnit ring_unit(int u, const RingArgs &A) {
+// Unit u of a ring that holds the npairs row pairs from row y0 on (a whole plane: y0 = 0, npairs = hh).
+__device__ __forceinline__ RingUnit ring_unit(int u, const RingArgs &A, int y0 = 0, int npairs = -1) {
     RingUnit r;
-    r.own = u >= 0 && u < A.hw * A.hh;
+    r.own = u >= 0 && u < A.hw * (npairs < 0 ? A.hh : npairs);
     const int by = r.own ? u / A.hw : 0;
     const int gx = r.own ? 2 * (u - by * A.hw) : 0;
-    r.gy = 2 * by;
+    r.gy = y0 + 2 * by;
     r.hasb = r.own && gx + 1 < A.nx;
     r.row1 = r.own && r.gy + 1 < A.ny;
     r.col0 = r.gy * A.nx + gx;
     r.col1 = r.col0 + A.nx;
-    r.rb0 = r.gy * A.rs * 8 + (kRingPad + gx) * 8;
+    r.rb0 = (2 + (r.gy - y0) * A.rs + gx) * 8;
     r.rb1 = r.rb0 + A.rs * 8;
     r.rb1z = r.row1 ? r.rb1 : 0;
+    const int xlo = max(0, 3 - gx / 2), xhi = min(6, A.hw + 2 - gx / 2);
+    r.xm = ((1 << (xhi + 1)) - 1) & ~((1 << xlo) - 1);
+    r.bx = gx / 2;
     return r;
 }
 
@@ -1033,6 +1074,34 @@ __device__ __forceinline__ void ring_front(const RingUnit &U, int f, int nz, int
     if (U.row1) *reinterpret_cast<float4 *>(slot + U.rb1) = make_float4(pk[2].x, pk[2].y, pk[3].x, pk[3].y);
 }
 
+// Periodic grids: p_k of a unit at a plane from its raw values (as ring_front forms it), into a ring
+// slot only: nothing is written back and nothing summed.
+template <bool EVEN>
+__device__ __forceinline__ void ring_halo_plane(const RingUnit &U, bool first, float alr, float ali, float ber,
+                                                float bei, const RingFront &F, unsigned char *slot) {
+    const float2 zero = make_float2(0.f, 0.f);
+    float2 pk[4];
+    const float2 N1 = make_float2(-alr, -alr), N2 = make_float2(ali, -ali);
+    const float2 B1 = make_float2(ber, ber), B2 = make_float2(-bei, bei);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pk[i] = first ? F.r[i] : cax(cax(F.r[i], N1, N2, F.q[i]), B1, B2, F.p[i]);
+    if (!U.hasb) pk[1] = pk[3] = zero;
+    if (!U.row1) pk[2] = pk[3] = zero;
+    *reinterpret_cast<float4 *>(slot + U.rb0) = make_float4(pk[0].x, pk[0].y, pk[1].x, pk[1].y);
+    if (U.row1) *reinterpret_cast<float4 *>(slot + U.rb1) = make_float4(pk[2].x, pk[2].y, pk[3].x, pk[3].y);
+}
+
+// Periodic grids: p_k of a unit at plane z (< the step's plane, so formed and written by this
+// thread earlier in the sweep) from global memory into a ring slot.
+template <bool EVEN>
+__device__ __forceinline__ void ring_wrap_front(const RingUnit &U, int g0, const float2 *psv, unsigned char *slot) {
+    float2 a, b, c = make_float2(0.f, 0.f), d = c;
+    ld_pair<EVEN>(psv, g0, U.hasb, a, b);
+    if (U.row1) ld_pair<EVEN>(psv, g0 + (U.col1 - U.col0), U.hasb, c, d);
+    *reinterpret_cast<float4 *>(slot + U.rb0) = make_float4(a.x, a.y, b.x, b.y);
+    if (U.row1) *reinterpret_cast<float4 *>(slot + U.rb1) = make_float4(c.x, c.y, d.x, d.y);
+}
+
 // r_k and V of a unit at plane z (r_k written at the step that formed plane z).
 template <bool EVEN>
 __device__ __forceinline__ void ring_load_rv(const RingUnit &U, int g0, const float2 *rsv, const float *vloc,
@@ -1048,29 +1117,77 @@ __device__ __forceinline__ void ring_load_rv(const RingUnit &U, int g0, const fl
     }
 }
 
+// Cluster form: the rows of a block's band, [y0, y1), and the same ring slot in this block and in
+// the blocks of the bands above and below, as shared::cluster addresses (a shared::cta address is
+// one for the executing block).
+struct Band {
+    int y0, y1, rows;              // rows: 2 bp, the height of every band but the last
+    unsigned self, up, dn;
+};
+
+// Two x-adjacent points from a ring slot of any block of the cluster: one 16-byte load.
+__device__ __forceinline__ void ring_pair_cl(unsigned addr, float2 &a, float2 &b) {
+    float4 t;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(t.x), "=f"(t.y), "=f"(t.z), "=f"(t.w)
+                 : "r"(addr)
+                 : "memory");
+    a = make_float2(t.x, t.y);
+    b = make_float2(t.z, t.w);
+}
+
 // q_k = (H + sigma) p_k on plane z for a unit, from the ring (cz: the ring slot of plane z), stored;
-// sums pi = p_k^T q_k, tau = r_k^T q_k, theta = q_k^T q_k (acc[0..5]).
-template <bool EVEN>
-__device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned char *ring, int psb, int rsb, int ny,
-                                             int cz, int gq0, const float2 (&rk)[4], const float (&vv)[4], float shr,
-                                             float shi, const Coef<float> &cf, float2 *qs, float (&acc)[6]) {
+// sums pi = p_k^T q_k, tau = r_k^T q_k, theta = q_k^T q_k (acc[0..5]); rk, vv: r_k and V of the
+// unit's points (V's term of the diagonal is added last).  A variant that loaded each row of y
+// neighbours once for both rows (12 loads instead of 22) and one that loaded r_k and V inside this
+// function both measured slower: the values they keep live spill registers.
+template <bool EVEN, bool PER, bool BAND = false>
+__device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned char *ring, int psb, int rsb, int hw,
+                                             int ny, int cz, int gq0, const float2 (&rk)[4], const float (&vv)[4],
+                                             float shr, float shi, const Coef<float> &cf, float2 *qs,
+                                             float (&acc)[6], const Band &B = Band{}) {
     const float2 zero = make_float2(0.f, 0.f);
     const unsigned char *const pz = ring + cz * psb;
+    // row r of the plane (periodic: its image; cluster form: in this block's band or a neighbour's;
+    // else the zero word outside the box)
+    auto row = [&](int r) -> const unsigned char * {
+        if (PER) return pz + U.rb0 + (wrap_index(r, ny) - U.gy) * rsb;
+        return (r >= 0 && r < ny) ? pz + U.rb0 + (r - U.gy) * rsb : pz;
+    };
+    // cluster form: row r in this block's band or a neighbour's, or the zero word outside the box,
+    // all through shared::cluster addresses (one load instruction for every case: a branch between
+    // shared and distributed shared loads measured more spills)
+    auto yrow = [&](int r, float2 &a, float2 &b) {
+        if (BAND) {
+            unsigned ad = B.self;
+            if (r >= 0 && r < ny) {
+                if (r < B.y0) ad = B.up + U.rb0 + (r - U.gy + B.rows) * rsb;
+                else if (r >= B.y1) ad = B.dn + U.rb0 + (r - U.gy - (B.y1 - B.y0)) * rsb;
+                else ad = B.self + U.rb0 + (r - U.gy) * rsb;
+            }
+            ring_pair_cl(ad, a, b);
+        } else {
+            ring_pair(row(r), a, b);
+        }
+    };
     const float2 c0 = make_float2(3.f * cf.a[0], 3.f * cf.a[0]);
     const float2 SH = make_float2(shr, shr), SI = make_float2(-shi, shi);
-    // centre and x neighbours of one row: 7 16-byte loads (positions x-6 .. x+7)
-    auto xrow = [&](const unsigned char *pr, float va, float vb, float2 &ca, float2 &cb, float2 &qa, float2 &qb) {
+    // centre and x neighbours of one row: 7 16-byte loads (positions x-6 .. x+7; those past the row
+    // read the plane's zero word)
+    auto xrow = [&](const unsigned char *pr, float2 &ca, float2 &cb, float2 &qa, float2 &qb) {
         float4 X[7];
 #pragma unroll
-        for (int m = 0; m < 7; ++m) X[m] = *reinterpret_cast<const float4 *>(pr - 48 + 16 * m);
+        for (int m = 0; m < 7; ++m)
+            X[m] = *reinterpret_cast<const float4 *>(
+                PER ? pr + 16 * (wrap_index(U.bx - 3 + m, hw) - U.bx) : ((U.xm >> m) & 1 ? pr - 48 + 16 * m : pz));
         auto xat = [&](int o) -> float2 {
             const float4 t = X[(o + 6) >> 1];
             return ((o + 6) & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
         };
         ca = xat(0);
         cb = xat(1);
-        qa = __ffma2_rn(SI, swp(ca), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(va, va))), ca));
-        qb = __ffma2_rn(SI, swp(cb), __fmul2_rn(__fadd2_rn(c0, __fadd2_rn(SH, make_float2(vb, vb))), cb));
+        qa = __ffma2_rn(SI, swp(ca), __fmul2_rn(__fadd2_rn(c0, SH), ca));
+        qb = __ffma2_rn(SI, swp(cb), __fmul2_rn(__fadd2_rn(c0, SH), cb));
 #pragma unroll
         for (int d = 1; d <= kRadius; ++d) {
             const float2 cd = make_float2(cf.a[d], cf.a[d]);
@@ -1079,24 +1196,37 @@ __device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned c
         }
     };
     float2 c0_, c1_, c2_, c3_, q0, q1, q2, q3;
-    xrow(pz + U.rb0, vv[0], vv[1], c0_, c1_, q0, q1);
+    xrow(pz + U.rb0, c0_, c1_, q0, q1);
     // row y+1 outside the box (odd ny): its values are zero neighbours of row y, and its own q is
     // discarded (the loads repeat row y, an address inside the plane)
-    xrow(pz + (U.row1 ? U.rb1 : U.rb0), vv[2], vv[3], c2_, c3_, q2, q3);
+    xrow(pz + (U.row1 ? U.rb1 : U.rb0), c2_, c3_, q2, q3);
     if (!U.row1) c2_ = c3_ = zero;
-    // y neighbours: rows y-6 .. y-1 and y+2 .. y+7 from the ring (the plane's first 16 bytes are
-    // padding, i.e. zero, and stand for rows outside the box); rows y and y+1 are the centres
+    const bool row1_centre = U.row1 || !PER;   // row y+1 is a centre, or outside the box (zero)
+    // y neighbours: rows y-d and y+1+d, and for d > 1 rows y+d and y+1-d (rows outside the box read
+    // the zero word); rows y and y+1 are the centres
 #pragma unroll
     for (int d = 1; d <= kRadius; ++d) {
         float2 u0, u1, l0, l1;              // rows y-d and y+1+d
-        ring_pair(pz + (U.gy - d >= 0 ? U.rb0 - d * rsb : 0), u0, u1);
-        ring_pair(pz + (U.gy + 1 + d < ny ? U.rb1 + d * rsb : 0), l0, l1);
+        if (PER || BAND) {
+            yrow(U.gy - d, u0, u1);
+            yrow(U.gy + 1 + d, l0, l1);
+        } else {
+            ring_pair(pz + (U.gy - d >= 0 ? U.rb0 - d * rsb : 0), u0, u1);
+            ring_pair(pz + (U.gy + 1 + d < ny ? U.rb1 + d * rsb : 0), l0, l1);
+        }
         float2 dn0, dn1, up0, up1;          // row y+d (for row y), row y+1-d (for row y+1)
         if (d == 1) {
-            dn0 = c2_;
-            dn1 = c3_;
+            if (row1_centre) {
+                dn0 = c2_;
+                dn1 = c3_;
+            } else {                        // periodic, row y+1 past the box: its image
+                yrow(U.gy + 1, dn0, dn1);
+            }
             up0 = c0_;
             up1 = c1_;
+        } else if (PER || BAND) {
+            yrow(U.gy + d, dn0, dn1);
+            yrow(U.gy + 1 - d, up0, up1);
         } else {
             ring_pair(pz + (U.gy + d < ny ? U.rb0 + d * rsb : 0), dn0, dn1);
             ring_pair(pz + (U.gy + 1 - d >= 0 ? U.rb1 - d * rsb : 0), up0, up1);
@@ -1106,7 +1236,7 @@ __device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned c
         float2 zm0, zm1, zm2, zm3, zp0, zp1, zp2, zp3;
         ring_pair(ring + sm * psb + U.rb0, zm0, zm1);
         ring_pair(ring + sp * psb + U.rb0, zp0, zp1);
-        ring_pair(ring + sm * psb + U.rb1z, zm2, zm3);   // row y+1 outside the box: padding
+        ring_pair(ring + sm * psb + U.rb1z, zm2, zm3);   // row y+1 outside the box: the zero word
         ring_pair(ring + sp * psb + U.rb1z, zp2, zp3);
         const float2 cd = make_float2(cf.a[d], cf.a[d]);
         q0 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(u0, dn0), __fadd2_rn(zm0, zp0)), q0);
@@ -1114,6 +1244,10 @@ __device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned c
         q2 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up0, l0), __fadd2_rn(zm2, zp2)), q2);
         q3 = __ffma2_rn(cd, __fadd2_rn(__fadd2_rn(up1, l1), __fadd2_rn(zm3, zp3)), q3);
     }
+    q0 = __ffma2_rn(make_float2(vv[0], vv[0]), c0_, q0);
+    q1 = __ffma2_rn(make_float2(vv[1], vv[1]), c1_, q1);
+    q2 = __ffma2_rn(make_float2(vv[2], vv[2]), c2_, q2);
+    q3 = __ffma2_rn(make_float2(vv[3], vv[3]), c3_, q3);
     st_pair<EVEN>(qs, gq0, U.hasb, q0, q1);
     if (U.row1) st_pair<EVEN>(qs, gq0 + (U.col1 - U.col0), U.hasb, q2, q3);
     cdot(acc[0], acc[1], c0_, q0);
@@ -1166,7 +1300,7 @@ __device__ __forceinline__ bool ring_end_sweep(const RingArgs &A, Slot &sl, bool
 
 // The fused kernel: every thread takes one unit through both phases of a step (front, then the
 // stencil six planes behind), the front's loads for the next plane in flight during the stencil.
-template <bool EVEN>
+template <bool EVEN, bool PER>
 __global__ void __launch_bounds__(kRingMaxThreads, 1)
     k_cocg_ring(RingArgs A, float2 *__restrict__ xg, float2 *__restrict__ rg, float2 *__restrict__ pg,
                 float2 *__restrict__ qg, const float *__restrict__ vloc, Coef<float> cf) {
@@ -1193,11 +1327,20 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
             const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
             const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
             __syncthreads();                       // the previous sweep's ring readers are done
-            if (U.own) {                           // planes -6 .. -1 (ring slots 8 .. 13) are zero
+            if (U.own) {                           // planes -6 .. -1 (ring slots 8 .. 13)
+                if (PER) {                         // p_k of their images nz-6 .. nz-1
+                    for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                        RingFront H;
+                        ring_load_front<EVEN>(U, wrap_index(m - kRingPlanes, nz) * plane + U.col0, first, xs, rsv,
+                                              psv, qs, H);
+                        ring_halo_plane<EVEN>(U, first, alr, ali, ber, bei, H, ring + m * psb);
+                    }
+                } else {                           // zero
 #pragma unroll
-                for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
-                    *reinterpret_cast<float4 *>(ring + m * psb + U.rb0) = zero4;
-                    if (U.row1) *reinterpret_cast<float4 *>(ring + m * psb + U.rb1) = zero4;
+                    for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                        *reinterpret_cast<float4 *>(ring + m * psb + U.rb0) = zero4;
+                        if (U.row1) *reinterpret_cast<float4 *>(ring + m * psb + U.rb1) = zero4;
+                    }
                 }
             }
             RingFront F;
@@ -1211,9 +1354,14 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
                 float2 rk[4] = {};
                 float vv[4] = {0.f, 0.f, 0.f, 0.f};
                 if (U.own && z >= 0) ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
-                // 1. front plane f, p_k into ring slot u
-                if (U.own)
-                    ring_front<EVEN>(U, f, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring + u * psb, fa);
+                // 1. front plane f, p_k into ring slot u (periodic, f >= nz: p_k of plane f - nz)
+                if (U.own) {
+                    if (PER && f >= nz)
+                        ring_wrap_front<EVEN>(U, wrap_index(f, nz) * plane + U.col0, psv, ring + u * psb);
+                    else
+                        ring_front<EVEN>(U, f, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring + u * psb,
+                                         fa);
+                }
                 // 2. the next front plane, in flight during the stencil below
                 if (U.own && f + 1 < nz)
                     ring_load_front<EVEN>(U, (f + 1) * plane + U.col0, first, xs, rsv, psv, qs, F);
@@ -1221,12 +1369,158 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
                 // 3. q_k on plane z, its 6 neighbour planes from the ring
                 if (U.own && z >= 0) {
                     const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
-                    ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs, sa);
+                    ring_stencil<EVEN, PER>(U, ring, psb, rsb, A.hw, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf,
+                                            qs, sa);
                 }
             }
             more = ring_end_sweep(A, sl, first, fa, sa);
         }
     }
+}
+
+// Cluster form of the fused kernel, for planes whose ring does not fit one block's shared memory
+// (72 x 72: 580 KB), and for smaller planes as two blocks per SM: the C blocks of a thread-block
+// cluster split every plane into bands of bp row pairs (the last band may hold fewer; bp >= 3, so
+// that the y neighbours of a band lie in the bands next to it) and each block keeps the ring of its
+// band.  The stencil reads the y neighbours past its band from the neighbouring blocks' rings
+// (distributed shared memory); x and z neighbours are in its own ring.  Only the centre plane's rows
+// are read across blocks, and that plane was written six steps before, so the cluster barrier (a
+// release / acquire fence across the cluster) is needed only every kClusterEvery steps and runs one
+// step behind: a block arrives after writing its front plane at steps f = 0 mod kClusterEvery and
+// waits for that phase at step f+1, a step of work after the others arrived; the block barrier of
+// every step orders the block's own ring.  Remote rows of plane z, read at step z+6, were written at
+// step z and released by the first arrival at or after it (at most kClusterEvery-1 steps later,
+// waited on one step after that, so by step z+kClusterEvery <= z+5); the ring slot a block overwrites
+// at step f was last read by any block at step f-8, before that block's next arrival (one falls in
+// every window of kClusterEvery steps) and so before the writer's wait.  Units whose y neighbours
+// all lie in their own band run the single-block stencil; the others load rows through
+// shared::cluster addresses.  The scalar step is taken by rank 0 from the bands' sums, added in rank
+// order; the next system, the stopping decision and the bands' sums pass through shared memory of
+// the cluster.  Dirichlet grids.
+namespace cg = cooperative_groups;
+
+constexpr int kClusterEvery = 4;           // steps per cluster barrier phase (at most 5, see above)
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <bool EVEN>
+__global__ void __launch_bounds__(kRingMaxThreads, 1)
+    k_cocg_ring_cl(RingArgs A, float2 *__restrict__ xg, float2 *__restrict__ rg, float2 *__restrict__ pg,
+                   float2 *__restrict__ qg, const float *__restrict__ vloc, Coef<float> cf) {
+    extern __shared__ float4 ring4[];
+    __shared__ int cl_item, cl_more;
+    __shared__ double cl_part[9];
+    unsigned char *const ring = reinterpret_cast<unsigned char *>(ring4);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), ncl = (int)cl.num_blocks();
+    const int tid = threadIdx.x;
+    const int nz = A.nz, plane = A.nx * A.ny;
+    const int rsb = A.rs * 8, psb = A.ps * 8;
+    Band B;
+    B.rows = 2 * A.bp;
+    B.y0 = rank * B.rows;
+    B.y1 = min(A.ny, B.y0 + B.rows);
+    const int npairs = max(0, (B.y1 - B.y0 + 1) / 2);
+    const RingUnit U = ring_unit(tid, A, B.y0, npairs);
+    // a unit whose y neighbours (rows y-6 .. y+7) reach into another block's band
+    const bool remote = (U.gy - kRadius < B.y0 && B.y0 > 0) || (U.gy + 1 + kRadius >= B.y1 && B.y1 < A.ny);
+    // the rings' shared::cluster addresses: this block's, and those of the neighbouring bands' blocks
+    const unsigned ring_self = (unsigned)__cvta_generic_to_shared(ring);
+    unsigned ring_up = 0, ring_dn = 0;
+    if (rank > 0) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ring_up) : "r"(ring_self), "r"(rank - 1));
+    if (rank + 1 < ncl) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ring_dn) : "r"(ring_self), "r"(rank + 1));
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
+    const int n_items = *A.cnt_in;
+    for (;;) {
+        cl.sync();                                 // every block is done with the previous system
+        if (rank == 0 && tid == 0) {
+            const int it = atomicAdd(A.grab, 1);
+            for (int t = 0; t < ncl; ++t) *cl.map_shared_rank(&cl_item, t) = it;
+        }
+        cl.sync();
+        const int it = cl_item;
+        if (it >= n_items) break;
+        const int s = A.list_in[n_items - 1 - it];
+        Slot &sl = A.slots[s];
+        const float shr = (float)sl.shift_re, shi = (float)sl.shift_im;
+        const long long off = (long long)s * A.nd;
+        float2 *const xs = xg + off;
+        float2 *const rsv = rg + off;
+        float2 *const psv = pg + off;
+        float2 *const qs = qg + off;
+        bool more = true;
+        while (more) {                             // sweeps of this system (iterations of COCG)
+            const bool first = sl.iters == 0;
+            const float alr = (float)sl.alpha_re, ali = (float)sl.alpha_im;
+            const float ber = (float)sl.beta_re, bei = (float)sl.beta_im;
+            if (U.own) {                           // planes -6 .. -1 (ring slots 8 .. 13) are zero
+#pragma unroll
+                for (int m = kRingPlanes - kRadius; m < kRingPlanes; ++m) {
+                    *reinterpret_cast<float4 *>(ring + m * psb + U.rb0) = zero4;
+                    if (U.row1) *reinterpret_cast<float4 *>(ring + m * psb + U.rb1) = zero4;
+                }
+            }
+            RingFront F;
+            if (U.own) ring_load_front<EVEN>(U, U.col0, first, xs, rsv, psv, qs, F);   // front plane 0
+            float fa[3] = {0.f, 0.f, 0.f}, sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int nsteps = nz + kRadius;
+            for (int f = 0, u = 0; f < nsteps; ++f, u = (u + 1 == kRingPlanes) ? 0 : u + 1) {
+                // r_k and V of the stencil's plane z = f - 6, in flight during the front and the barrier
+                const int z = f - kRadius;
+                float2 rk[4] = {};
+                float vv[4] = {0.f, 0.f, 0.f, 0.f};
+                if (U.own && z >= 0) ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
+                if (f % kClusterEvery == 1) cluster_wait();   // the phase this block arrived at last step
+                // 1. front plane f, p_k into ring slot u
+                if (U.own)
+                    ring_front<EVEN>(U, f, nz, plane, first, alr, ali, ber, bei, F, xs, rsv, psv, ring + u * psb, fa);
+                if (f % kClusterEvery == 0) cluster_arrive();
+                // 2. the next front plane, in flight during the stencil
+                if (U.own && f + 1 < nz)
+                    ring_load_front<EVEN>(U, (f + 1) * plane + U.col0, first, xs, rsv, psv, qs, F);
+                __syncthreads();
+                // 3. q_k on plane z, its 6 neighbour planes from the ring, rows past the band from the
+                // neighbouring blocks' rings
+                if (U.own && z >= 0) {
+                    const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
+                    if (remote) {
+                        B.self = ring_self + cz * psb;
+                        B.up = ring_up + cz * psb;      // used only for rows of a band above (rank > 0)
+                        B.dn = ring_dn + cz * psb;      // and below (rank < ncl - 1)
+                        ring_stencil<EVEN, false, true>(U, ring, psb, rsb, A.hw, A.ny, cz, z * plane + U.col0, rk, vv,
+                                                        shr, shi, cf, qs, sa, B);
+                    } else {
+                        ring_stencil<EVEN, false>(U, ring, psb, rsb, A.hw, A.ny, cz, z * plane + U.col0, rk, vv, shr,
+                                                  shi, cf, qs, sa);
+                    }
+                }
+            }
+            if ((nsteps - 1) % kClusterEvery == 0) cluster_wait();   // the last arrival's phase
+            // the sweep's sums: the band's, then the cluster's in rank order (rank 0)
+            double v[9] = {fa[0], fa[1], fa[2], sa[0], sa[1], sa[2], sa[3], sa[4], sa[5]};
+            block_sum_any<9>(v);
+            if (tid == 0)
+                for (int c = 0; c < 9; ++c) cl_part[c] = v[c];
+            cl.sync();
+            if (rank == 0 && tid == 0) {
+                double tot[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                for (int t = 0; t < ncl; ++t) {
+                    const double *pt = cl.map_shared_rank(cl_part, t);
+                    for (int c = 0; c < 9; ++c) tot[c] += pt[c];
+                }
+                const int m = ring_scalar_step(A, sl, tot) ? 1 : 0;
+                if (A.prof) {
+                    atomicAdd(A.prof + 1, (unsigned long long)A.nd);
+                    if (first) atomicAdd(A.prof + 2, (unsigned long long)A.nd);
+                }
+                for (int t = 0; t < ncl; ++t) *cl.map_shared_rank(&cl_more, t) = m;
+            }
+            cl.sync();                             // also: every block's ring readers of the sweep are done
+            more = cl_more != 0;
+        }
+    }
+    cl.sync();                                     // no block leaves while another may read its ring
 }
 
 // Warp-specialised form of the fused kernel: the first threads (consumers, one unit each) apply
@@ -1303,8 +1597,8 @@ __global__ void __maxnreg__(96)
                         float vv[4] = {0.f, 0.f, 0.f, 0.f};
                         ring_load_rv<EVEN>(U, z * plane + U.col0, rsv, vloc, rk, vv);
                         const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;
-                        ring_stencil<EVEN>(U, ring, psb, rsb, A.ny, cz, z * plane + U.col0, rk, vv, shr, shi, cf, qs,
-                                           sa);
+                        ring_stencil<EVEN, false>(U, ring, psb, rsb, A.hw, A.ny, cz, z * plane + U.col0, rk, vv, shr,
+                                                  shi, cf, qs, sa);
                     }
                 }
                 __syncthreads();
@@ -1367,6 +1661,30 @@ bool ring_fits(int nx, int ny, RingFn fn, int smem_optin, bool ws = false) {
     const long long threads = ws ? (units + 31) / 32 * 32 + ((units + 1) / 2 + 31) / 32 * 32 : units;
     return threads <= (ws ? kRingWsMaxThreads : kRingMaxThreads) &&
            ring_bytes(nx, ny) + fa.sharedSizeBytes <= (size_t)smem_optin;
+}
+
+// Cluster form of the fused kernel: the smallest cluster of C <= 8 blocks whose bands of bp row pairs
+// (bp >= 3, every band non-empty) fit a block's shared memory and kRingMaxThreads units.  With
+// `two_per_sm` it asks for rings small enough for two blocks per SM.  False where none fits.
+bool cluster_plan(int nx, int ny, int smem_optin, bool two_per_sm, int &ncl, int &bp) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_cocg_ring_cl<true>) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    const int hw = (nx + 1) / 2, hh = (ny + 1) / 2, rs = 2 * hw + ring_row_pad(hw);
+    const size_t limit = two_per_sm ? (size_t)smem_optin / 2 - 1024 : (size_t)smem_optin;
+    for (int c = 2; c <= 8; ++c) {
+        const int b = (hh + c - 1) / c;
+        if (b < 3 || (long long)(c - 1) * b >= hh) continue;
+        const size_t bytes = (size_t)kRingPlanes * (2 + (size_t)2 * b * rs) * sizeof(float2) + fa.sharedSizeBytes;
+        if ((long long)hw * b <= kRingMaxThreads && bytes <= limit) {
+            ncl = c;
+            bp = b;
+            return true;
+        }
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1462,12 +1780,21 @@ __device__ __forceinline__ void df_stencil(const float2 *__restrict__ v, long lo
             two_sum(ai, u.y, ai, t);
             ei += t;
         };
-        if (i - s >= 0) add(v[idx - s]);
-        if (i + s < g.nx) add(v[idx + s]);
-        if (j - s >= 0) add(v[idx - s * sy]);
-        if (j + s < g.ny) add(v[idx + s * sy]);
-        if (k - s >= 0) add(v[idx - s * sz]);
-        if (k + s < g.nz) add(v[idx + s * sz]);
+        if (g.periodic) {
+            add(v[idx + (wrap_index(i - s, g.nx) - i)]);
+            add(v[idx + (wrap_index(i + s, g.nx) - i)]);
+            add(v[idx + (wrap_index(j - s, g.ny) - j) * sy]);
+            add(v[idx + (wrap_index(j + s, g.ny) - j) * sy]);
+            add(v[idx + (wrap_index(k - s, g.nz) - k) * sz]);
+            add(v[idx + (wrap_index(k + s, g.nz) - k) * sz]);
+        } else {
+            if (i - s >= 0) add(v[idx - s]);
+            if (i + s < g.nx) add(v[idx + s]);
+            if (j - s >= 0) add(v[idx - s * sy]);
+            if (j + s < g.ny) add(v[idx + s * sy]);
+            if (k - s >= 0) add(v[idx - s * sz]);
+            if (k + s < g.nz) add(v[idx + s * sz]);
+        }
         // a_s (ar + er): the sum's low part times the coefficient's high part joins the error term
         df_mad(ch.a[s], cl.a[s], ar, Sr, Er);
         Er += ch.a[s] * er;
@@ -1557,9 +1884,36 @@ __global__ void __launch_bounds__(kThreads) k_residual_df(Params P, double2 *__r
 // the occupied components of the first refinement's residual raise the next inner solve's
 // iterations by 15% at 40^3.)
 // A work item is one chunk of grid points of kSlotGroup consecutive slots: each orbital value
-// loaded (from L2) serves all of them, and one block reduction per orbital covers the group.
+// loaded (from L2) serves all of them.  A thread sums its kPPT points in FP32 for kDotK orbitals
+// at a time (32 sums: kDotK orbitals x kSlotGroup slots x re/im), its warp adds them over the
+// lanes with a transposing butterfly (each level exchanges half of the remaining sums, so 31
+// shuffles give lane l the warp's total of sum l, instead of 5 shuffles per sum), and the warps'
+// totals are added in FP64 in warp order: one barrier per kDotBatch orbitals instead of a block
+// reduction per orbital.  Fixed order throughout.
 constexpr int kSlotGroup = 4;
+constexpr int kDotK = 4;                          // orbitals per butterfly (kDotK * 2 * kSlotGroup = 32)
+constexpr int kDotBatch = 32;                     // orbitals per shared-memory batch
+static_assert(kDotK * 2 * kSlotGroup == 32, "one butterfly reduces 32 sums");
+
+// In-warp transposing reduction: on return lane l holds the sum over the warp's lanes of a[l].
+__device__ __forceinline__ float warp_transpose_sum(float (&a)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;          // this lane keeps the upper half of the h-blocks
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float keep = up ? a[i + h] : a[i];
+            const float send = up ? a[i] : a[i + h];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    return a[0];
+}
+
 __global__ void __launch_bounds__(kThreads) k_cproj_dots(Params P, const float2 *__restrict__ v) {
+    __shared__ float red[kWarpsPerBlock][kDotBatch * 2 * kSlotGroup];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ngroups = (P.S + kSlotGroup - 1) / kSlotGroup;
     const long long items = (long long)ngroups * P.nblk;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
@@ -1582,35 +1936,47 @@ __global__ void __launch_bounds__(kThreads) k_cproj_dots(Params P, const float2 
                 vv[q][t] = (act[q] && idx < P.g.nd) ? v[(long long)(g * kSlotGroup + q) * P.g.nd + idx]
                                                     : make_float2(0.f, 0.f);
             }
-        for (int k = 0; k < P.ns; ++k) {
-            float uu[kPPT];
+        for (int k0 = 0; k0 < P.ns; k0 += kDotBatch) {
+            const int kn = min(kDotBatch, P.ns - k0);
+            for (int kk = 0; kk < kn; kk += kDotK) {
+                float a[32];
 #pragma unroll
-            for (int t = 0; t < kPPT; ++t) {
-                const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
-                uu[t] = idx < P.g.nd ? P.psi32[(long long)k * P.g.nd + idx] : 0.f;
-            }
-            double acc[2 * kSlotGroup];
+                for (int j = 0; j < kDotK; ++j) {
+                    const int k = k0 + kk + j;
+                    float2 acc[kSlotGroup];
 #pragma unroll
-            for (int q = 0; q < kSlotGroup; ++q) {
-                float a0 = 0.f, a1 = 0.f;
+                    for (int q = 0; q < kSlotGroup; ++q) acc[q] = make_float2(0.f, 0.f);
+                    if (k < P.ns) {
 #pragma unroll
-                for (int t = 0; t < kPPT; ++t) {
-                    a0 += uu[t] * vv[q][t].x;
-                    a1 += uu[t] * vv[q][t].y;
-                }
-                acc[2 * q] = a0;
-                acc[2 * q + 1] = a1;
-            }
-            block_sum<2 * kSlotGroup>(acc);
-            if (threadIdx.x == 0)
+                        for (int t = 0; t < kPPT; ++t) {
+                            const long long idx = (long long)chunk * kChunk + t * kThreads + threadIdx.x;
+                            const float u = idx < P.g.nd ? P.psi32[(long long)k * P.g.nd + idx] : 0.f;
+                            const float2 uu = make_float2(u, u);
 #pragma unroll
-                for (int q = 0; q < kSlotGroup; ++q)
-                    if (act[q]) {
-                        const int s = g * kSlotGroup + q;
-                        double *o = P.partP + (((long long)s * P.nblk + chunk) * P.ns + k) * 2;
-                        o[0] = acc[2 * q];
-                        o[1] = acc[2 * q + 1];
+                            for (int q = 0; q < kSlotGroup; ++q) acc[q] = __ffma2_rn(uu, vv[q][t], acc[q]);
+                        }
                     }
+#pragma unroll
+                    for (int q = 0; q < kSlotGroup; ++q) {
+                        a[j * 2 * kSlotGroup + 2 * q] = acc[q].x;
+                        a[j * 2 * kSlotGroup + 2 * q + 1] = acc[q].y;
+                    }
+                }
+                red[warp][kk * 2 * kSlotGroup + lane] = warp_transpose_sum(a);
+            }
+            __syncthreads();
+            // thread e: orbital k0 + e / (2 kSlotGroup), slot e / 2 % kSlotGroup, part e % 2
+            for (int e = threadIdx.x; e < kn * 2 * kSlotGroup; e += blockDim.x) {
+                const int q = (e >> 1) % kSlotGroup;
+                if (act[q]) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < kWarpsPerBlock; ++w) sum += (double)red[w][e];
+                    const int s = g * kSlotGroup + q, k = k0 + e / (2 * kSlotGroup);
+                    P.partP[(((long long)s * P.nblk + chunk) * P.ns + k) * 2 + (e & 1)] = sum;
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -2177,17 +2543,28 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     int dev_sms = 0, smem_optin = 0;
     RPA_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device));
     RPA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
-    // rpa_options.stencil_shape: 0 = automatic (the fused kernel where a plane fits its ring, else
-    // split variant 1), 1..3 = the split kernels' variants, 4 = the fused kernel (split variant 1
-    // where a plane does not fit).  The plain FP64 form always runs the split kernels.
-    const int want = std::max(0, std::min(5, c.opt.stencil_shape));
+    // rpa_options.stencil_shape: 0 = automatic (the fused kernel where a plane fits its ring, its
+    // cluster form where a band of the plane does, else split variant 1), 1..3 = the split kernels'
+    // variants, 4 = the fused kernel (as 0), 5 = its warp-specialised form, 6 = its cluster form
+    // with two blocks per SM where the bands fit (else as 0).  The plain FP64 form always runs the
+    // split kernels.  Periodic grids: the fused kernel needs even nx (point pairs wrap onto point
+    // pairs); the warp-specialised and cluster forms and the two-column split variant are Dirichlet
+    // only (the fused kernel or the first split variant stands in for them).
+    const int want = std::max(0, std::min(6, c.opt.stencil_shape));
+    const bool per = c.opt.periodic != 0;
     const bool even_nx = (c.nx % 2) == 0;
-    const bool ws = want == 5 && ring_fits(c.nx, c.ny, even_nx ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>,
-                                           smem_optin, true);
+    const bool ws = want == 5 && !per &&
+                    ring_fits(c.nx, c.ny, even_nx ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>, smem_optin, true);
+    const RingFn ring1_fn = per ? k_cocg_ring<true, true> : even_nx ? k_cocg_ring<true, false> : k_cocg_ring<false, false>;
+    const bool ring1 = (!per || even_nx) && ring_fits(c.nx, c.ny, ring1_fn, smem_optin);
+    int ncl = 1, band_pairs = 0;
+    const bool clus = mixed && !per && !ws && (want == 0 || want >= 4) &&
+                      ((want == 6 && cluster_plan(c.nx, c.ny, smem_optin, true, ncl, band_pairs)) ||
+                       (!ring1 && cluster_plan(c.nx, c.ny, smem_optin, false, ncl, band_pairs)));
     const RingFn ring_fn = ws ? (even_nx ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>)
-                              : (even_nx ? k_cocg_ring<true> : k_cocg_ring<false>);
-    const bool use_ring = mixed && (want == 0 || want >= 4) && ring_fits(c.nx, c.ny, ring_fn, smem_optin, ws);
-    const int variant = (want >= 1 && want <= 3) ? want - 1 : 0;
+                              : clus ? (even_nx ? k_cocg_ring_cl<true> : k_cocg_ring_cl<false>) : ring1_fn;
+    const bool use_ring = mixed && (want == 0 || want >= 4) && (ws || clus || ring1);
+    const int variant = (want >= 1 && want <= 3 && !(per && want == 3)) ? want - 1 : 0;
     const PaShape shape = mixed ? kPaShapes32[variant] : kPaShape64;
     Tiles tl = pick_tiles(c.nx, c.ny, shape.max_threads, shape.pairs != 0);
     if (c.opt.z_chunks > 1) {
@@ -2224,7 +2601,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     P.S = S;
     P.nblk = nblk;
     P.nparta = ntiles;
-    P.g = Grid3{c.nx, c.ny, c.nz, nd};
+    P.g = Grid3{c.nx, c.ny, c.nz, nd, c.opt.periodic};
     P.partA = partA;
     P.partB = partB;
     P.list = list;
@@ -2260,7 +2637,8 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     // per parity: the stencil kernel's and the update kernel's views of P
     IterArgs ia_pa[2], ia_b[2];
     for (int par = 0; par < 2; ++par) {
-        const IterArgs base{slots, list + par * S, cnt + par, nullptr, nullptr, nd, c.nx, c.ny, c.nz, 0};
+        const IterArgs base{slots, list + par * S, cnt + par, nullptr, nullptr, nd, c.nx, c.ny, c.nz, 0,
+                            c.opt.periodic};
         ia_pa[par] = base;
         ia_pa[par].part = partA;
         ia_pa[par].nper = ntiles;
@@ -2323,18 +2701,38 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         ra.nz = c.nz;
         ra.hw = hw;
         ra.hh = (c.ny + 1) / 2;
-        ra.rs = 2 * hw + kRingPad;
-        ra.ps = c.ny * ra.rs + kRingPad;
-        ring_smem = ring_bytes(c.nx, c.ny);
+        ra.rs = 2 * hw + ring_row_pad(hw);
+        ra.ps = clus ? 2 + 2 * band_pairs * ra.rs : 2 + c.ny * ra.rs;
+        ra.bp = band_pairs;
+        ring_smem = (size_t)kRingPlanes * ra.ps * sizeof(float2);
         {
-            const int units = hw * ((c.ny + 1) / 2);
+            const int units = hw * (clus ? band_pairs : (c.ny + 1) / 2);
             ring_threads = (unsigned)((units + 31) / 32 * 32);
             if (ws) ring_threads += (unsigned)(((units + 1) / 2 + 31) / 32 * 32);   // consumers + producers
         }
         allow_dynamic_smem((const void *)ring_fn, ring_smem);
-        int per_sm = 1;
-        RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_fn, (int)ring_threads, ring_smem));
-        ring_grid = (unsigned)std::max<long long>(1, std::min<long long>(S, (long long)dev_sms * std::max(1, per_sm)));
+        if (clus) {
+            // one cluster of ncl blocks per system at a time, as many clusters as are resident
+            cudaLaunchConfig_t lc{};
+            cudaLaunchAttribute at{};
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = (unsigned)ncl;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            lc.gridDim = dim3((unsigned)ncl * (unsigned)dev_sms, 1, 1);
+            lc.blockDim = dim3(ring_threads, 1, 1);
+            lc.dynamicSmemBytes = ring_smem;
+            lc.attrs = &at;
+            lc.numAttrs = 1;
+            int nclusters = 0;
+            RPA_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, (const void *)ring_fn, &lc));
+            if (nclusters < 1) fail(RPA_ERR_CUDA, "cluster form of the fused kernel: no cluster of %d blocks fits", ncl);
+            ring_grid = (unsigned)ncl * (unsigned)std::min<long long>(S, nclusters);
+        } else {
+            int per_sm = 1;
+            RPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_fn, (int)ring_threads, ring_smem));
+            ring_grid = (unsigned)std::max<long long>(1, std::min<long long>(S, (long long)dev_sms * std::max(1, per_sm)));
+        }
     }
 
     // profiling: events around every launch of the item kernels of the iteration
@@ -2343,7 +2741,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     char names[3][32];
     std::snprintf(names[0], 32, "-");
     if (use_ring) {
-        std::snprintf(names[1], 32, ws ? "k_cocg_ring_ws<%s>" : "k_cocg_ring<%s>", tn);
+        std::snprintf(names[1], 32, ws ? "k_cocg_ring_ws<%s>" : clus ? "k_cocg_ring_cl<%s>" : "k_cocg_ring<%s>", tn);
         std::snprintf(names[2], 32, "-");
     } else {
         std::snprintf(names[1], 32, "k_cocg_pa<%s>", tn);
@@ -2424,8 +2822,25 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         if (use_ring) {
             k_ring_list<<<1, 1024, 0, ss>>>(P);
             rec(0);
-            ring_fn<<<ring_grid, ring_threads, ring_smem, ss>>>(ra, (float2 *)xin, (float2 *)r, (float2 *)p,
-                                                                (float2 *)q, c.vloc32, cf32);
+            if (clus) {
+                cudaLaunchConfig_t lc{};
+                cudaLaunchAttribute at{};
+                at.id = cudaLaunchAttributeClusterDimension;
+                at.val.clusterDim.x = (unsigned)ncl;
+                at.val.clusterDim.y = 1;
+                at.val.clusterDim.z = 1;
+                lc.gridDim = dim3(ring_grid, 1, 1);
+                lc.blockDim = dim3(ring_threads, 1, 1);
+                lc.dynamicSmemBytes = ring_smem;
+                lc.stream = ss;
+                lc.attrs = &at;
+                lc.numAttrs = 1;
+                RPA_CUDA(cudaLaunchKernelEx(&lc, ring_fn, ra, (float2 *)xin, (float2 *)r, (float2 *)p, (float2 *)q,
+                                            (const float *)c.vloc32, cf32));
+            } else {
+                ring_fn<<<ring_grid, ring_threads, ring_smem, ss>>>(ra, (float2 *)xin, (float2 *)r, (float2 *)p,
+                                                                    (float2 *)q, c.vloc32, cf32);
+            }
             rec(1);
             RPA_LAUNCH("cocg inner solves (fused)");
             maintenance(ss);
@@ -2619,13 +3034,19 @@ void check_orbitals(const Ctx &c, const int *orb, int nsys) {
 
 }  // namespace
 
-bool fused_kernel_applies(const Ctx &c, bool warp_specialised) {
+bool fused_kernel_applies(const Ctx &c, bool warp_specialised, bool cluster) {
     int smem_optin = 0;
     RPA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     const bool even = (c.nx % 2) == 0;
+    if (cluster) {
+        int ncl = 0, bp = 0;
+        return !c.opt.periodic && cluster_plan(c.nx, c.ny, smem_optin, true, ncl, bp);
+    }
+    if (c.opt.periodic)
+        return !warp_specialised && even && ring_fits(c.nx, c.ny, k_cocg_ring<true, true>, smem_optin);
     if (warp_specialised)
         return ring_fits(c.nx, c.ny, even ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>, smem_optin, true);
-    return ring_fits(c.nx, c.ny, even ? k_cocg_ring<true> : k_cocg_ring<false>, smem_optin);
+    return ring_fits(c.nx, c.ny, even ? k_cocg_ring<true, false> : k_cocg_ring<false, false>, smem_optin);
 }
 
 int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

@@ -115,9 +115,11 @@ __global__ void __launch_bounds__(256) k_axis(const double *__restrict__ in, dou
     }
 }
 
+// Pointwise factor (4 pi / lam)^power of nu^power in the eigenbasis; lam = 0 only for the G = 0
+// mode of a periodic grid, which nu^power maps to zero.
 __global__ void k_scale_grid(const double *__restrict__ lam, double *__restrict__ sc, long long nd, double power) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nd) sc[i] = pow(4.0 * 3.14159265358979323846, power) * pow(lam[i], -power);
+    if (i < nd) sc[i] = lam[i] > 0.0 ? pow(4.0 * 3.14159265358979323846, power) * pow(lam[i], -power) : 0.0;
 }
 
 }  // namespace
@@ -128,13 +130,33 @@ void coulomb_setup(Ctx &c) {
     for (int a = 0; a < 3; ++a) {
         const int n = dims[a];
         std::vector<double> K((size_t)n * n, 0.0), Q;
-        // K = -D, D the 1D second difference with weights w_k / h^2;  c.coef.a = -w/(2h^2)
+        // K = -D, D the 1D second difference with weights w_k / h^2;  c.coef.a = -w/(2h^2).
+        // Dirichlet: taps past the ends are dropped (Toeplitz); periodic: taps wrap, and taps
+        // that land on the same point add up (circulant).
         for (int i = 0; i < n; ++i)
-            for (int j = std::max(0, i - kRadius); j <= std::min(n - 1, i + kRadius); ++j)
-                K[(size_t)i * n + j] = 2.0 * c.coef.a[std::abs(i - j)];
+            for (int d = -kRadius; d <= kRadius; ++d) {
+                int j = i + d;
+                if (c.opt.periodic) j = ((j % n) + n) % n;
+                else if (j < 0 || j >= n) continue;
+                K[(size_t)i * n + j] += 2.0 * c.coef.a[std::abs(d)];
+            }
         jacobi_eigh(K, n, mu[a], Q);
-        for (double m : mu[a])
-            if (!(m > 0.0)) fail(RPA_ERR_INVALID, "1D Laplacian not positive definite (n=%d)", n);
+        if (c.opt.periodic) {
+            // one zero eigenvalue (the constant mode), returned to rounding: made exactly zero so
+            // that the G = 0 mode of the 3D operator is the one point where lam = 0
+            double top = 0.0;
+            for (double m : mu[a]) top = std::max(top, std::fabs(m));
+            int zi = 0;
+            for (int i = 1; i < n; ++i)
+                if (std::fabs(mu[a][i]) < std::fabs(mu[a][zi])) zi = i;
+            if (!(std::fabs(mu[a][zi]) <= 1e-10 * top)) fail(RPA_ERR_INVALID, "periodic 1D Laplacian: no zero mode (n=%d)", n);
+            mu[a][zi] = 0.0;
+            for (int i = 0; i < n; ++i)
+                if (i != zi && !(mu[a][i] > 0.0)) fail(RPA_ERR_INVALID, "periodic 1D Laplacian not semidefinite (n=%d)", n);
+        } else {
+            for (double m : mu[a])
+                if (!(m > 0.0)) fail(RPA_ERR_INVALID, "1D Laplacian not positive definite (n=%d)", n);
+        }
         RPA_CUDA(cudaMalloc(&c.Q[a], sizeof(double) * n * n));
         RPA_CUDA(cudaMemcpy(c.Q[a], Q.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
     }

@@ -198,7 +198,7 @@ void ritz_rotation(const double *Q, const double *w, int n, double weight, doubl
 
 // Whether the fused single-pass COCG kernel applies to this context's grid (a whole xy plane fits
 // its shared-memory ring); the mixed form then uses it by default.
-bool fused_kernel_applies(const Ctx &c, bool warp_specialised = false);
+bool fused_kernel_applies(const Ctx &c, bool warp_specialised = false, bool cluster = false);
 
 // Same as sternheimer_batch, with b replaced by P_c b first.
 int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

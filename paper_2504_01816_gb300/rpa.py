@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import dataclasses
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
 
@@ -42,7 +43,8 @@ class rpa_options(ctypes.Structure):
                 ("batch_systems", ctypes.c_int), ("profile", ctypes.c_int), ("project_solution", ctypes.c_int),
                 ("z_chunks", ctypes.c_int), ("stencil_shape", ctypes.c_int),
                 ("independent_frequencies", ctypes.c_int), ("sq_order", ctypes.c_int),
-                ("contractions", ctypes.c_int), ("omega_first", ctypes.c_int), ("omega_count", ctypes.c_int)]
+                ("contractions", ctypes.c_int), ("omega_first", ctypes.c_int), ("omega_count", ctypes.c_int),
+                ("periodic", ctypes.c_int)]
 
 
 PROF_SLOTS = 8
@@ -176,6 +178,7 @@ class Options:
     contractions: int = 0
     omega_first: int = 0
     omega_count: int = 0
+    periodic: int = 0
 
     def to_c(self) -> rpa_options:
         o = rpa_options()
@@ -224,6 +227,8 @@ class Context:
         import torch
         vloc = torch.as_tensor(system.vloc, dtype=torch.float64, device=device).contiguous()
         psi = torch.as_tensor(system.psi, dtype=torch.float64, device=device).contiguous()
+        if getattr(system, "periodic", False):      # the system's boundary conditions
+            options = dataclasses.replace(options if options is not None else default_options(), periodic=1)
         return cls(system.nx, system.ny, system.nz, system.h, vloc, psi, system.eps, options)
 
     def close(self):
@@ -297,7 +302,8 @@ class Context:
                            for shape in ("1 column/thread <= 640 threads", "1 column/thread <= 320 threads x 2 blocks",
                                          "2 columns/thread <= 384 threads") for z in (1, 2)] + \
                           ["fused single-pass kernel, whole planes in a shared-memory ring",
-                           "fused single-pass kernel, warp-specialised (producer / consumer threads)"]
+                           "fused single-pass kernel, warp-specialised (producer / consumer threads)",
+                           "fused single-pass kernel, cluster form (bands of the plane, two blocks per SM)"]
 
     def autotune(self, omega: float, V, stream=None):
         """rpa_autotune: time the COCG kernel configurations on this workload, keep the fastest.

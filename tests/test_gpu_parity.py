@@ -342,14 +342,16 @@ def test_lih72_sampled_column_matches_oracle(rpa):
     assert relerr(R.cpu().numpy()[:1], ref) < 1e-5
 
 
-@pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11), (16, 5, 4)])
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("grid", [(70, 3, 9), (15, 13, 11), (16, 5, 4), (20, 26, 7)])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
 def test_stencil_variants_match_oracle(rpa, shape, grid):
     """(70, 3, 9): two x tiles with side halos and more halo elements per plane than twice the
     block's threads (the split kernels' fallback halo loop), and rows of 35 point pairs in the
     fused kernel; (15, 13, 11): an odd nx, where the two-column kernels hold a point past the box
-    at zero; (16, 5, 4): fewer planes than the stencil's reach (nz < 6), even nx (16-byte pair
-    loads in the fused kernel)."""
+    at zero (and the cluster form splits 7 row pairs into bands of 4 and 3); (16, 5, 4): fewer
+    planes than the stencil's reach (nz < 6), even nx (16-byte pair loads in the fused kernel);
+    (20, 26, 7): the cluster form with bands of 7 and 6 row pairs.  The cluster form (6) needs
+    bands of at least 3 row pairs and stands in with the fused kernel where they do not fit."""
     s = synth.small_system(grid, h=0.5, n_s=2, n_wells=2, seed=29)
     g = oracle.Grid(s.nx, s.ny, s.nz, s.h)
     rng = np.random.default_rng(8)
@@ -447,3 +449,29 @@ def test_frequency_ranges_sum_to_the_full_quadrature(rpa, tiny):
     assert np.array_equal(parts[0].e_c_per_omega[:3], full.e_c_per_omega[:3])
     assert np.array_equal(parts[1].e_c_per_omega[3:], full.e_c_per_omega[3:])
     assert np.all(parts[0].lambdas[3:] == 0) and np.array_equal(parts[1].lambdas[3:], full.lambdas[3:])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cluster_form_for_planes_past_one_block(rpa, prec):
+    """A 46 x 46 plane's ring (248 KB) does not fit one block's shared memory: the mixed form runs
+    the cluster form of the fused kernel (two blocks, each with the ring of a band of 12 or 11 row
+    pairs, the rows past its band read from the other block), the FP64 form the split kernels."""
+    s = synth.small_system((46, 46, 2), h=0.5, n_s=2, n_wells=2, seed=37)
+    g = oracle.Grid(s.nx, s.ny, s.nz, s.h)
+    b = np.random.default_rng(9).standard_normal((5, s.n_d))
+    orbs = np.array([0, 1, 0, 1, 1])
+    omega, tol = 0.25, 1e-11
+    p = rpa.RPA_MIXED if prec == "mixed" else rpa.RPA_FP64
+    with rpa.Context.from_system(s, opts(rpa, tol=tol, prec=p)) as ctx:
+        x, _, st, code = ctx.sternheimer_solve(omega, orbs, cuda(b), project=True)
+        # which COCG kernel ran: the per-kernel profile of a short E_c evaluation
+        ctx.set_options(opts(rpa, tol=1e-8, prec=p, profile=1, n_omega=1, fixed_subspace_iters=1))
+        res = ctx.ec(cuda(synth.trial_vectors(37, 2, s.n_d)))
+    names = {k["name"] for k in res.stats["kernels"]}
+    assert ("k_cocg_ring_cl<c64>" in names) if prec == "mixed" else ("k_cocg_pa<c128>" in names), names
+    assert code == rpa.RPA_OK and np.all(st.cpu().numpy() == 0)
+    sig = -s.eps[orbs] + 1j * omega
+    bp = b - (b @ s.psi.T) @ s.psi
+    ref, _, rst = oracle.cocg(g, s.vloc, sig, bp.astype(complex), tol, 100000)
+    assert np.all(rst == 0)
+    assert relerr(x.cpu().numpy(), ref) < 1e-8
