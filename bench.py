@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mixed40")
+    ap.add_argument("--precondition", type=int, default=0,
+                    help="rpa_options.precondition: 1 = Laplacian-preconditioned COCG")
     ap.add_argument("--stencil-shape", type=int, default=-1,
                     help="rpa_options.stencil_shape for the timed steps (-1: the autotuner's choice)")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
@@ -303,6 +305,7 @@ def run_ours(args):
     opts.n_atoms = s.n_atoms
     opts.profile = 0                           # the timed steps run without per-launch events
     opts.periodic = int(getattr(s, "periodic", False))   # the system's boundary conditions
+    opts.precondition = args.precondition
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = rpa.Context.from_system(s, opts)
@@ -392,6 +395,7 @@ def run_ours(args):
                            "l2": "flushed (512 MB write) between timed steps",
                            "contractions": "tensor cores (tcgen05, exact integer pieces)"
                            if args.prec == "mixed" else "FP64 CUDA cores",
+                           "cocg": "Laplacian-preconditioned" if args.precondition else "plain",
                            "mean_cocg_iterations_per_solve": mean_iters,
                            "near_breakdowns_per_step": sum(st.get("near_breakdowns", 0) for st in kstats) / args.steps,
                            "autotune": tune,
@@ -405,7 +409,7 @@ def run_ours(args):
                 "e_c_per_atom_last_step": res.e_c_per_atom}
     if not args.no_fp64 and rank == 0:
         o64 = rpa.default_options()
-        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "periodic"):
+        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "periodic", "precondition"):
             setattr(o64, k, getattr(opts, k))
         o64.prec = rpa.RPA_FP64
         r64, ms64 = timed_ec(o64)
@@ -421,7 +425,7 @@ def run_ours(args):
         tts = {}
         for name, prec in (("mixed", rpa.RPA_MIXED), ("fp64", rpa.RPA_FP64)):
             ot = rpa.default_options()
-            for k in ("tol", "n_omega", "n_atoms", "stencil_shape", "z_chunks", "periodic"):
+            for k in ("tol", "n_omega", "n_atoms", "stencil_shape", "z_chunks", "periodic", "precondition"):
                 setattr(ot, k, getattr(opts, k))
             ot.prec = prec
             ot.eps_c = 1e-5

@@ -135,6 +135,15 @@ typedef struct {
                                   stencil takes the periodic continuation of every grid function,
                                   and nu^p acts with the G = 0 mode removed (the constant function
                                   maps to zero: the neutralising background of a periodic cell). */
+    int precondition;          /* 1: COCG preconditioned by M = (-1/2 L_h + s)^-1, s = mean(V_loc) -
+                                  eps_n + i omega, applied through the Kronecker eigendecomposition
+                                  of L_h (the paper's Laplacian-based preconditioning, Section
+                                  "Implementation"): fewer iterations, each with three extra passes
+                                  over the vectors.  Runs the split COCG kernels (stencil_shape 1..3;
+                                  the fused kernels 4..6 stand in with 1).  Needs a plane's two
+                                  complex copies and the x and y factors in one block's shared
+                                  memory (FP32: planes up to ~80 x 80; FP64: ~64 x 64) and
+                                  nz <= 96.  0 (default): plain COCG. */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8
@@ -174,7 +183,8 @@ typedef struct {
 /* Fill *opt with defaults: FP64, tol 1e-8, maxit 20000, max_refine 20, inner_tol 1e-4,
  * eps_c 1e-5, n_omega 8, omega0 1, max_subspace_iters 100, fixed 0, n_atoms 1, batch 0,
  * profile 0, project_solution 0, z_chunks 0, stencil_shape 0 (automatic), independent_frequencies 0,
- * sq_order 0, contractions 0 (automatic), omega_first 0, omega_count 0 (all frequencies), periodic 0. */
+ * sq_order 0, contractions 0 (automatic), omega_first 0, omega_count 0 (all frequencies), periodic 0,
+ * precondition 0. */
 void rpa_default_options(rpa_options *opt);
 
 /* Create a context for one system (the inputs of Algorithm 1: H, P = the orbitals, eps).

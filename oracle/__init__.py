@@ -17,10 +17,16 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                         quadrature of the dense integrand; convergence in N_omega
   rpa_ec_gradient       central finite differences of a dense sum-over-states E_c built
                         from the unoccupied eigenpairs of the projected Hamiltonian
+  periodic grids        the stencil's closed-form symbol on Fourier modes, plane waves, dense
+                        pseudo-inverses, sum over states (tests/test_oracle_pins_periodic.py)
+  laplacian_preconditioner  dense inverse of -1/2 L_h + shift
+  pcocg                 dense complex solve; with a multiple of the identity as M it is COCG
+                        (same iterates as cocg); fewer iterations than cocg at small omega
   gauss_sq_trace        exactness for polynomials of degree <= 2 N_o - 1 (Gauss rule); order 1
                         is sum f(C_rr); order >= the dimension is Tr f(C) by dense eigenvalues
 """
 from .rpa_oracle import *  # noqa: F401,F403
 from .rpa_oracle import (Oracle, Grid, Coulomb, SolveStats, EcResult, fd_weights, apply_h, cocg,  # noqa: F401
                          frequency_quadrature, g_rpa, orthonormalize_cholesky, rpa_ec, num_threads,
-                         set_threads, second_difference_1d, NotSPD, rpa_ec_gradient, gauss_sq_trace)
+                         set_threads, second_difference_1d, NotSPD, rpa_ec_gradient, gauss_sq_trace,
+                         laplacian_preconditioner, pcocg)

@@ -157,6 +157,8 @@ def cocg(grid: Grid, vloc: np.ndarray, sigma: np.ndarray, b: np.ndarray, tol: fl
 # ------------------------------------------------------------------------------------
 # Coulomb operator by the Kronecker-product formalism (Section "Implementation")
 # ------------------------------------------------------------------------------------
+# (The preconditioned COCG, which uses the same eigendecomposition of -L_h, follows the Coulomb
+# operator below.)
 def second_difference_1d(n: int, h: float, periodic: bool = False) -> np.ndarray:
     """Dense 1D second-derivative matrix: zero boundary values (Toeplitz), or the periodic
     continuation (circulant: every tap i +- k taken modulo n, so taps that wrap onto the same
@@ -210,6 +212,74 @@ class Coulomb:
 
 
 # ------------------------------------------------------------------------------------
+# Laplacian-preconditioned COCG (Section "Implementation": Laplacian-based preconditioning
+# through the Kronecker product formalism)
+# ------------------------------------------------------------------------------------
+def laplacian_preconditioner(coulomb: "Coulomb", shift: complex):
+    """M = (-1/2 L_h + shift)^(-1) applied to rows of a complex block, through the Kronecker
+    eigendecomposition -L_h = (Q_z x Q_y x Q_x) diag(lam) (...)^T: the Sternheimer operator
+    H - eps_n + i omega with V_loc replaced by a constant (the paper names the preconditioner and
+    the formalism, not the shift; reading: shift = mean(V_loc) - eps_n + i omega)."""
+    g = coulomb.grid
+    Qx, Qy, Qz = coulomb.Q
+    d = 1.0 / (0.5 * coulomb.lam + shift)
+
+    def apply(R):
+        Y = np.asarray(R, dtype=np.complex128).reshape(-1, g.nz, g.ny, g.nx)
+        Y = np.einsum("ia,kzyi->kzya", Qx, Y)
+        Y = np.einsum("ja,kzjx->kzax", Qy, Y)
+        Y = np.einsum("la,klyx->kayx", Qz, Y)
+        Y = Y * d[None]
+        Y = np.einsum("ia,kzya->kzyi", Qx, Y)
+        Y = np.einsum("ja,kzax->kzjx", Qy, Y)
+        Y = np.einsum("la,kayx->klyx", Qz, Y)
+        return Y.reshape(np.shape(R))
+    return apply
+
+
+def pcocg(grid: Grid, vloc: np.ndarray, sigma: complex, b: np.ndarray, tol: float, maxit: int, apply_m):
+    """Preconditioned COCG for (H + sigma) x = b, every row of b, with the complex-symmetric
+    preconditioner apply_m (van der Vorst & Melissen's COCG with M; unconjugated r^T z):
+        r = b, z = M r, p = z, rho = r^T z;  repeat: q = A p, alpha = rho / p^T q, x += alpha p,
+        r -= alpha q, z = M r, rho' = r^T z, p = z + (rho'/rho) p;
+    stop when ||r||_2 <= tol ||b||_2 (checked before each iteration).  Returns (x, iterations,
+    status) like cocg; status 5 where p^T q or r^T z vanishes."""
+    b = np.atleast_2d(np.asarray(b, dtype=np.complex128))
+    ns = b.shape[0]
+    x = np.zeros_like(b)
+    its = np.zeros(ns, dtype=np.int32)
+    st = np.zeros(ns, dtype=np.int32)
+    for s in range(ns):
+        r = b[s].copy()
+        bn = np.linalg.norm(b[s])
+        z = apply_m(r[None])[0]
+        p = z.copy()
+        rho = r @ z
+        k = 0
+        while True:
+            if np.linalg.norm(r) <= tol * bn:
+                break
+            if k >= maxit:
+                st[s] = NOT_CONVERGED
+                break
+            q = apply_h(grid, vloc, p, sigma)
+            pq = p @ q
+            if pq == 0 or rho == 0:
+                st[s] = BREAKDOWN
+                break
+            alpha = rho / pq
+            x[s] += alpha * p
+            r -= alpha * q
+            z = apply_m(r[None])[0]
+            rho_new = r @ z
+            p = z + (rho_new / rho) * p
+            rho = rho_new
+            k += 1
+        its[s] = k
+    return x, its, st
+
+
+# ------------------------------------------------------------------------------------
 # chi0 by density functional perturbation theory (Eqs. 7-9, Algorithm 1 inner loop)
 # ------------------------------------------------------------------------------------
 @dataclass
@@ -255,7 +325,8 @@ class Oracle:
 
     def chi0(self, dv: np.ndarray, omega: float, tol: float, maxit: int = 100000, sign: int = +1,
              stats: Optional[SolveStats] = None, max_chunk_bytes: float = 2.5e8,
-             galerkin: bool = False, return_x: bool = False, project_solution: bool = False):
+             galerkin: bool = False, return_x: bool = False, project_solution: bool = False,
+             precondition: bool = False):
         """drho = chi0(i omega) dV for every row of dv (Eqs. 7-9).
 
         For each occupied n and each dV: solve (H - eps_n + sign*i*omega) x = b by COCG, then
@@ -263,7 +334,8 @@ class Oracle:
         initial guess instead of projecting the right-hand side (Section "Implementation").
         project_solution=True also removes the occupied components of x (x <- P_c x): the same
         operator when the orbitals are exact eigenvectors of H, and the first-order-consistent
-        response of the fixed occupied space when V_loc moves away from them.
+        response of the fixed occupied space when V_loc moves away from them.  precondition=True
+        solves by the Laplacian-preconditioned COCG (pcocg) instead.
         """
         g = self.grid
         dv = np.atleast_2d(np.asarray(dv, dtype=np.float64))
@@ -280,7 +352,11 @@ class Oracle:
                     x = self._galerkin_solve(n, blk, sigma, tol, maxit, stats)
                 else:
                     b = self.sternheimer_rhs(n, blk).astype(np.complex128)
-                    x, it, st = cocg(g, self.vloc, np.full(len(blk), sigma), b, tol, maxit)
+                    if precondition:
+                        m = laplacian_preconditioner(self.coulomb, float(np.mean(self.vloc)) + sigma)
+                        x, it, st = pcocg(g, self.vloc, sigma, b, tol, maxit, m)
+                    else:
+                        x, it, st = cocg(g, self.vloc, np.full(len(blk), sigma), b, tol, maxit)
                     if stats is not None:
                         stats.iterations.append(it)
                         stats.status.append(st)

@@ -74,6 +74,11 @@ Ctx::~Ctx() {
     cudaFree(eps_dev);
     for (double *q : Q) cudaFree(q);
     cudaFree(lam);
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(mu[a]);
+        cudaFree(Qf[a]);
+        cudaFree(muf[a]);
+    }
     for (DevBuf *b : {&cocg_state, &cocg_partials, &sys_state, &rhs, &pc_coef, &coul_tmp, &blockA, &blockB,
                       &blockC, &blockD, &small, &slot_idx, &dense_scratch, &proj_buf, &coef_buf, &blockE})
         b->release();
@@ -161,6 +166,7 @@ void validate_options(const rpa_options &o) {
     if (o.sq_order < 0 || o.sq_order > kMaxSqOrder) fail(RPA_ERR_INVALID, "sq_order must be in [0, %d]", kMaxSqOrder);
     if (o.contractions < 0 || o.contractions > 3) fail(RPA_ERR_INVALID, "contractions must be in [0, 3]");
     if (o.periodic != 0 && o.periodic != 1) fail(RPA_ERR_INVALID, "periodic must be 0 or 1");
+    if (o.precondition != 0 && o.precondition != 1) fail(RPA_ERR_INVALID, "precondition must be 0 or 1");
     if (o.omega_count < 0 || o.omega_first < 0 || (o.omega_count > 0 && o.omega_first + o.omega_count > o.n_omega) ||
         (o.omega_count == 0 && o.omega_first != 0))
         fail(RPA_ERR_INVALID, "omega_first/omega_count must select a range of the n_omega frequencies");
@@ -322,6 +328,7 @@ void rpa_default_options(rpa_options *o) {
     o->omega_first = 0;
     o->omega_count = 0;
     o->periodic = 0;
+    o->precondition = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }
@@ -392,6 +399,13 @@ rpa_status rpa_setup(rpa_ctx **out, int nx, int ny, int nz, double h, int fd_ord
                 c.use_graphs = !(g && g[0] == '0');
             }
             RPA_CUDA(cudaStreamSynchronize(s));
+            {   // mean V_loc: the constant potential of the Laplacian preconditioner
+                std::vector<double> v((size_t)nd);
+                RPA_CUDA(cudaMemcpy(v.data(), c.vloc64, sizeof(double) * nd, cudaMemcpyDeviceToHost));
+                double sum = 0.0;
+                for (double x : v) sum += x;
+                c.vbar = sum / (double)nd;
+            }
             coulomb_setup(c);
         } catch (...) {
             delete ctx;

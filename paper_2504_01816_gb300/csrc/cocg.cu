@@ -118,6 +118,9 @@ struct Params {
     int proj_re_only;           // only Re(u_k . x) is needed (the solutions retire into drho)
     float *Tp32;                // [S][ns][2]       Tp in FP32 (for FP32 updates)
     const float *psi32;         // ns x nd orbitals in FP32
+    // Laplacian-preconditioned COCG: rho = r^T z from the per-plane partial sums of z = M r
+    int precond;
+    double *partZ;              // [S][nz][3] r^T z (re, im), ||z||^2
 };
 
 // The fields of Params that the two streaming kernels of the iteration read, passed on their
@@ -214,6 +217,257 @@ __device__ __forceinline__ void coords(long long idx, const Grid3 &g, int &i, in
 }
 
 // ---------------------------------------------------------------------------------------------
+// Laplacian preconditioner (rpa_options.precondition; paper, Section "Implementation": Laplacian-
+// based preconditioning through the Kronecker product formalism).  z = M r with
+//   M = (-1/2 L_h + s)^(-1) = Q diag(1 / (lam / 2 + s)) Q^T,  s = mean(V_loc) - eps_n + i omega,
+// Q = Q_z x Q_y x Q_x and lam = mu_x + mu_y + mu_z the eigendecompositions of the 1D -D (those of
+// the Coulomb operator), for every slot in its inner solve, in three passes over the slot's vector:
+// the x and y transforms of every plane (k_pc_xy, forward), the z transform, the diagonal and the
+// inverse z transform of every column (k_pc_z), the inverse x and y transforms (k_pc_xy, back, which
+// also forms the partial sums of r^T z and ||z||^2 per plane).  Each transform is a small matrix
+// product in shared memory with 2 x 4 outputs per thread.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPcThreads = 256;
+
+template <typename T> struct PcArgs {
+    Slot *slots;
+    int S, nx, ny, nz;
+    long long nd;
+    const T *Qx, *Qy, *Qz;         // n x n, Q[i n + a] = component i of eigenvector a
+    const T *mux, *muy, *muz;      // their eigenvalues (of -D, the 1D factors of -L_h)
+    double vbar;                   // mean V_loc, the constant potential of the preconditioner
+    double *partZ;                 // [S][nz][3] per plane: r^T z (re, im), ||z||^2
+};
+
+// Bytes of the real 1D matrices at the start of the preconditioner kernels' shared memory, rounded
+// up to 16 so that the complex arrays after them are aligned for their element type.
+__host__ __device__ inline size_t pc_mat_bytes(size_t elems, size_t tsz) { return (elems * tsz + 15) / 16 * 16; }
+constexpr int kPcTiles = 4;        // 2 x 4 output tiles per thread in k_pc_xy (planes of <= 4 x 256 tiles)
+// Shared-memory bytes of k_pc_xy: the two 1D matrices and one complex plane (rows padded by one).
+template <typename T> size_t pc_xy_bytes(int nx, int ny) {
+    return pc_mat_bytes((size_t)nx * nx + (size_t)ny * ny, sizeof(T)) + sizeof(typename Cx<T>::t) * (size_t)ny * (nx + 1);
+}
+// acc += m x for a real m and a complex x (packed FP32x2 for float)
+__device__ __forceinline__ void cmac(float2 &acc, float m, float2 x) { acc = __ffma2_rn(make_float2(m, m), x, acc); }
+__device__ __forceinline__ void cmac(double2 &acc, double m, double2 x) {
+    acc.x = fma(m, x.x, acc.x);
+    acc.y = fma(m, x.y, acc.y);
+}
+
+// out(plane) = (M_y (x) M_x) in(plane) for every plane of every slot in its inner solve, with
+// M = Q^T (FWD) or Q (back); back also sums r^T out and ||out||^2 per plane.  The x pass keeps its
+// tiles in registers and writes them over the plane after a barrier (one plane buffer).
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kPcThreads) k_pc_xy(PcArgs<T> A, const typename Cx<T>::t *__restrict__ in,
+                                                      typename Cx<T>::t *__restrict__ out,
+                                                      const typename Cx<T>::t *__restrict__ r) {
+    using C = typename Cx<T>::t;
+    extern __shared__ double pc_sh[];
+    const int nx = A.nx, ny = A.ny, W = nx + 1;
+    T *const Mx = reinterpret_cast<T *>(pc_sh);          // Mx[i nx + a]: x pass Y[j][a] = sum_i X[j][i] Mx[i][a]
+    T *const My = Mx + (size_t)nx * nx;                   // My[b ny + j]: y pass Z[b][a] = sum_j My[b][j] Y[j][a]
+    C *const X = reinterpret_cast<C *>(reinterpret_cast<char *>(pc_sh) +
+                                       pc_mat_bytes((size_t)nx * nx + (size_t)ny * ny, sizeof(T)));
+    for (int e = threadIdx.x; e < nx * nx; e += blockDim.x) {
+        const int i = e / nx, a = e - i * nx;
+        Mx[e] = FWD ? A.Qx[(size_t)i * nx + a] : A.Qx[(size_t)a * nx + i];
+    }
+    for (int e = threadIdx.x; e < ny * ny; e += blockDim.x) {
+        const int b = e / ny, j = e - b * ny;
+        My[e] = FWD ? A.Qy[(size_t)j * ny + b] : A.Qy[(size_t)b * ny + j];
+    }
+    const int plane = nx * ny;
+    const int tx = (nx + 3) / 4, ty = (ny + 1) / 2;      // 2 x 4 output tiles
+    const C zc = C{0, 0};
+    const long long items = (long long)A.S * A.nz;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / A.nz), k = (int)(it - (long long)s * A.nz);
+        if (A.slots[s].phase != kInner) continue;         // uniform per block
+        const long long base = (long long)s * A.nd + (long long)k * plane;
+        __syncthreads();                                  // the previous item's readers are done
+        for (int e = threadIdx.x; e < plane; e += blockDim.x) {
+            const int j = e / nx, i = e - j * nx;
+            X[j * W + i] = in[base + e];
+        }
+        __syncthreads();
+        // x pass: Y = X Mx, tiles in registers
+        C acc[kPcTiles][2][4];
+#pragma unroll
+        for (int u = 0; u < kPcTiles; ++u) {
+            const int t = threadIdx.x + u * kPcThreads;
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[u][rr][q] = zc;
+            if (t < tx * ty) {
+                const int j0 = 2 * (t / tx), a0 = 4 * (t % tx);
+                const int j1 = min(j0 + 1, ny - 1);          // a row past the plane repeats the last (discarded)
+                for (int i = 0; i < nx; ++i) {
+                    const C x0 = X[j0 * W + i], x1 = X[j1 * W + i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const T m = a0 + q < nx ? Mx[i * nx + a0 + q] : (T)0;
+                        cmac(acc[u][0][q], m, x0);
+                        cmac(acc[u][1][q], m, x1);
+                    }
+                }
+            }
+        }
+        __syncthreads();                                  // every thread has read X
+#pragma unroll
+        for (int u = 0; u < kPcTiles; ++u) {
+            const int t = threadIdx.x + u * kPcThreads;
+            if (t < tx * ty) {
+                const int j0 = 2 * (t / tx), a0 = 4 * (t % tx);
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (j0 + rr < ny && a0 + q < nx) X[(j0 + rr) * W + a0 + q] = acc[u][rr][q];
+            }
+        }
+        __syncthreads();
+        // y pass: Z = My Y, written out; back: partial sums with r
+        T d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+        for (int u = 0; u < kPcTiles; ++u) {
+            const int t = threadIdx.x + u * kPcThreads;
+            if (t >= tx * ty) continue;
+            const int b0 = 2 * (t / tx), a0 = 4 * (t % tx);
+            C z[2][4];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) z[rr][q] = zc;
+            for (int j = 0; j < ny; ++j) {
+                const T m0 = My[b0 * ny + j], m1 = b0 + 1 < ny ? My[(b0 + 1) * ny + j] : (T)0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const C y = a0 + q < nx ? X[j * W + a0 + q] : zc;
+                    cmac(z[0][q], m0, y);
+                    cmac(z[1][q], m1, y);
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (b0 + rr < ny && a0 + q < nx) {
+                        const long long g = base + (long long)(b0 + rr) * nx + a0 + q;
+                        out[g] = z[rr][q];
+                        if (!FWD) {
+                            const C rv = r[g];
+                            d0 += rv.x * z[rr][q].x - rv.y * z[rr][q].y;
+                            d1 += rv.x * z[rr][q].y + rv.y * z[rr][q].x;
+                            d2 += z[rr][q].x * z[rr][q].x + z[rr][q].y * z[rr][q].y;
+                        }
+                    }
+        }
+        if (!FWD) {
+            const T dv[3] = {d0, d1, d2};
+            double v[3];
+            block_sum_t<T, 3>(dv, v);
+            if (threadIdx.x == 0) {
+                double *o = A.partZ + ((long long)s * A.nz + k) * 3;
+                o[0] = v[0];
+                o[1] = v[1];
+                o[2] = v[2];
+            }
+        }
+    }
+}
+
+// In place, for every column of every slot in its inner solve: the z transform (Q_z^T), the
+// diagonal 1 / (lam / 2 + s), the inverse z transform (Q_z).  A block takes 32 consecutive
+// columns; warp w forms the outputs c = w, w + 8, ... of its lane's column.
+template <typename T>
+__global__ void __launch_bounds__(kPcThreads) k_pc_z(PcArgs<T> A, typename Cx<T>::t *__restrict__ buf) {
+    using C = typename Cx<T>::t;
+    constexpr int kMaxPer = 12;                           // outputs per thread: nz <= 8 kMaxPer
+    extern __shared__ double pc_sh[];
+    const int nz = A.nz, plane = A.nx * A.ny;
+    T *const Qz = reinterpret_cast<T *>(pc_sh);           // Qz[k nz + c]
+    C *const X = reinterpret_cast<C *>(reinterpret_cast<char *>(pc_sh) + pc_mat_bytes((size_t)nz * nz, sizeof(T)));   // X[k * 33 + lane]
+    for (int e = threadIdx.x; e < nz * nz; e += blockDim.x) Qz[e] = A.Qz[e];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles = (plane + 31) / 32;
+    const long long items = (long long)A.S * tiles;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = (int)(it / tiles), p0 = (int)(it - (long long)s * tiles) * 32;
+        const Slot &sl = A.slots[s];
+        if (sl.phase != kInner) continue;                 // uniform per block
+        const long long base = (long long)s * A.nd;
+        const int p = p0 + lane;
+        const bool own = p < plane;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nz * 32; e += blockDim.x) {
+            const int k = e >> 5, l = e & 31;
+            X[k * 33 + l] = p0 + l < plane ? buf[base + (long long)k * plane + p0 + l] : C{0, 0};
+        }
+        __syncthreads();
+        // forward and diagonal: W[c] = d_c sum_k Qz[k][c] X[k]
+        T wr[kMaxPer], wi[kMaxPer];
+#pragma unroll
+        for (int m = 0; m < kMaxPer; ++m) wr[m] = wi[m] = 0;
+        for (int k = 0; k < nz; ++k) {
+            const C x = X[k * 33 + lane];
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m) {
+                const int c = warp + 8 * m;
+                if (c < nz) {
+                    const T q = Qz[k * nz + c];
+                    wr[m] += q * x.x;
+                    wi[m] += q * x.y;
+                }
+            }
+        }
+        const int iy = own ? p / A.nx : 0, ix = own ? p - iy * A.nx : 0;
+        const T sr = (T)(A.vbar + sl.shift_re), si = (T)sl.shift_im;
+        const T mxy = own ? A.mux[ix] + A.muy[iy] : (T)0;
+#pragma unroll
+        for (int m = 0; m < kMaxPer; ++m) {
+            const int c = warp + 8 * m;
+            if (c < nz) {
+                const T dr = (T)0.5 * (mxy + A.muz[c]) + sr;
+                const T inv = (T)1 / (dr * dr + si * si);
+                const T fr = dr * inv, fi = -si * inv;                // 1 / (dr + i si)
+                const T a = wr[m], b = wi[m];
+                wr[m] = a * fr - b * fi;
+                wi[m] = a * fi + b * fr;
+            }
+        }
+        __syncthreads();                                  // every warp has read X
+#pragma unroll
+        for (int m = 0; m < kMaxPer; ++m) {
+            const int c = warp + 8 * m;
+            if (c < nz) X[c * 33 + lane] = C{wr[m], wi[m]};
+        }
+        __syncthreads();
+        // inverse: Z[k] = sum_c Qz[k][c] W[c]
+#pragma unroll
+        for (int m = 0; m < kMaxPer; ++m) wr[m] = wi[m] = 0;
+        for (int c = 0; c < nz; ++c) {
+            const C w = X[c * 33 + lane];
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m) {
+                const int k = warp + 8 * m;
+                if (k < nz) {
+                    const T q = Qz[k * nz + c];
+                    wr[m] += q * w.x;
+                    wi[m] += q * w.y;
+                }
+            }
+        }
+        if (own)
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m) {
+                const int k = warp + 8 * m;
+                if (k < nz) buf[base + (long long)k * plane + p] = C{wr[m], wi[m]};
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // COCG iteration: two per-slot scalar kernels (one warp per slot, the only writers of the slot
 // state during the iteration) and three kernels over the active (slot, chunk) items.
 // ---------------------------------------------------------------------------------------------
@@ -227,6 +481,14 @@ __global__ void k_beta(Params P, int par) {
     if (sl.phase != kInner) return;
     double v[3];
     warp_slot_sum<3, 3>(P.partB + (long long)w * P.nblk * 3, P.nblk, v);
+    double zz = v[2];                   // ||z||^2 (preconditioned), else ||r||^2
+    if (P.precond) {                    // rho = r^T z, the stopping test on ||r||
+        double vz[3];
+        warp_slot_sum<3, 3>(P.partZ + (long long)w * P.g.nz * 3, P.g.nz, vz);
+        v[0] = vz[0];
+        v[1] = vz[1];
+        zz = vz[2];
+    }
     if (lane != 0) return;
     const int k = sl.iters;
     const double rn = sqrt(v[2]);
@@ -236,7 +498,7 @@ __global__ void k_beta(Params P, int par) {
     const double rr2 = v[0] * v[0] + v[1] * v[1];
     const bool nonfinite = !isfinite(rn) || !isfinite(rr2);
     const bool zero = !(rr2 > 0.0);
-    const bool nearb = P.mixed && k > 0 && !(rr2 > kNearBreak * kNearBreak * v[2] * v[2]);
+    const bool nearb = P.mixed && k > 0 && !(rr2 > kNearBreak * kNearBreak * v[2] * zz);
     sl.rnorm = rn;
     if (conv || k >= P.maxit || nonfinite || zero || nearb) {
         if (P.mixed) {
@@ -1117,12 +1379,12 @@ __device__ __forceinline__ void ring_load_rv(const RingUnit &U, int g0, const fl
     }
 }
 
-// Cluster form: the rows of a block's band, [y0, y1), and the same ring slot in this block and in
-// the blocks of the bands above and below, as shared::cluster addresses (a shared::cta address is
-// one for the executing block).
+// Cluster form: the rows of a block's band, [y0, y1), and the block's copy of the plane's 6 rows
+// above and 6 rows below its band (the halo, rows y0-6 .. y0-1 then y1 .. y1+5, laid out as ring rows
+// after a zero word), taken from the neighbouring blocks' rings.
 struct Band {
-    int y0, y1, rows;              // rows: 2 bp, the height of every band but the last
-    unsigned self, up, dn;
+    int y0, y1;
+    const unsigned char *halo;
 };
 
 // Two x-adjacent points from a ring slot of any block of the cluster: one 16-byte load.
@@ -1154,18 +1416,18 @@ __device__ __forceinline__ void ring_stencil(const RingUnit &U, const unsigned c
         if (PER) return pz + U.rb0 + (wrap_index(r, ny) - U.gy) * rsb;
         return (r >= 0 && r < ny) ? pz + U.rb0 + (r - U.gy) * rsb : pz;
     };
-    // cluster form: row r in this block's band or a neighbour's, or the zero word outside the box,
-    // all through shared::cluster addresses (one load instruction for every case: a branch between
-    // shared and distributed shared loads measured more spills)
+    // cluster form: row r in this block's band, in its halo copy of the neighbouring bands' rows, or
+    // the zero word outside the box
     auto yrow = [&](int r, float2 &a, float2 &b) {
         if (BAND) {
-            unsigned ad = B.self;
+            const int xoff = U.rb0 - (U.gy - B.y0) * rsb;      // the unit's column within a row
+            const unsigned char *ad = pz;
             if (r >= 0 && r < ny) {
-                if (r < B.y0) ad = B.up + U.rb0 + (r - U.gy + B.rows) * rsb;
-                else if (r >= B.y1) ad = B.dn + U.rb0 + (r - U.gy - (B.y1 - B.y0)) * rsb;
-                else ad = B.self + U.rb0 + (r - U.gy) * rsb;
+                if (r < B.y0) ad = B.halo + xoff + (r - B.y0 + kRadius) * rsb;
+                else if (r >= B.y1) ad = B.halo + xoff + (r - B.y1 + kRadius) * rsb;
+                else ad = pz + xoff + (r - B.y0) * rsb;
             }
-            ring_pair_cl(ad, a, b);
+            ring_pair(ad, a, b);
         } else {
             ring_pair(row(r), a, b);
         }
@@ -1392,11 +1654,14 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
 // step z and released by the first arrival at or after it (at most kClusterEvery-1 steps later,
 // waited on one step after that, so by step z+kClusterEvery <= z+5); the ring slot a block overwrites
 // at step f was last read by any block at step f-8, before that block's next arrival (one falls in
-// every window of kClusterEvery steps) and so before the writer's wait.  Units whose y neighbours
-// all lie in their own band run the single-block stencil; the others load rows through
-// shared::cluster addresses.  The scalar step is taken by rank 0 from the bands' sums, added in rank
-// order; the next system, the stopping decision and the bands' sums pass through shared memory of
-// the cluster.  Dirichlet grids.
+// every window of kClusterEvery steps) and so before the writer's wait.  The neighbours' rows are
+// not read in the stencil: at step f a block copies the 6 rows next to its band of plane f-5 from
+// the neighbouring blocks' rings into a local halo (double-buffered by plane parity; the copy's
+// distributed shared-memory loads overlap the stencil), and the stencil of step f+1 reads them
+// there.  Units whose y neighbours all lie in their own band run the single-block stencil.  The
+// scalar step is taken by rank 0 from the bands' sums, added in rank order; the next system, the
+// stopping decision and the bands' sums pass through shared memory of the cluster.  Dirichlet
+// grids.
 namespace cg = cooperative_groups;
 
 constexpr int kClusterEvery = 4;           // steps per cluster barrier phase (at most 5, see above)
@@ -1416,10 +1681,12 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
     const int tid = threadIdx.x;
     const int nz = A.nz, plane = A.nx * A.ny;
     const int rsb = A.rs * 8, psb = A.ps * 8;
+    const int hsb = (2 + 2 * kRadius * A.rs) * 8;  // halo buffer: zero word and 12 rows
+    unsigned char *const halo = ring + kRingPlanes * psb;
+    const int rows = 2 * A.bp;                     // every band but the last
     Band B;
-    B.rows = 2 * A.bp;
-    B.y0 = rank * B.rows;
-    B.y1 = min(A.ny, B.y0 + B.rows);
+    B.y0 = rank * rows;
+    B.y1 = min(A.ny, B.y0 + rows);
     const int npairs = max(0, (B.y1 - B.y0 + 1) / 2);
     const RingUnit U = ring_unit(tid, A, B.y0, npairs);
     // a unit whose y neighbours (rows y-6 .. y+7) reach into another block's band
@@ -1430,7 +1697,8 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
     if (rank > 0) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ring_up) : "r"(ring_self), "r"(rank - 1));
     if (rank + 1 < ncl) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ring_dn) : "r"(ring_self), "r"(rank + 1));
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int e = tid; e < kRingPlanes * A.ps / 2; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
+    for (int e = tid; e < (kRingPlanes * psb + 2 * hsb) / 16; e += blockDim.x) ring4[e] = zero4;   // padding stays zero
+    const int nhalo = 2 * kRadius * A.hw;          // 16-byte words copied into the halo per plane
     const int n_items = *A.cnt_in;
     for (;;) {
         cl.sync();                                 // every block is done with the previous system
@@ -1480,14 +1748,27 @@ __global__ void __launch_bounds__(kRingMaxThreads, 1)
                 if (U.own && f + 1 < nz)
                     ring_load_front<EVEN>(U, (f + 1) * plane + U.col0, first, xs, rsv, psv, qs, F);
                 __syncthreads();
-                // 3. q_k on plane z, its 6 neighbour planes from the ring, rows past the band from the
-                // neighbouring blocks' rings
+                // 3. the halo of plane f-5 (used at the next step) from the neighbouring blocks' rings
+                const int zc = f - kRadius + 1;
+                if (zc >= 0 && zc < nz) {
+                    const int cs = u >= kRadius - 1 ? u - (kRadius - 1) : u + kRingPlanes - (kRadius - 1);   // slot of zc
+                    unsigned char *const hb = halo + (zc & 1) * hsb;
+                    for (int e = tid; e < nhalo; e += blockDim.x) {
+                        const int h = e / A.hw, bx = e - h * A.hw;          // halo row, point pair
+                        const int r = h < kRadius ? B.y0 - kRadius + h : B.y1 + h - kRadius;
+                        if (r < 0 || r >= A.ny) continue;                   // outside the box: read as zeros
+                        const unsigned src = (h < kRadius ? ring_up : ring_dn) + cs * psb +
+                                             (2 + (h < kRadius ? r - (B.y0 - rows) : r - B.y1) * A.rs + 2 * bx) * 8;
+                        float2 a, b;
+                        ring_pair_cl(src, a, b);
+                        *reinterpret_cast<float4 *>(hb + (2 + h * A.rs + 2 * bx) * 8) = make_float4(a.x, a.y, b.x, b.y);
+                    }
+                }
+                // 4. q_k on plane z, its 6 neighbour planes from the ring, rows past the band from the halo
                 if (U.own && z >= 0) {
                     const int cz = u >= kRadius ? u - kRadius : u + kRingPlanes - kRadius;   // ring slot of z
                     if (remote) {
-                        B.self = ring_self + cz * psb;
-                        B.up = ring_up + cz * psb;      // used only for rows of a band above (rank > 0)
-                        B.dn = ring_dn + cz * psb;      // and below (rank < ncl - 1)
+                        B.halo = halo + (z & 1) * hsb;
                         ring_stencil<EVEN, false, true>(U, ring, psb, rsb, A.hw, A.ny, cz, z * plane + U.col0, rk, vv,
                                                         shr, shi, cf, qs, sa, B);
                     } else {
@@ -1677,7 +1958,8 @@ bool cluster_plan(int nx, int ny, int smem_optin, bool two_per_sm, int &ncl, int
     for (int c = 2; c <= 8; ++c) {
         const int b = (hh + c - 1) / c;
         if (b < 3 || (long long)(c - 1) * b >= hh) continue;
-        const size_t bytes = (size_t)kRingPlanes * (2 + (size_t)2 * b * rs) * sizeof(float2) + fa.sharedSizeBytes;
+        const size_t bytes = ((size_t)kRingPlanes * (2 + (size_t)2 * b * rs) + 2 * (2 + (size_t)2 * kRadius * rs)) *
+                                 sizeof(float2) + fa.sharedSizeBytes;
         if ((long long)hw * b <= kRingMaxThreads && bytes <= limit) {
             ncl = c;
             bp = b;
@@ -2509,9 +2791,9 @@ struct Carver {
     }
 };
 
-size_t slot_storage_bytes(bool mixed, long long nd, int S) {
+size_t slot_storage_bytes(bool mixed, long long nd, int S, bool precond) {
     const size_t n = (size_t)nd * S;
-    return 16 * n + 16 * n + (mixed ? 5 * 8 * n : 4 * 16 * n) + 8 * 256;
+    return 16 * n + 16 * n + (mixed ? 5 * 8 * n : 4 * 16 * n) + (precond ? 2 * (mixed ? 8 : 16) * n : 0) + 8 * 256;
 }
 
 int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
@@ -2523,8 +2805,10 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const int nblk = (int)cdiv(nd, kChunk);
     const size_t n = (size_t)nd * S;
 
-    // slot storage: x64, b, then the inner vectors x, r, p, q (FP32 complex, or FP64 sharing x64)
-    Carver cv{(char *)c.cocg_state.ensure(slot_storage_bytes(mixed, nd, S))};
+    // slot storage: x64, b, then the inner vectors x, r, p, q (FP32 complex, or FP64 sharing x64),
+    // and with the preconditioner z = M r and the transforms' work vector
+    const bool precond = c.opt.precondition != 0;
+    Carver cv{(char *)c.cocg_state.ensure(slot_storage_bytes(mixed, nd, S, precond))};
     double2 *x64 = cv.take<double2>(n);
     double2 *b = cv.take<double2>(n);      // right-hand side; the mixed form's FP64 residual r64
     void *xin, *r, *p, *q;           // p: two direction buffers, pstride elements apart
@@ -2538,6 +2822,11 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         r = cv.take<double2>(n);
         p = cv.take<double2>(2 * n);
         q = cv.take<double2>(n);
+    }
+    void *zv = nullptr, *wv = nullptr;
+    if (precond) {
+        zv = mixed ? (void *)cv.take<float2>(n) : (void *)cv.take<double2>(n);
+        wv = mixed ? (void *)cv.take<float2>(n) : (void *)cv.take<double2>(n);
     }
     const long long pstride = (long long)n;
     int dev_sms = 0, smem_optin = 0;
@@ -2558,12 +2847,13 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     const RingFn ring1_fn = per ? k_cocg_ring<true, true> : even_nx ? k_cocg_ring<true, false> : k_cocg_ring<false, false>;
     const bool ring1 = (!per || even_nx) && ring_fits(c.nx, c.ny, ring1_fn, smem_optin);
     int ncl = 1, band_pairs = 0;
-    const bool clus = mixed && !per && !ws && (want == 0 || want >= 4) &&
-                      ((want == 6 && cluster_plan(c.nx, c.ny, smem_optin, true, ncl, band_pairs)) ||
+    const bool clus = mixed && !per && !ws && !precond && (want == 0 || want >= 4) &&
+                      ((want == 6 && (cluster_plan(c.nx, c.ny, smem_optin, true, ncl, band_pairs) ||
+                                      cluster_plan(c.nx, c.ny, smem_optin, false, ncl, band_pairs))) ||
                        (!ring1 && cluster_plan(c.nx, c.ny, smem_optin, false, ncl, band_pairs)));
     const RingFn ring_fn = ws ? (even_nx ? k_cocg_ring_ws<true> : k_cocg_ring_ws<false>)
                               : clus ? (even_nx ? k_cocg_ring_cl<true> : k_cocg_ring_cl<false>) : ring1_fn;
-    const bool use_ring = mixed && (want == 0 || want >= 4) && (ws || clus || ring1);
+    const bool use_ring = mixed && !precond && (want == 0 || want >= 4) && (ws || clus || ring1);
     const int variant = (want >= 1 && want <= 3 && !(per && want == 3)) ? want - 1 : 0;
     const PaShape shape = mixed ? kPaShapes32[variant] : kPaShape64;
     Tiles tl = pick_tiles(c.nx, c.ny, shape.max_threads, shape.pairs != 0);
@@ -2574,8 +2864,10 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         tl.zlen = c.nz;
     }
     const int ntiles = tl.ntx * tl.nty * tl.nzc;
-    double *partA = (double *)c.cocg_partials.ensure(sizeof(double) * (size_t)S * (2 * ntiles + 3 * nblk));
+    double *partA =
+        (double *)c.cocg_partials.ensure(sizeof(double) * (size_t)S * (2 * ntiles + 3 * nblk + 3 * c.nz));
     double *partB = partA + (size_t)S * ntiles * 2;
+    double *partZ = partB + (size_t)S * nblk * 3;
     Slot *slots = (Slot *)c.sys_state.ensure(sizeof(Slot) * S);
     // ints: head, count, cnt[4], list[4][S], then per system: n, j, iters, status, refines,
     // near-breakdowns; then the finished-slot count and list [S].  The split kernels use lists 0
@@ -2620,6 +2912,8 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
     // mixed form with P_c applied to the right-hand sides: the refinement works in the
     // unoccupied space.  The FP32 projections leave occupied components of ~1e-9 of the
     // solution's norm; below that tolerance the finished solution is also projected in FP64.
+    P.precond = precond ? 1 : 0;
+    P.partZ = partZ;
     P.cproject = mixed && sp.Tc != nullptr;
     P.project = c.opt.project_solution != 0 || sp.grad != nullptr || (P.cproject && c.opt.tol < 1e-9);
     P.proj_re_only = sp.drho != nullptr && sp.grad == nullptr;
@@ -2705,6 +2999,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         ra.ps = clus ? 2 + 2 * band_pairs * ra.rs : 2 + c.ny * ra.rs;
         ra.bp = band_pairs;
         ring_smem = (size_t)kRingPlanes * ra.ps * sizeof(float2);
+        if (clus) ring_smem += 2 * (2 + (size_t)2 * kRadius * ra.rs) * sizeof(float2);   // the halo buffers
         {
             const int units = hw * (clus ? band_pairs : (c.ny + 1) / 2);
             ring_threads = (unsigned)((units + 31) / 32 * 32);
@@ -2734,6 +3029,70 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
             ring_grid = (unsigned)std::max<long long>(1, std::min<long long>(S, (long long)dev_sms * std::max(1, per_sm)));
         }
     }
+
+    // the Laplacian preconditioner: z = M r in three passes (see k_pc_xy, k_pc_z)
+    PcArgs<float> pc32{};
+    PcArgs<double> pc64{};
+    size_t pcxy_smem = 0, pcz_smem = 0;
+    unsigned pcxy_grid = 1, pcz_grid = 1;
+    if (precond) {
+        auto fill = [&](auto &a, auto Qs, auto mus) {
+            a.slots = slots;
+            a.S = S;
+            a.nx = c.nx;
+            a.ny = c.ny;
+            a.nz = c.nz;
+            a.nd = nd;
+            a.Qx = Qs[0];
+            a.Qy = Qs[1];
+            a.Qz = Qs[2];
+            a.mux = mus[0];
+            a.muy = mus[1];
+            a.muz = mus[2];
+            a.vbar = c.vbar;
+            a.partZ = partZ;
+        };
+        const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+        pcxy_smem = mixed ? pc_xy_bytes<float>(c.nx, c.ny) : pc_xy_bytes<double>(c.nx, c.ny);
+        pcz_smem = pc_mat_bytes((size_t)c.nz * c.nz, tsz) + 2 * tsz * (size_t)c.nz * 33;
+        if (pcxy_smem > (size_t)smem_optin || pcz_smem > (size_t)smem_optin || c.nz > 8 * 12 ||
+            (long long)((c.nx + 3) / 4) * ((c.ny + 1) / 2) > (long long)kPcTiles * kPcThreads)
+            fail(RPA_ERR_INVALID, "precondition: a %d x %d plane or %d planes exceed the preconditioner's limits",
+                 c.nx, c.ny, c.nz);
+        if (mixed) {
+            fill(pc32, c.Qf, c.muf);
+            allow_dynamic_smem((const void *)k_pc_xy<float, true>, pcxy_smem);
+            allow_dynamic_smem((const void *)k_pc_xy<float, false>, pcxy_smem);
+            allow_dynamic_smem((const void *)k_pc_z<float>, pcz_smem);
+        } else {
+            const double *Qd[3] = {c.Q[0], c.Q[1], c.Q[2]};
+            const double *md[3] = {c.mu[0], c.mu[1], c.mu[2]};
+            fill(pc64, Qd, md);
+            allow_dynamic_smem((const void *)k_pc_xy<double, true>, pcxy_smem);
+            allow_dynamic_smem((const void *)k_pc_xy<double, false>, pcxy_smem);
+            allow_dynamic_smem((const void *)k_pc_z<double>, pcz_smem);
+        }
+        const int per_sm_xy = std::max<int>(1, (int)(smem_optin / std::max<size_t>(pcxy_smem, 1)));
+        pcxy_grid = (unsigned)std::max<long long>(
+            1, std::min<long long>((long long)S * c.nz, (long long)dev_sms * std::min(per_sm_xy, 4)));
+        pcz_grid = (unsigned)std::max<long long>(
+            1, std::min<long long>((long long)S * cdiv((long long)c.nx * c.ny, 32), (long long)dev_sms * 4));
+    }
+    auto precondition = [&](cudaStream_t ss) {   // z = M r for the slots in their inner solve
+        if (mixed) {
+            k_pc_xy<float, true><<<pcxy_grid, kPcThreads, pcxy_smem, ss>>>(pc32, (const float2 *)r, (float2 *)wv,
+                                                                           nullptr);
+            k_pc_z<float><<<pcz_grid, kPcThreads, pcz_smem, ss>>>(pc32, (float2 *)wv);
+            k_pc_xy<float, false><<<pcxy_grid, kPcThreads, pcxy_smem, ss>>>(pc32, (const float2 *)wv, (float2 *)zv,
+                                                                            (const float2 *)r);
+        } else {
+            k_pc_xy<double, true><<<pcxy_grid, kPcThreads, pcxy_smem, ss>>>(pc64, (const double2 *)r,
+                                                                            (double2 *)wv, nullptr);
+            k_pc_z<double><<<pcz_grid, kPcThreads, pcz_smem, ss>>>(pc64, (double2 *)wv);
+            k_pc_xy<double, false><<<pcxy_grid, kPcThreads, pcxy_smem, ss>>>(pc64, (const double2 *)wv,
+                                                                             (double2 *)zv, (const double2 *)r);
+        }
+    };
 
     // profiling: events around every launch of the item kernels of the iteration
     const bool prof = c.opt.profile != 0;
@@ -2849,10 +3208,12 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         for (int e = 0; e < kEpoch; ++e) {
             const int par = e & 1;
             const int t0 = 2 * e * 2;
+            if (precond) precondition(ss);
             k_beta<<<wgrid, kThreads, 0, ss>>>(P, par);
+            // the direction update takes z = M r in place of r when preconditioned
             if (mixed) {
                 rec(t0 + 0);
-                pa32<<<pa_grid, pa_threads, pa_smem, ss>>>(ia_pa[par], tl, (const float2 *)r, (float2 *)p,
+                pa32<<<pa_grid, pa_threads, pa_smem, ss>>>(ia_pa[par], tl, (const float2 *)(precond ? zv : r), (float2 *)p,
                                                                       pstride, (float2 *)q, c.vloc32, cf32);
                 rec(t0 + 1);
                 k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
@@ -2862,7 +3223,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
                 rec(t0 + 3);
             } else {
                 rec(t0 + 0);
-                pa64<<<pa_grid, pa_threads, pa_smem, ss>>>(ia_pa[par], tl, (const double2 *)r, (double2 *)p,
+                pa64<<<pa_grid, pa_threads, pa_smem, ss>>>(ia_pa[par], tl, (const double2 *)(precond ? zv : r), (double2 *)p,
                                                                         pstride, (double2 *)q, c.vloc64, cf64);
                 rec(t0 + 1);
                 k_alpha<<<wgrid, kThreads, 0, ss>>>(P, par);
@@ -2876,7 +3237,7 @@ int run_queue(Ctx &c, SolveSpec &sp, cudaStream_t st, std::vector<int> *iters_ou
         maintenance(ss);
     };
     const int per_maint = (mixed ? 8 : 5) + (P.project ? 2 : 0) + (P.cproject ? 5 : 0);
-    const int per_epoch = (use_ring ? 2 : 4 * kEpoch) + per_maint;
+    const int per_epoch = (use_ring ? 2 : (precond ? 7 : 4) * kEpoch) + per_maint;
 
     // device-driven queue: CUDA graphs, no profiling, no per-system outputs wanted
     const bool device_loop = use_graph && !prof && !iters_out && !status_out;
@@ -3035,6 +3396,7 @@ void check_orbitals(const Ctx &c, const int *orb, int nsys) {
 }  // namespace
 
 bool fused_kernel_applies(const Ctx &c, bool warp_specialised, bool cluster) {
+    if (c.opt.precondition) return false;   // the preconditioned COCG runs the split kernels
     int smem_optin = 0;
     RPA_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     const bool even = (c.nx % 2) == 0;

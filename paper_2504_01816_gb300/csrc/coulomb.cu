@@ -159,6 +159,14 @@ void coulomb_setup(Ctx &c) {
         }
         RPA_CUDA(cudaMalloc(&c.Q[a], sizeof(double) * n * n));
         RPA_CUDA(cudaMemcpy(c.Q[a], Q.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
+        // the same factors for the Laplacian preconditioner of COCG, in FP64 and FP32
+        std::vector<float> qf(Q.begin(), Q.end()), mf(mu[a].begin(), mu[a].end());
+        RPA_CUDA(cudaMalloc(&c.mu[a], sizeof(double) * n));
+        RPA_CUDA(cudaMemcpy(c.mu[a], mu[a].data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        RPA_CUDA(cudaMalloc(&c.Qf[a], sizeof(float) * n * n));
+        RPA_CUDA(cudaMemcpy(c.Qf[a], qf.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice));
+        RPA_CUDA(cudaMalloc(&c.muf[a], sizeof(float) * n));
+        RPA_CUDA(cudaMemcpy(c.muf[a], mf.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
     }
     std::vector<double> lam((size_t)c.nd);
     for (int k = 0; k < c.nz; ++k)

@@ -106,6 +106,12 @@ struct Ctx {
     // summed eigenvalue grid lam = mu_x + mu_y + mu_z (nd).
     double *Q[3] = {nullptr, nullptr, nullptr};
     double *lam = nullptr;
+    // Laplacian preconditioner of COCG: the 1D eigenvalues mu_a (FP64), FP32 copies of Q_a and mu_a,
+    // and the mean of V_loc
+    double *mu[3] = {nullptr, nullptr, nullptr};
+    float *Qf[3] = {nullptr, nullptr, nullptr};
+    float *muf[3] = {nullptr, nullptr, nullptr};
+    double vbar = 0.0;
 
     // workspaces
     DevBuf cocg_state;            // complex vectors of the systems in flight

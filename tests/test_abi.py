@@ -50,11 +50,11 @@ def test_struct_layouts_match_header(rpa, tmp_path):
 #include <stddef.h>
 #include "rpa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
          offsetof(rpa_options, independent_frequencies), offsetof(rpa_stats, ms_coulomb),
          offsetof(rpa_stats, worst_status), offsetof(rpa_stats, prof_bytes), offsetof(rpa_stats, launches),
          offsetof(rpa_stats, near_breakdowns), offsetof(rpa_options, sq_order), offsetof(rpa_options, contractions),
-         offsetof(rpa_options, periodic));
+         offsetof(rpa_options, periodic), offsetof(rpa_options, precondition));
   return 0;
 }
 """)
@@ -64,7 +64,8 @@ int main(void) {
     O, S = rpa.rpa.rpa_options, rpa.rpa.rpa_stats
     assert got == [ctypes.sizeof(O), ctypes.sizeof(S), O.independent_frequencies.offset, S.ms_coulomb.offset,
                    S.worst_status.offset, S.prof_bytes.offset, S.launches.offset,
-                   S.near_breakdowns.offset, O.sq_order.offset, O.contractions.offset, O.periodic.offset]
+                   S.near_breakdowns.offset, O.sq_order.offset, O.contractions.offset, O.periodic.offset,
+                   O.precondition.offset]
 
 
 def test_setup_rejects_bad_arguments_without_a_gpu(rpa):
@@ -86,7 +87,7 @@ def test_setup_rejects_bad_arguments_without_a_gpu(rpa):
     st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)
     assert st == rpa.RPA_ERR_INVALID and b"n_omega" in lib.rpa_last_error()
     for field, value in (("sq_order", 33), ("stencil_shape", 7), ("z_chunks", -1), ("contractions", 4),
-                         ("periodic", 2)):
+                         ("periodic", 2), ("precondition", 3)):
         lib.rpa_default_options(ctypes.byref(bad))
         setattr(bad, field, value)
         st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)
