@@ -208,12 +208,13 @@ __device__ __forceinline__ void warp_slot_sum(const double *part, int nblk, doub
         for (int o = 16; o > 0; o >>= 1) out[c] += __shfl_xor_sync(0xffffffffu, out[c], o);
 }
 
+// Grid coordinates of a point index (grid functions have < 2^31 points: 32-bit divisions).
 __device__ __forceinline__ void coords(long long idx, const Grid3 &g, int &i, int &j, int &k) {
-    const long long pl = (long long)g.nx * g.ny;
-    k = (int)(idx / pl);
-    const long long rem = idx - (long long)k * pl;
-    j = (int)(rem / g.nx);
-    i = (int)(rem - (long long)j * g.nx);
+    const int id = (int)idx, pl = g.nx * g.ny;
+    k = id / pl;
+    const int rem = id - k * pl;
+    j = rem / g.nx;
+    i = rem - j * g.nx;
 }
 
 // ---------------------------------------------------------------------------------------------

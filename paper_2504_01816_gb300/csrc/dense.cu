@@ -155,10 +155,12 @@ __global__ void k_symmetrize(double *C, int n) {
 }
 
 // Householder reduction of the symmetric matrix A (n x n, row-major, destroyed) to tridiagonal
-// form, then every eigenvalue by bisection on Sturm counts (one thread per eigenvalue), then
-// the energy sum in ascending order.  One block.  work: 3n doubles.
+// form, written to work[0..2n) (diagonal, off-diagonal) for k_sturm_bisect; k_eig_energy then sums
+// the energy in ascending order.  One block.  work: 3n doubles.
 // With use_smem the matrix and the work vectors are copied to shared memory first (n^2 + 3n
-// doubles); A is then left unchanged.
+// doubles); A is then left unchanged.  (The eigenvalues by bisection in this block, one thread
+// each, took ~2.3 ms for n = 64 on the FP64 pipe of one SM; one warp per eigenvalue over n SMs, by
+// multisection, takes a few tens of microseconds.)
 __global__ void __launch_bounds__(kEigThreads) k_sym_eigvals(double *__restrict__ Ag, int n, double *__restrict__ lam,
                                                              double *__restrict__ workg, double weight,
                                                              double *__restrict__ e_out, int use_smem) {
@@ -175,7 +177,6 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eigvals(double *__restrict_
     }
     double *v = work;           // Householder vector (length n, entries k+1..n-1 used)
     double *p = work + n;       // A v
-    double *d = work + 2 * n;   // diagonal, then off-diagonal in A's subdiagonal
     auto block_sum = [&](double x) -> double {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if ((tid & 31) == 0) red[tid >> 5] = x;
@@ -231,46 +232,65 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eigvals(double *__restrict_
         }
         __syncthreads();
     }
+    // the tridiagonal matrix to global memory for the bisection kernel: diagonal, then off-diagonal
     for (int i = tid; i < n; i += nt) {
-        d[i] = A[(long long)i * n + i];
-        v[i] = (i + 1 < n) ? A[(long long)(i + 1) * n + i] : 0.0;   // off-diagonal e_i
+        workg[i] = A[(long long)i * n + i];
+        workg[n + i] = (i + 1 < n) ? A[(long long)(i + 1) * n + i] : 0.0;
     }
-    __syncthreads();
+}
+
+// Eigenvalue t = blockIdx.x of the symmetric tridiagonal matrix (diagonal tri[0..n), off-diagonal
+// tri[n..2n)), ascending, by multisection on Sturm counts: the warp's 32 lanes count the eigenvalues
+// below 32 points splitting the interval into 33 parts, the interval shrinks to the part where the
+// count passes t (5 bits per step), until it reaches machine precision.  One warp per eigenvalue,
+// so the eigenvalues run on different SMs.
+__global__ void __launch_bounds__(32) k_sturm_bisect(const double *__restrict__ tri, int n, double *__restrict__ lam) {
+    const int t = blockIdx.x, lane = threadIdx.x;
+    const double *d = tri, *e = tri + n;
     // Gershgorin bounds
-    if (tid == 0) {
-        double lo = 1e300, hi = -1e300;
-        for (int i = 0; i < n; ++i) {
-            const double r = (i > 0 ? fabs(v[i - 1]) : 0.0) + (i + 1 < n ? fabs(v[i]) : 0.0);
-            lo = fmin(lo, d[i] - r);
-            hi = fmax(hi, d[i] + r);
-        }
-        const double pad = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
-        sh_scalar[0] = lo - pad;
-        sh_scalar[1] = hi + pad;
+    double lo = 1e300, hi = -1e300;
+    for (int i = lane; i < n; i += 32) {
+        const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
     }
-    __syncthreads();
-    const double glo = sh_scalar[0], ghi = sh_scalar[1];
-    for (int t = tid; t < n; t += nt) {
-        double lo = glo, hi = ghi;
-        for (int it = 0; it < 200; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            // number of eigenvalues < mid
-            int cnt = 0;
-            double q = d[0] - mid;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double pad = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+    lo -= pad;
+    hi += pad;
+    for (int it = 0; it < 40; ++it) {
+        const double w = (hi - lo) / 33.0;
+        if (!(lo + w > lo) || !(hi - w < hi)) break;   // the interval is at machine precision
+        const double x = lane == 31 ? hi - w : lo + (lane + 1) * w;
+        int cnt = 0;                                     // eigenvalues below x
+        double q = d[0] - x;
+        if (q < 0) ++cnt;
+        for (int i = 1; i < n; ++i) {
+            if (q == 0.0) q = 1e-300;
+            q = d[i] - x - e[i - 1] * e[i - 1] / q;
             if (q < 0) ++cnt;
-            for (int i = 1; i < n; ++i) {
-                if (q == 0.0) q = 1e-300;
-                q = d[i] - mid - v[i - 1] * v[i - 1] / q;
-                if (q < 0) ++cnt;
-            }
-            if (cnt > t) hi = mid;
-            else lo = mid;
         }
-        lam[t] = 0.5 * (lo + hi);
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > t);   // points past eigenvalue t
+        const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
+        if (above == 0u) {
+            lo = __shfl_sync(0xffffffffu, x, 31);
+        } else {
+            const int f = __ffs(above) - 1;
+            const double xf = __shfl_sync(0xffffffffu, x, f);
+            const double xl = __shfl_sync(0xffffffffu, xprev, f);
+            if (f > 0) lo = xl;
+            hi = xf;
+        }
     }
-    __syncthreads();
-    if (tid == 0) {
+    if (lane == 0) lam[t] = 0.5 * (lo + hi);
+}
+
+// E = weight * sum_i [log(1 - lambda_i) + lambda_i], in index order (one thread).
+__global__ void k_eig_energy(const double *__restrict__ lam, int n, double weight, double *__restrict__ e_out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
         for (int i = 0; i < n; ++i) s += log1p(-lam[i]) + lam[i];
         *e_out = weight * s;
@@ -587,8 +607,10 @@ void sym_eigvals(double *C, int n, double *lam, double *work, double weight, dou
     const bool use_smem = sh <= 200 * 1024;
     if (use_smem) allow_dynamic_smem((const void *)k_sym_eigvals, sh);
     k_sym_eigvals<<<1, kEigThreads, use_smem ? sh : 0, s>>>(C, n, lam, work, weight, e_out, use_smem ? 1 : 0);
+    k_sturm_bisect<<<n, 32, 0, s>>>(work, n, lam);
+    k_eig_energy<<<1, 32, 0, s>>>(lam, n, weight, e_out);
     RPA_LAUNCH("sym_eigvals");
-    count_launches(1);
+    count_launches(3);
 }
 
 }  // namespace rpa
