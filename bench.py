@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mixed40")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="rpa_options.batch_systems: systems in flight (0: as many as fit the slot budget)")
     ap.add_argument("--precondition", type=int, default=0,
                     help="rpa_options.precondition: 1 = Laplacian-preconditioned COCG")
     ap.add_argument("--stencil-shape", type=int, default=-1,
@@ -306,6 +308,7 @@ def run_ours(args):
     opts.profile = 0                           # the timed steps run without per-launch events
     opts.periodic = int(getattr(s, "periodic", False))   # the system's boundary conditions
     opts.precondition = args.precondition
+    opts.batch_systems = args.slots
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = rpa.Context.from_system(s, opts)
