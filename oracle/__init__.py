@@ -22,6 +22,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   laplacian_preconditioner  dense inverse of -1/2 L_h + shift
   pcocg                 dense complex solve; with a multiple of the identity as M it is COCG
                         (same iterates as cocg); fewer iterations than cocg at small omega
+  block_cocg            one column is cocg (same iterates); dense complex solve; finite
+                        termination in ceil(N / s) steps on an N-dimensional operator; block
+                        orthogonality of the residuals and block A-conjugacy of the directions
+                        (tests/test_oracle_pins_block.py)
   gauss_sq_trace        exactness for polynomials of degree <= 2 N_o - 1 (Gauss rule); order 1
                         is sum f(C_rr); order >= the dimension is Tr f(C) by dense eigenvalues
 """
@@ -29,4 +33,4 @@ from .rpa_oracle import *  # noqa: F401,F403
 from .rpa_oracle import (Oracle, Grid, Coulomb, SolveStats, EcResult, fd_weights, apply_h, cocg,  # noqa: F401
                          frequency_quadrature, g_rpa, orthonormalize_cholesky, rpa_ec, num_threads,
                          set_threads, second_difference_1d, NotSPD, rpa_ec_gradient, gauss_sq_trace,
-                         laplacian_preconditioner, pcocg)
+                         laplacian_preconditioner, pcocg, block_cocg, block_cocg_generic)

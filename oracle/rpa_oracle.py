@@ -279,6 +279,58 @@ def pcocg(grid: Grid, vloc: np.ndarray, sigma: complex, b: np.ndarray, tol: floa
     return x, its, st
 
 
+def block_cocg_generic(apply_a, B: np.ndarray, tol: float, maxit: int, history: Optional[list] = None):
+    """Block COCG for A X = B, every row of B a right-hand side of the same complex-symmetric A
+    (the block variant of COCG named in Section "Implementation" as the paper's preliminary
+    alternative).  Block conjugate gradients (O'Leary's block CG) with the unconjugated form
+    x^T y in place of the inner product, as COCG is to CG; with the s right-hand sides as the
+    columns of B:
+        X = 0, R = B, P = R, rho = R^T R                           (s x s)
+        repeat:  Q = A P, alpha = (P^T Q)^-1 rho, X += P alpha, R -= Q alpha,
+                 rho' = R^T R, beta = rho^-1 rho', P = R + P beta, rho = rho'
+    stopping when every column has ||r_j||_2 <= tol ||b_j||_2 (checked before each iteration).
+    apply_a maps an (s, N) block of rows to A applied to each row.  Returns (X as rows,
+    iterations, status): status 5 where P^T Q or rho is singular to working precision.
+    history, if a list, receives (R, P, Q) of every iteration as columns (the pins check the
+    block orthogonality of the residuals and the block A-conjugacy of the directions)."""
+    Bc = np.asarray(B, dtype=np.complex128).T.copy()        # (N, s)
+    X = np.zeros_like(Bc)
+    R = Bc.copy()
+    P = R.copy()
+    rho = R.T @ R
+    bn = np.linalg.norm(Bc, axis=0)
+    k, status = 0, OK
+    while True:
+        if np.all(np.linalg.norm(R, axis=0) <= tol * bn):
+            break
+        if k >= maxit:
+            status = NOT_CONVERGED
+            break
+        Q = apply_a(P.T).T
+        if history is not None:
+            history.append((R.copy(), P.copy(), Q.copy()))
+        G = P.T @ Q
+        if not np.all(np.isfinite(G)) or np.linalg.cond(G) > 1e14 or np.linalg.cond(rho) > 1e14:
+            status = BREAKDOWN
+            break
+        alpha = np.linalg.solve(G, rho)
+        X += P @ alpha
+        R -= Q @ alpha
+        rho_new = R.T @ R
+        beta = np.linalg.solve(rho, rho_new)
+        P = R + P @ beta
+        rho = rho_new
+        k += 1
+    return X.T.copy(), k, status
+
+
+def block_cocg(grid: Grid, vloc: np.ndarray, sigma: complex, B: np.ndarray, tol: float, maxit: int):
+    """Block COCG (block_cocg_generic) for (H + sigma) X = B, the rows of B sharing one shift."""
+    def apply_a(P):
+        return np.array([apply_h(grid, vloc, p, sigma) for p in P])
+    return block_cocg_generic(apply_a, np.atleast_2d(B), tol, maxit)
+
+
 # ------------------------------------------------------------------------------------
 # chi0 by density functional perturbation theory (Eqs. 7-9, Algorithm 1 inner loop)
 # ------------------------------------------------------------------------------------
@@ -326,7 +378,7 @@ class Oracle:
     def chi0(self, dv: np.ndarray, omega: float, tol: float, maxit: int = 100000, sign: int = +1,
              stats: Optional[SolveStats] = None, max_chunk_bytes: float = 2.5e8,
              galerkin: bool = False, return_x: bool = False, project_solution: bool = False,
-             precondition: bool = False):
+             precondition: bool = False, block: int = 0):
         """drho = chi0(i omega) dV for every row of dv (Eqs. 7-9).
 
         For each occupied n and each dV: solve (H - eps_n + sign*i*omega) x = b by COCG, then
@@ -335,7 +387,9 @@ class Oracle:
         project_solution=True also removes the occupied components of x (x <- P_c x): the same
         operator when the orbitals are exact eigenvectors of H, and the first-order-consistent
         response of the fixed occupied space when V_loc moves away from them.  precondition=True
-        solves by the Laplacian-preconditioned COCG (pcocg) instead.
+        solves by the Laplacian-preconditioned COCG (pcocg) instead.  block=s > 0 solves the
+        right-hand sides of each orbital s at a time by block COCG (block_cocg; every column of a
+        block reports the block's iteration count).
         """
         g = self.grid
         dv = np.atleast_2d(np.asarray(dv, dtype=np.float64))
@@ -344,6 +398,8 @@ class Oracle:
         xs = [] if return_x else None
         per_row = 16.0 * 2 * g.n_d
         chunk = max(1, int(max_chunk_bytes // per_row))
+        if block > 0:
+            chunk = block
         for n in range(self.n_s):
             sigma = -self.eps[n] + sign * 1j * omega
             for j0 in range(0, k, chunk):
@@ -352,7 +408,11 @@ class Oracle:
                     x = self._galerkin_solve(n, blk, sigma, tol, maxit, stats)
                 else:
                     b = self.sternheimer_rhs(n, blk).astype(np.complex128)
-                    if precondition:
+                    if block > 0:
+                        x, it1, st1 = block_cocg(g, self.vloc, sigma, b, tol, maxit)
+                        it = np.full(len(blk), it1, dtype=np.int32)
+                        st = np.full(len(blk), st1, dtype=np.int32)
+                    elif precondition:
                         m = laplacian_preconditioner(self.coulomb, float(np.mean(self.vloc)) + sigma)
                         x, it, st = pcocg(g, self.vloc, sigma, b, tol, maxit, m)
                     else:
