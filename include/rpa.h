@@ -72,7 +72,8 @@ typedef struct {
     int max_subspace_iters;    /* subspace iteration limit per frequency */
     int fixed_subspace_iters;  /* > 0: run exactly this many iterations per frequency */
     int n_atoms;               /* divides eps_c and the reported per-atom energy */
-    int batch_systems;         /* Sternheimer systems in flight at once (0 = automatic) */
+    int batch_systems;         /* Sternheimer systems in flight at once (0 = automatic; with
+                                  block_cocg rounded down to whole groups, at least one) */
     int profile;               /* != 0: time every launch of the COCG kernels with CUDA events and
                                   count the grid points they process (filled into rpa_stats.prof_*) */
     int project_solution;      /* != 0: also remove the occupied components of every Sternheimer
@@ -144,6 +145,18 @@ typedef struct {
                                   complex copies and the x and y factors in one block's shared
                                   memory (FP32: planes up to ~80 x 80; FP64: ~64 x 64) and
                                   nz <= 96.  0 (default): plain COCG. */
+    int block_cocg;            /* s in 1..16: the chi0 applications (rpa_apply_nuchi0, rpa_ec) and
+                                  rpa_sternheimer_solve take the systems of one orbital s at a time
+                                  (consecutive systems with the same orbital for the latter) and
+                                  solve each group by block COCG, the paper's block variant of COCG
+                                  (Section "Implementation"): X += P alpha, R -= Q alpha, P = R +
+                                  P beta with s x s matrices alpha = (P^T A P)^-1 R^T R and beta =
+                                  (R^T R)^-1 R'^T R' (unconjugated products), to the same per-system
+                                  stopping rule, inside the same FP64 refinement for the mixed form.
+                                  The block iterations restart from the true residual where an s x s
+                                  matrix turns singular to working precision, and leave out columns
+                                  already converged.  Not with precondition or project_solution;
+                                  rpa_ec_gradient's adjoint solves stay single.  0 (default): off. */
 } rpa_options;
 
 #define RPA_PROF_SLOTS 8

@@ -167,6 +167,9 @@ void validate_options(const rpa_options &o) {
     if (o.contractions < 0 || o.contractions > 3) fail(RPA_ERR_INVALID, "contractions must be in [0, 3]");
     if (o.periodic != 0 && o.periodic != 1) fail(RPA_ERR_INVALID, "periodic must be 0 or 1");
     if (o.precondition != 0 && o.precondition != 1) fail(RPA_ERR_INVALID, "precondition must be 0 or 1");
+    if (o.block_cocg < 0 || o.block_cocg > kMaxBlock) fail(RPA_ERR_INVALID, "block_cocg must be in [0, %d]", kMaxBlock);
+    if (o.block_cocg > 0 && (o.precondition || o.project_solution))
+        fail(RPA_ERR_INVALID, "block_cocg runs without precondition and project_solution");
     if (o.omega_count < 0 || o.omega_first < 0 || (o.omega_count > 0 && o.omega_first + o.omega_count > o.n_omega) ||
         (o.omega_count == 0 && o.omega_first != 0))
         fail(RPA_ERR_INVALID, "omega_first/omega_count must select a range of the n_omega frequencies");
@@ -329,6 +332,7 @@ void rpa_default_options(rpa_options *o) {
     o->omega_count = 0;
     o->periodic = 0;
     o->precondition = 0;
+    o->block_cocg = 0;
 }
 
 const char *rpa_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,944 @@
+// Block COCG for the Sternheimer systems that share an orbital: the block variant of COCG that the
+// paper names beside Laplacian preconditioning as its preliminary alternative (arXiv 2504.01816,
+// Section "Implementation").  The systems (H - eps_n + i omega) x = b of Eq. 9 for the columns of
+// one orbital n share their operator, so s of them (a group) are solved together.
+//
+// Block conjugate gradients with the unconjugated bilinear form x^T y (as COCG is to CG), with the
+// group's right-hand sides as the columns of B:
+//   X = 0, R = B, P = R, rho = R^T R                                    (s x s)
+//   repeat: Q = A P, alpha = (P^T Q)^-1 rho, X += P alpha, R -= Q alpha,
+//           rho' = R^T R, beta = rho^-1 rho', P = R + P beta, rho = rho'
+// until every column meets its stopping threshold.
+//
+// The inner solves sit in the same FP64 iterative refinement as the single-system queue: r64 =
+// b - A x64 in FP64, block COCG for A D = r64 (complex FP32 for the mixed form, FP64 for the plain
+// form) on the columns not yet converged, each scaled to unit norm, x64 += D, repeat until every
+// column has ||r64|| <= tol ||b||.  Where alpha or beta needs an s x s matrix that is singular to
+// working precision (the block form of COCG's breakdown: the residuals of the block have become
+// nearly dependent, as they do once the FP32 solves reach their rounding floor and every column's
+// residual is dominated by the same few directions) the inner solve ends, and the refinement
+// restarts it from the true residual with at most half as many columns, those with the largest
+// relative residuals; a group can so shrink to single-column COCG.  Converged columns are left out
+// of every inner solve, and max_refine bounds the inner solves each column takes part in.
+//
+// One inner iteration is seven launches over the groups in flight: the stencil, a Gram kernel
+// (P^T Q), a per-group kernel (alpha by Gaussian elimination with partial pivoting on the
+// equilibrated s x s system), the X/R update, a Gram kernel (R^T R and the column norms), a
+// per-group kernel (stopping test, beta) and the direction update.  The Gram partial sums are
+// written per tile and added in tile order, so results do not depend on scheduling.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace rpa {
+namespace {
+
+constexpr int kBT = 256;               // threads of the streaming kernels
+constexpr int kBChunk = 2048;          // grid points per norm work item (8 per thread)
+constexpr int kBCheckEvery = 8;        // inner iterations between the host's looks at the active count
+constexpr double kBBudget = 8.0e9;     // bytes of vectors of the groups in flight
+
+enum BPhase : int { kBDone = 0, kBInner = 1, kBInnerDone = 2, kBCheck = 3 };
+
+template <typename T> struct BCx;
+template <> struct BCx<float> { using t = float2; };
+template <> struct BCx<double> { using t = double2; };
+
+// grid points per Gram tile (two tiles of s rows in shared memory)
+template <typename T> struct BTile { static constexpr int v = 256; };
+template <> struct BTile<double> { static constexpr int v = 128; };
+
+// One group: the columns row0 .. row0 + ncol - 1 of orbital n (systems sys0 ..).
+struct BGroup {
+    int n, ncol, sys0, row0;
+    int phase, status, iters, refines, nearb, discard, nin, inner_iters;
+    int nonfinite;
+    int cap;                       // most columns an inner solve takes (halved at a near-breakdown)
+    double sre, sim;               // shift -eps_n + i omega
+    int refc[kMaxBlock];           // inner solves column c took part in
+    int itc[kMaxBlock];            // inner iterations of column c
+    int cmap[kMaxBlock];           // inner column -> column of the group
+    double bn[kMaxBlock];          // ||b_c||
+    double thr[kMaxBlock];         // stopping threshold of inner column ci (its residual starts at 1)
+    double scl[kMaxBlock];         // ||r64|| of inner column ci at the start of the inner solve
+};
+
+struct BArgs {
+    BGroup *g;
+    int ngroups, sb;               // groups in flight, columns per group in the vector storage
+    long long nd;
+    int nx, ny, nz, periodic;
+    int ntile;                     // Gram tiles per group
+    int nchunk;                    // norm work items per column
+    int mixed, maxit, max_refine;
+    double tol, inner_tol, piv_tol;
+    double a[kRadius + 1];         // stencil coefficients
+    double2 *gpart;                // [group][ntile][sb*sb + sb] Gram partial sums; norms in .x of the tail
+    double2 *rho;                  // [group][nin*nin]
+    void *coef;                    // [group][nin*nin] alpha, then beta (complex T)
+    double *npart;                 // [group*sb + c][nchunk][2] ||r64_c||^2, ||b_c||^2
+    int *count;
+};
+
+__device__ __forceinline__ int bwrap(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// (H + sigma) v at point idx of one grid function: (3 a_0 + V + sigma) v + sum_k a_k (the six
+// neighbours at distance k), zero outside the box or the periodic continuation.
+template <typename T, typename C>
+__device__ __forceinline__ C bstencil_at(const C *__restrict__ v, const T *__restrict__ V, int idx, int nx, int ny,
+                                         int nz, int per, const T (&a)[kRadius + 1], T sre, T sim) {
+    const int ix = idx % nx, t = idx / nx, iy = t % ny, iz = t / ny;
+    const int sxy = nx * ny;
+    const C c0 = v[idx];
+    const T d = (T)3 * a[0] + V[idx] + sre;
+    T re = d * c0.x - sim * c0.y, im = d * c0.y + sim * c0.x;
+#pragma unroll
+    for (int k = 1; k <= kRadius; ++k) {
+        T sr = 0, si = 0;
+        auto add = [&](int j) {
+            const C w = v[j];
+            sr += w.x;
+            si += w.y;
+        };
+        if (per) {
+            const int row = idx - ix, plane = idx - iy * nx, col = idx - iz * sxy;
+            add(row + bwrap(ix - k, nx));
+            add(row + bwrap(ix + k, nx));
+            add(plane + bwrap(iy - k, ny) * nx);
+            add(plane + bwrap(iy + k, ny) * nx);
+            add(col + bwrap(iz - k, nz) * sxy);
+            add(col + bwrap(iz + k, nz) * sxy);
+        } else {
+            if (ix - k >= 0) add(idx - k);
+            if (ix + k < nx) add(idx + k);
+            if (iy - k >= 0) add(idx - k * nx);
+            if (iy + k < ny) add(idx + k * nx);
+            if (iz - k >= 0) add(idx - k * sxy);
+            if (iz + k < nz) add(idx + k * sxy);
+        }
+        re += a[k] * sr;
+        im += a[k] * si;
+    }
+    C out;
+    out.x = re;
+    out.y = im;
+    return out;
+}
+
+// Sum two doubles over the block (256 threads); valid in thread 0.  Fixed order.
+__device__ __forceinline__ void bblock_sum2(double &a, double &b) {
+    __shared__ double sh[2][kBT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sh[0][warp] = a;
+        sh[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = 0.0;
+        for (int w = 0; w < kBT / 32; ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+    }
+}
+
+// b = sign * (base - sum_k Tc[sys][k] u_k), base = u_n (.) vt_row (pairs) or rhs_row; x64 = 0,
+// r64 = b.  Grid: (points / 256, groups * sb).
+__global__ void __launch_bounds__(kBT) k_bload(BArgs A, const double *__restrict__ psi, int ns,
+                                               const double *__restrict__ vt, const double *__restrict__ rhs,
+                                               const double *__restrict__ Tc, double sign, double *__restrict__ b,
+                                               double2 *__restrict__ x64, double2 *__restrict__ r64) {
+    const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (c >= G.ncol || idx >= A.nd) return;
+    const int row = G.row0 + c, sys = G.sys0 + c;
+    double base = vt ? psi[(long long)G.n * A.nd + idx] * vt[(long long)row * A.nd + idx]
+                     : rhs[(long long)row * A.nd + idx];
+    if (Tc)
+        for (int k = 0; k < ns; ++k) base -= Tc[(long long)sys * ns + k] * psi[(long long)k * A.nd + idx];
+    const double bv = sign * base;
+    const long long o = ((long long)gi * A.sb + c) * A.nd + idx;
+    b[o] = bv;
+    x64[o] = make_double2(0.0, 0.0);
+    r64[o] = make_double2(bv, 0.0);
+}
+
+// Partial sums of ||r64_c||^2 and ||b_c||^2 for the groups awaiting a check.
+// Grid: (nchunk, groups * sb).
+__global__ void __launch_bounds__(kBT) k_bnorm(BArgs A, const double *__restrict__ b,
+                                               const double2 *__restrict__ r64) {
+    const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    if (c >= G.ncol || (G.phase != kBInnerDone && G.phase != kBCheck)) return;
+    const long long o = ((long long)gi * A.sb + c) * A.nd;
+    double rr = 0.0, bb = 0.0;
+    for (int t = 0; t < kBChunk / kBT; ++t) {
+        const long long idx = (long long)blockIdx.x * kBChunk + t * kBT + threadIdx.x;
+        if (idx < A.nd) {
+            const double2 r = r64[o + idx];
+            const double bv = b[o + idx];
+            rr += r.x * r.x + r.y * r.y;
+            bb += bv * bv;
+        }
+    }
+    bblock_sum2(rr, bb);
+    if (threadIdx.x == 0) {
+        double *q = A.npart + ((long long)blockIdx.y * A.nchunk + blockIdx.x) * 2;
+        q[0] = rr;
+        q[1] = bb;
+    }
+}
+
+// Per group (one warp): the stopping test on the FP64 residual, then either the group is done or
+// its next inner solve is set up on at most cap of the columns not yet converged (those with the
+// largest relative residuals, ties by column; columns that have had max_refine inner solves are
+// not taken again).
+__global__ void k_bcheck(BArgs A) {
+    const int gi = blockIdx.x, c = threadIdx.x;
+    BGroup &G = A.g[gi];
+    const int ph = G.phase;
+    if (ph != kBInnerDone && ph != kBCheck) return;
+    bool unconv = false, bad = false, elig = false;
+    double rn = 0.0, bn = 0.0, key = -1.0;
+    if (c < G.ncol) {
+        const double *q = A.npart + ((long long)gi * A.sb + c) * A.nchunk * 2;
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = 0; k < A.nchunk; ++k) {
+            s0 += q[2 * k];
+            s1 += q[2 * k + 1];
+        }
+        rn = sqrt(s0);
+        if (ph == kBCheck) G.bn[c] = sqrt(s1);
+        bn = G.bn[c];
+        unconv = !(rn <= A.tol * bn);
+        bad = !isfinite(rn);
+        elig = unconv && G.refc[c] < A.max_refine;
+        if (elig) key = bad ? 0.0 : rn / bn;
+    }
+    int rank = 0;
+    for (int o = 0; o < 32; ++o) {
+        const double ko = __shfl_sync(0xffffffffu, key, o);
+        const int eo = __shfl_sync(0xffffffffu, (int)elig, o);
+        if (eo && (ko > key || (ko == key && o < c))) ++rank;
+    }
+    const bool take = elig && rank < G.cap;
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    const unsigned mu = __ballot_sync(0xffffffffu, unconv);
+    const unsigned mb = __ballot_sync(0xffffffffu, bad);
+    const int nin = __popc(m);
+    if (take) {
+        const int ci = __popc(m & ((1u << c) - 1u));
+        G.cmap[ci] = c;
+        G.scl[ci] = rn;
+        G.thr[ci] = A.mixed ? fmax(A.inner_tol, 0.3 * A.tol * bn / rn) : A.tol * bn / rn;
+        G.refc[c] += 1;
+    }
+    __syncwarp();
+    if (c == 0) {
+        if (mu == 0) {
+            G.phase = kBDone;
+            G.status = RPA_OK;
+        } else if (nin == 0) {
+            G.phase = kBDone;
+            G.status = (mb || G.nonfinite) ? RPA_ERR_BREAKDOWN : RPA_ERR_NOT_CONVERGED;
+        } else {
+            G.phase = kBInner;
+            G.nin = nin;
+            G.refines += 1;
+            G.inner_iters = 0;
+            G.discard = 0;
+            atomicAdd(A.count, 1);
+        }
+    }
+}
+
+// Inner solve start: R = r64 / ||r64|| on the inner columns, X = 0, P = R.
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_bstart(BArgs A, const double2 *__restrict__ r64,
+                                                typename BCx<T>::t *__restrict__ x, typename BCx<T>::t *__restrict__ r,
+                                                typename BCx<T>::t *__restrict__ p) {
+    using C = typename BCx<T>::t;
+    const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (G.phase != kBInner || ci >= G.nin || idx >= A.nd) return;
+    const double inv = 1.0 / G.scl[ci];
+    const double2 v = r64[((long long)gi * A.sb + G.cmap[ci]) * A.nd + idx];
+    const long long o = ((long long)gi * A.sb + ci) * A.nd + idx;
+    C rv, z;
+    rv.x = (T)(v.x * inv);
+    rv.y = (T)(v.y * inv);
+    z.x = (T)0;
+    z.y = (T)0;
+    x[o] = z;
+    r[o] = rv;
+    p[o] = rv;
+}
+
+// out = (H + sigma) in on the inner columns (T = the inner precision).
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_bstencil(BArgs A, const typename BCx<T>::t *__restrict__ in,
+                                                  typename BCx<T>::t *__restrict__ out, const T *__restrict__ V) {
+    const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (G.phase != kBInner || ci >= G.nin || idx >= A.nd) return;
+    T a[kRadius + 1];
+#pragma unroll
+    for (int k = 0; k <= kRadius; ++k) a[k] = (T)A.a[k];
+    const long long o = ((long long)gi * A.sb + ci) * A.nd;
+    out[o + idx] = bstencil_at<T>(in + o, V, (int)idx, A.nx, A.ny, A.nz, A.periodic, a, (T)G.sre, (T)G.sim);
+}
+
+// Gram partial sums of one tile: G_ij = sum_t X_i(t) Y_j(t) (unconjugated) over the tile's points,
+// and with norms != 0 also ||X_i||^2.  Thread (e, sub) of the block adds every nsub-th point for
+// entry e = (i, j); the nsub sums of an entry are added in order.  Grid: (ntile, groups).
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t *__restrict__ X,
+                                               const typename BCx<T>::t *__restrict__ Y, int norms) {
+    using C = typename BCx<T>::t;
+    constexpr int TP = BTile<T>::v;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    C *sx = reinterpret_cast<C *>(bsm);
+    C *sy = sx + (size_t)A.sb * (TP + 1);
+    __shared__ double2 red[kBT];
+    __shared__ double redn[kBT];
+    const int gi = blockIdx.y;
+    const BGroup &G = A.g[gi];
+    if (G.phase != kBInner) return;
+    const int n = G.nin, E = n * n, tid = threadIdx.x;
+    const long long p0 = (long long)blockIdx.x * TP;
+    const int len = (int)min((long long)TP, A.nd - p0);
+    const long long base = (long long)gi * A.sb * A.nd + p0;
+    for (int e = tid; e < n * TP; e += kBT) {
+        const int c = e / TP, t = e % TP;
+        C xv, yv;
+        xv.x = xv.y = yv.x = yv.y = (T)0;
+        if (t < len) {
+            xv = X[base + (long long)c * A.nd + t];
+            yv = Y[base + (long long)c * A.nd + t];
+        }
+        sx[c * (TP + 1) + t] = xv;
+        sy[c * (TP + 1) + t] = yv;
+    }
+    __syncthreads();
+    const int nsub = kBT / E;
+    double2 acc = make_double2(0.0, 0.0);
+    double accn = 0.0;
+    if (tid < E * nsub) {
+        const int e = tid % E, sub = tid / E, i = e / n, j = e % n;
+        T ar = 0, ai = 0, an = 0;
+        for (int t = sub; t < len; t += nsub) {
+            const C u = sx[i * (TP + 1) + t], w = sy[j * (TP + 1) + t];
+            ar += u.x * w.x - u.y * w.y;
+            ai += u.x * w.y + u.y * w.x;
+            an += u.x * u.x + u.y * u.y;
+        }
+        acc = make_double2((double)ar, (double)ai);
+        accn = (double)an;
+    }
+    red[tid] = acc;
+    redn[tid] = accn;
+    __syncthreads();
+    if (tid < E) {
+        double sr = 0.0, si = 0.0, sn = 0.0;
+        for (int sub = 0; sub < nsub; ++sub) {
+            sr += red[sub * E + tid].x;
+            si += red[sub * E + tid].y;
+            sn += redn[sub * E + tid];
+        }
+        const int i = tid / n, j = tid % n;
+        const int ld = A.sb * A.sb + A.sb;
+        double2 *o = A.gpart + ((long long)gi * A.ntile + blockIdx.x) * ld;
+        o[i * A.sb + j] = make_double2(sr, si);
+        if (norms && i == j) o[A.sb * A.sb + i] = make_double2(sn, 0.0);
+    }
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+// Per group (one block): add the Gram partial sums in tile order, then
+//   mode 0 (inner start): rho = R^T R; stopping test;
+//   mode 1: alpha = (P^T Q)^-1 rho;
+//   mode 2: stopping test on the column norms, iteration limit; beta = rho^-1 rho', rho = rho'.
+// The s x s solves run in FP64 by Gaussian elimination with partial pivoting on the system
+// equilibrated by the rows' largest entries (D M D) y = D rhs, x = D y, D_i = max_j |M_ij|^-1/2; a
+// pivot below piv_tol (entries of D M D are at most 1) ends the inner solve.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bsmall(BArgs A, int mode) {
+    using C = typename BCx<T>::t;
+    __shared__ double2 M[kMaxBlock * kMaxBlock];
+    __shared__ double2 Bm[kMaxBlock * kMaxBlock];
+    __shared__ double2 S[kMaxBlock * kMaxBlock];
+    __shared__ double nrm[kMaxBlock], sc[kMaxBlock];
+    __shared__ double2 fct[kMaxBlock];
+    __shared__ int flag, piv;     // flag: 1 converged, 2 singular, 3 non-finite, 4 iteration limit
+    const int gi = blockIdx.x, tid = threadIdx.x;
+    BGroup &G = A.g[gi];
+    if (G.phase != kBInner) return;
+    const int n = G.nin, E = n * n, ld = A.sb * A.sb + A.sb;
+    for (int e = tid; e < E + n; e += blockDim.x) {
+        const int off = e < E ? (e / n) * A.sb + e % n : A.sb * A.sb + (e - E);
+        const double2 *q = A.gpart + (long long)gi * A.ntile * ld + off;
+        double sr = 0.0, si = 0.0;
+        for (int t = 0; t < A.ntile; ++t) {
+            const double2 v = q[(long long)t * ld];
+            sr += v.x;
+            si += v.y;
+        }
+        if (e < E) S[e] = make_double2(sr, si);
+        else nrm[e - E] = sr;
+    }
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    double2 *rho = A.rho + (long long)gi * A.sb * A.sb;
+    if (tid == 0) {
+        bool fin = true, all = true;
+        for (int e = 0; e < E; ++e)
+            if (!isfinite(S[e].x) || !isfinite(S[e].y)) fin = false;
+        if (mode != 1)
+            for (int i = 0; i < n; ++i) {
+                const double r = sqrt(nrm[i]);
+                if (!isfinite(r)) fin = false;
+                if (!(r <= G.thr[i])) all = false;
+            }
+        if (!fin) flag = 3;
+        else if (mode != 1 && all) flag = 1;
+        else if (mode == 2 && G.inner_iters >= A.maxit) flag = 4;
+    }
+    __syncthreads();
+    if (flag) {
+        if (tid == 0) {
+            if (flag == 3) {
+                G.discard = 1;
+                G.nonfinite = 1;
+            }
+            G.phase = kBInnerDone;
+        }
+        return;
+    }
+    if (mode == 0) {
+        for (int e = tid; e < E; e += blockDim.x) rho[e] = S[e];
+        return;
+    }
+    for (int e = tid; e < E; e += blockDim.x) {
+        M[e] = mode == 1 ? S[e] : rho[e];
+        Bm[e] = mode == 1 ? rho[e] : S[e];
+    }
+    __syncthreads();
+    if (tid < n) {
+        double mx = 0.0;
+        for (int j = 0; j < n; ++j) mx = fmax(mx, hypot(M[tid * n + j].x, M[tid * n + j].y));
+        sc[tid] = (mx > 0.0 && isfinite(mx)) ? 1.0 / sqrt(mx) : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < E; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double f = sc[i] * sc[j];
+        M[e] = make_double2(M[e].x * f, M[e].y * f);
+        Bm[e] = make_double2(Bm[e].x * sc[i], Bm[e].y * sc[i]);
+    }
+    if (tid == 0)
+        for (int i = 0; i < n; ++i)
+            if (sc[i] == 0.0) flag = 2;
+    __syncthreads();
+    // flag is written by thread 0 only before a barrier and read by all only after one
+    for (int k = 0; k < n; ++k) {
+        if (tid == 0) {
+            int r = k;
+            double best = hypot(M[k * n + k].x, M[k * n + k].y);
+            for (int i = k + 1; i < n; ++i) {
+                const double v = hypot(M[i * n + k].x, M[i * n + k].y);
+                if (v > best) {
+                    best = v;
+                    r = i;
+                }
+            }
+            if (!(best > A.piv_tol)) flag = 2;
+            piv = r;
+        }
+        __syncthreads();
+        if (flag) break;
+        const int r = piv;
+        if (r != k)
+            for (int t = tid; t < 2 * n; t += blockDim.x) {
+                double2 *a = t < n ? &M[k * n + t] : &Bm[k * n + t - n];
+                double2 *b = t < n ? &M[r * n + t] : &Bm[r * n + t - n];
+                const double2 tmp = *a;
+                *a = *b;
+                *b = tmp;
+            }
+        __syncthreads();
+        if (tid > k && tid < n) fct[tid] = cdivd(M[tid * n + k], M[k * n + k]);
+        __syncthreads();
+        for (int t = tid; t < (n - k - 1) * 2 * n; t += blockDim.x) {
+            const int i = k + 1 + t / (2 * n), col = t % (2 * n);
+            if (col < n) {
+                if (col > k) {
+                    const double2 d = cmul(fct[i], M[k * n + col]);
+                    M[i * n + col].x -= d.x;
+                    M[i * n + col].y -= d.y;
+                }
+            } else {
+                const double2 d = cmul(fct[i], Bm[k * n + col - n]);
+                Bm[i * n + col - n].x -= d.x;
+                Bm[i * n + col - n].y -= d.y;
+            }
+        }
+        __syncthreads();
+    }
+    if (flag) {
+        if (tid == 0) {
+            G.nearb += 1;
+            G.cap = max(1, n / 2);
+            G.phase = kBInnerDone;
+        }
+        return;
+    }
+    if (tid < n) {
+        const int j = tid;
+        for (int k = n - 1; k >= 0; --k) {
+            double2 s = Bm[k * n + j];
+            for (int m = k + 1; m < n; ++m) {
+                const double2 d = cmul(M[k * n + m], Bm[m * n + j]);
+                s.x -= d.x;
+                s.y -= d.y;
+            }
+            Bm[k * n + j] = cdivd(s, M[k * n + k]);
+        }
+    }
+    __syncthreads();
+    C *cf = reinterpret_cast<C *>(A.coef) + (long long)gi * A.sb * A.sb;
+    for (int e = tid; e < E; e += blockDim.x) {
+        const double f = sc[e / n];
+        C v;
+        v.x = (T)(Bm[e].x * f);
+        v.y = (T)(Bm[e].y * f);
+        cf[e] = v;
+    }
+    if (mode == 1) {
+        if (tid == 0) {
+            G.inner_iters += 1;
+            G.iters += 1;
+            for (int i = 0; i < n; ++i) G.itc[G.cmap[i]] += 1;
+        }
+    } else {
+        for (int e = tid; e < E; e += blockDim.x) rho[e] = S[e];
+    }
+}
+
+// X += P alpha, R -= Q alpha (UPDATE), or P = R + P beta, per grid point over the group's inner
+// columns held in registers.  Grid: (points / 256, groups).
+template <typename T, int NB, bool UPDATE>
+__global__ void __launch_bounds__(kBT) k_bmix(BArgs A, typename BCx<T>::t *__restrict__ x,
+                                              typename BCx<T>::t *__restrict__ r, typename BCx<T>::t *__restrict__ p,
+                                              const typename BCx<T>::t *__restrict__ q) {
+    using C = typename BCx<T>::t;
+    __shared__ C cf[NB * NB];
+    const int gi = blockIdx.y;
+    const BGroup &G = A.g[gi];
+    if (G.phase != kBInner) return;
+    const int n = G.nin;
+    const C *src = reinterpret_cast<const C *>(A.coef) + (long long)gi * A.sb * A.sb;
+    for (int e = threadIdx.x; e < NB * NB; e += kBT) {
+        const int i = e / NB, j = e % NB;
+        C v;
+        v.x = v.y = (T)0;
+        if (i < n && j < n) v = src[i * n + j];
+        cf[e] = v;
+    }
+    __syncthreads();
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (idx >= A.nd) return;
+    const long long base = (long long)gi * A.sb * A.nd + idx;
+    C pk[NB], qk[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        pk[k].x = pk[k].y = (T)0;
+        qk[k] = pk[k];
+        if (k < n) {
+            pk[k] = p[base + (long long)k * A.nd];
+            if (UPDATE) qk[k] = q[base + (long long)k * A.nd];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < n) {
+            T ur = 0, ui = 0, vr = 0, vi = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const C a = cf[k * NB + j];
+                ur += pk[k].x * a.x - pk[k].y * a.y;
+                ui += pk[k].x * a.y + pk[k].y * a.x;
+                if (UPDATE) {
+                    vr += qk[k].x * a.x - qk[k].y * a.y;
+                    vi += qk[k].x * a.y + qk[k].y * a.x;
+                }
+            }
+            const long long o = base + (long long)j * A.nd;
+            C rv = r[o];
+            if (UPDATE) {
+                C xv = x[o];
+                xv.x += ur;
+                xv.y += ui;
+                rv.x -= vr;
+                rv.y -= vi;
+                x[o] = xv;
+                r[o] = rv;
+            } else {
+                rv.x += ur;
+                rv.y += ui;
+                p[o] = rv;
+            }
+        }
+    }
+}
+
+// x64 += ||r64|| X on the inner columns of the groups whose inner solve ended (unless it went
+// non-finite).  Grid: (points / 256, groups * sb).
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_bacc(BArgs A, const typename BCx<T>::t *__restrict__ x,
+                                              double2 *__restrict__ x64) {
+    const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (G.phase != kBInnerDone || G.discard || ci >= G.nin || idx >= A.nd) return;
+    const double s = G.scl[ci];
+    const typename BCx<T>::t d = x[((long long)gi * A.sb + ci) * A.nd + idx];
+    double2 &o = x64[((long long)gi * A.sb + G.cmap[ci]) * A.nd + idx];
+    o.x += s * (double)d.x;
+    o.y += s * (double)d.y;
+}
+
+// r64 = b - (H + sigma) x64 in FP64 on every column of the groups whose inner solve ended.
+__global__ void __launch_bounds__(kBT) k_bresid(BArgs A, const double *__restrict__ V, const double *__restrict__ b,
+                                                const double2 *__restrict__ x64, double2 *__restrict__ r64) {
+    const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (G.phase != kBInnerDone || c >= G.ncol || idx >= A.nd) return;
+    double a[kRadius + 1];
+#pragma unroll
+    for (int k = 0; k <= kRadius; ++k) a[k] = A.a[k];
+    const long long o = ((long long)gi * A.sb + c) * A.nd;
+    const double2 ax = bstencil_at<double>(x64 + o, V, (int)idx, A.nx, A.ny, A.nz, A.periodic, a, G.sre, G.sim);
+    r64[o + idx] = make_double2(b[o + idx] - ax.x, -ax.y);
+}
+
+// Number of groups with an inner solve running.
+__global__ void k_bcount(BArgs A) {
+    __shared__ int tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    int m = 0;
+    for (int g = threadIdx.x; g < A.ngroups; g += blockDim.x) m += A.g[g].phase == kBInner;
+    atomicAdd(&tot, m);
+    __syncthreads();
+    if (threadIdx.x == 0) *A.count = tot;
+}
+
+// drho_j += (4/h^3) u_n (.) Re x64 for every column j, the groups of orbitals added in wave order.
+// Grid: (points / 256, ncols).
+__global__ void __launch_bounds__(kBT) k_bretire_drho(BArgs A, const double2 *__restrict__ x64,
+                                                      const double *__restrict__ psi, double *__restrict__ drho,
+                                                      double scale) {
+    const int j = blockIdx.y;
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (idx >= A.nd) return;
+    double acc = drho[(long long)j * A.nd + idx];
+    for (int gi = 0; gi < A.ngroups; ++gi) {
+        const BGroup &G = A.g[gi];
+        const int c = j - G.row0;
+        if (c < 0 || c >= G.ncol) continue;
+        acc += scale * psi[(long long)G.n * A.nd + idx] * x64[((long long)gi * A.sb + c) * A.nd + idx].x;
+    }
+    drho[(long long)j * A.nd + idx] = acc;
+}
+
+// x_out[sys] = x64 for every column.  Grid: (points / 256, groups * sb).
+__global__ void __launch_bounds__(kBT) k_bretire_copy(BArgs A, const double2 *__restrict__ x64,
+                                                      double2 *__restrict__ xout) {
+    const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
+    const BGroup &G = A.g[gi];
+    const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
+    if (c >= G.ncol || idx >= A.nd) return;
+    xout[(long long)(G.sys0 + c) * A.nd + idx] = x64[((long long)gi * A.sb + c) * A.nd + idx];
+}
+
+// rows[j] = u_n (.) dv_j for j < ncols (right-hand sides of orbital n before the projection).
+__global__ void k_bpair_rows(const double *__restrict__ psi, const double *__restrict__ dv, int n, long long nd,
+                             double *__restrict__ rows) {
+    const int j = blockIdx.y;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (long long)gridDim.x * blockDim.x)
+        rows[(long long)j * nd + i] = psi[(long long)n * nd + i] * dv[(long long)j * nd + i];
+}
+
+struct BSpec {
+    const double *vt = nullptr;     // pair right-hand sides u_n (.) vt_row ...
+    const double *rhs = nullptr;    // ... or rows of rhs
+    const double *Tc = nullptr;     // P_c coefficients per system (or nullptr)
+    double sign = 1.0;
+    double omega = 0.0;
+    double *drho = nullptr;         // retire into drho (ncols rows) ...
+    int ncols = 0;
+    double2 *xout = nullptr;        // ... or copy the solutions out
+    std::vector<BGroup> groups;     // in retire order
+};
+
+template <typename T, int NB>
+void launch_mix(const BArgs &A, void *x, void *r, void *p, const void *q, bool update, dim3 grid, cudaStream_t s) {
+    using C = typename BCx<T>::t;
+    if (update)
+        k_bmix<T, NB, true><<<grid, kBT, 0, s>>>(A, (C *)x, (C *)r, (C *)p, (const C *)q);
+    else
+        k_bmix<T, NB, false><<<grid, kBT, 0, s>>>(A, (C *)x, (C *)r, (C *)p, (const C *)q);
+    RPA_LAUNCH("block COCG mix");
+}
+
+template <typename T>
+void mix(const BArgs &A, void *x, void *r, void *p, const void *q, bool update, dim3 grid, cudaStream_t s) {
+    if (A.sb <= 4) launch_mix<T, 4>(A, x, r, p, q, update, grid, s);
+    else if (A.sb <= 8) launch_mix<T, 8>(A, x, r, p, q, update, grid, s);
+    else launch_mix<T, 16>(A, x, r, p, q, update, grid, s);
+}
+
+template <typename T>
+int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
+    using C = typename BCx<T>::t;
+    constexpr int TP = BTile<T>::v;
+    const bool mixed = c.opt.prec == RPA_MIXED;
+    const int sb = c.opt.block_cocg;
+    const long long nd = c.nd;
+    const int total = (int)sp.groups.size();
+    if (total == 0) return RPA_OK;
+    const double per_group = (double)sb * nd * (8.0 + 16.0 + 16.0 + 4.0 * sizeof(C));
+    int W = (int)std::max(1.0, std::min((double)total, std::floor(kBBudget / per_group)));
+    W = std::min(W, 65535 / sb);
+    if (c.opt.batch_systems > 0) W = std::min(W, std::max(1, c.opt.batch_systems / sb));
+    const size_t n = (size_t)W * sb * nd;
+
+    BArgs A{};
+    A.sb = sb;
+    A.nd = nd;
+    A.nx = c.nx;
+    A.ny = c.ny;
+    A.nz = c.nz;
+    A.periodic = c.opt.periodic;
+    A.ntile = (int)((nd + TP - 1) / TP);
+    A.nchunk = (int)((nd + kBChunk - 1) / kBChunk);
+    A.mixed = mixed;
+    A.maxit = c.opt.maxit;
+    A.max_refine = c.opt.max_refine;
+    A.tol = c.opt.tol;
+    A.inner_tol = c.opt.inner_tol;
+    A.piv_tol = mixed ? 1e-5 : 1e-12;
+    for (int k = 0; k <= kRadius; ++k) A.a[k] = c.coef.a[k];
+
+    // storage: b, x64, r64 (FP64), then X, R, P, Q (inner precision), then the small arrays
+    const size_t ld = (size_t)sb * sb + sb;
+    const size_t bytes = n * (8 + 16 + 16 + 4 * sizeof(C)) + sizeof(BGroup) * W +
+                         sizeof(double2) * ((size_t)W * A.ntile * ld + 2 * (size_t)W * sb * sb) +
+                         sizeof(double) * (size_t)W * sb * A.nchunk * 2 + 16 * 256;
+    char *base = (char *)c.cocg_state.ensure(bytes);
+    size_t off = 0;
+    auto take = [&](size_t nb) {
+        off = (off + 255) / 256 * 256;
+        char *q = base + off;
+        off += nb;
+        return (void *)q;
+    };
+    double *b = (double *)take(sizeof(double) * n);
+    double2 *x64 = (double2 *)take(sizeof(double2) * n);
+    double2 *r64 = (double2 *)take(sizeof(double2) * n);
+    C *xv = (C *)take(sizeof(C) * n);
+    C *rv = (C *)take(sizeof(C) * n);
+    C *pv = (C *)take(sizeof(C) * n);
+    C *qv = (C *)take(sizeof(C) * n);
+    A.g = (BGroup *)take(sizeof(BGroup) * W);
+    A.gpart = (double2 *)take(sizeof(double2) * (size_t)W * A.ntile * ld);
+    A.rho = (double2 *)take(sizeof(double2) * (size_t)W * sb * sb);
+    A.coef = take(sizeof(double2) * (size_t)W * sb * sb);
+    A.npart = (double *)take(sizeof(double) * (size_t)W * sb * A.nchunk * 2);
+    A.count = (int *)take(sizeof(int) * 4);
+
+    const size_t gram_smem = 2 * (size_t)sb * (TP + 1) * sizeof(C);
+    allow_dynamic_smem((const void *)k_bgram<T>, gram_smem);
+    const T *Vt = mixed ? (const T *)(const void *)c.vloc32 : (const T *)(const void *)c.vloc64;
+    const unsigned pblk = (unsigned)((nd + kBT - 1) / kBT);
+
+    QueueStats qs{};
+    int worst = RPA_OK;
+    std::vector<BGroup> h(W);
+    auto read_count = [&]() {
+        RPA_CUDA(cudaMemcpyAsync(c.h_count, A.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        sync_stream(c, st);
+        return *c.h_count;
+    };
+    for (int w0 = 0; w0 < total; w0 += W) {
+        const int nw = std::min(W, total - w0);
+        A.ngroups = nw;
+        for (int i = 0; i < nw; ++i) {
+            BGroup g = sp.groups[w0 + i];
+            g.phase = kBCheck;
+            g.status = RPA_OK;
+            g.cap = g.ncol;
+            g.sre = -c.eps[g.n];
+            g.sim = sp.omega;
+            h[i] = g;
+        }
+        RPA_CUDA(cudaMemcpyAsync(A.g, h.data(), sizeof(BGroup) * nw, cudaMemcpyHostToDevice, st));
+        const dim3 gcols(pblk, nw * sb), ggrp(pblk, nw);
+        k_bload<<<gcols, kBT, 0, st>>>(A, c.psi64, c.ns, sp.vt, sp.rhs, sp.Tc, sp.sign, b, x64, r64);
+        RPA_LAUNCH("block COCG load");
+        count_launches(1);
+        for (;;) {
+            RPA_CUDA(cudaMemsetAsync(A.count, 0, sizeof(int), st));
+            k_bnorm<<<dim3(A.nchunk, nw * sb), kBT, 0, st>>>(A, b, r64);
+            RPA_LAUNCH("block COCG norms");
+            k_bcheck<<<nw, 32, 0, st>>>(A);
+            RPA_LAUNCH("block COCG check");
+            count_launches(2);
+            if (read_count() == 0) break;
+            k_bstart<T><<<gcols, kBT, 0, st>>>(A, r64, xv, rv, pv);
+            RPA_LAUNCH("block COCG start");
+            k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1);
+            RPA_LAUNCH("block COCG gram");
+            k_bsmall<T><<<nw, 256, 0, st>>>(A, 0);
+            RPA_LAUNCH("block COCG small");
+            count_launches(3);
+            for (int it = 1;; ++it) {
+                k_bstencil<T><<<gcols, kBT, 0, st>>>(A, pv, qv, Vt);
+                RPA_LAUNCH("block COCG stencil");
+                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, pv, qv, 0);
+                RPA_LAUNCH("block COCG gram");
+                k_bsmall<T><<<nw, 256, 0, st>>>(A, 1);
+                RPA_LAUNCH("block COCG small");
+                mix<T>(A, xv, rv, pv, qv, true, ggrp, st);
+                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1);
+                RPA_LAUNCH("block COCG gram");
+                k_bsmall<T><<<nw, 256, 0, st>>>(A, 2);
+                RPA_LAUNCH("block COCG small");
+                mix<T>(A, xv, rv, pv, qv, false, ggrp, st);
+                count_launches(7);
+                if (it % kBCheckEvery == 0) {
+                    k_bcount<<<1, 256, 0, st>>>(A);
+                    RPA_LAUNCH("block COCG count");
+                    count_launches(1);
+                    if (read_count() == 0) break;
+                }
+            }
+            k_bacc<T><<<gcols, kBT, 0, st>>>(A, xv, x64);
+            RPA_LAUNCH("block COCG accumulate");
+            k_bresid<<<gcols, kBT, 0, st>>>(A, c.vloc64, b, x64, r64);
+            RPA_LAUNCH("block COCG residual");
+            count_launches(2);
+        }
+        if (sp.drho) {
+            k_bretire_drho<<<dim3(pblk, sp.ncols), kBT, 0, st>>>(A, x64, c.psi64, sp.drho, 4.0 / (c.h * c.h * c.h));
+            RPA_LAUNCH("block COCG retire");
+        } else {
+            k_bretire_copy<<<gcols, kBT, 0, st>>>(A, x64, sp.xout);
+            RPA_LAUNCH("block COCG copy");
+        }
+        count_launches(1);
+        RPA_CUDA(cudaMemcpyAsync(h.data(), A.g, sizeof(BGroup) * nw, cudaMemcpyDeviceToHost, st));
+        sync_stream(c, st);
+        for (int i = 0; i < nw; ++i) {
+            const BGroup &g = h[i];
+            qs.solves += g.ncol;
+            qs.nearb += g.nearb;
+            worst = std::max(worst, g.status);
+            for (int k = 0; k < g.ncol; ++k) {
+                qs.iters += g.itc[k];
+                qs.refines += g.refc[k];
+                if (iters_out) (*iters_out)[g.sys0 + k] = g.itc[k];
+                if (status_out) (*status_out)[g.sys0 + k] = g.status;
+            }
+        }
+    }
+    qs.worst = worst;
+    return add_queue_stats(c, qs);
+}
+
+int run_block(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters, std::vector<int> *status) {
+    return c.opt.prec == RPA_MIXED ? run_block_t<float>(c, sp, st, iters, status)
+                                   : run_block_t<double>(c, sp, st, iters, status);
+}
+
+BGroup make_group(int n, int ncol, int sys0, int row0) {
+    BGroup g{};
+    g.n = n;
+    g.ncol = ncol;
+    g.sys0 = sys0;
+    g.row0 = row0;
+    return g;
+}
+
+}  // namespace
+
+int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
+    if (ncols == 0) return RPA_OK;
+    const int sb = c.opt.block_cocg;
+    // P_c coefficients T[(n, j)][k] = u_k . (u_n (.) dv_j), in FP64: the block iteration does not
+    // project its residuals again, so the right-hand sides keep whatever occupied components these
+    // coefficients leave
+    double *T = (double *)c.pc_coef.ensure(sizeof(double) * (size_t)c.ns * ncols * c.ns);
+    double *rows = (double *)c.rhs.ensure(sizeof(double) * (size_t)ncols * c.nd);
+    for (int n = 0; n < c.ns; ++n) {
+        k_bpair_rows<<<dim3((unsigned)std::min<long long>((c.nd + 255) / 256, 1024), ncols), 256, 0, s>>>(
+            c.psi64, dv, n, c.nd, rows);
+        RPA_LAUNCH("block COCG pair rows");
+        count_launches(1);
+        gram(rows, ncols, c.psi64, c.ns, c.nd, T + (size_t)n * ncols * c.ns, s, c.dense_scratch);
+    }
+    BSpec sp;
+    sp.vt = dv;
+    sp.Tc = T;
+    sp.sign = -1.0;
+    sp.omega = omega;
+    sp.drho = drho;
+    sp.ncols = ncols;
+    for (int n = 0; n < c.ns; ++n)
+        for (int j0 = 0; j0 < ncols; j0 += sb)
+            sp.groups.push_back(make_group(n, std::min(sb, ncols - j0), n * ncols + j0, j0));
+    return run_block(c, sp, s, nullptr, nullptr);
+}
+
+int sternheimer_block(Ctx &c, double omega, const int *orb, int nsys, const double *b, const double *Tc, double *x,
+                      std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {
+    const int sb = c.opt.block_cocg;
+    BSpec sp;
+    sp.rhs = b;
+    sp.Tc = Tc;
+    sp.sign = 1.0;
+    sp.omega = omega;
+    sp.xout = (double2 *)x;
+    for (int i = 0; i < nsys;) {
+        int e = i + 1;
+        while (e < nsys && e - i < sb && orb[e] == orb[i]) ++e;
+        sp.groups.push_back(make_group(orb[i], e - i, i, i));
+        i = e;
+    }
+    return run_block(c, sp, s, iters, status);
+}
+
+}  // namespace rpa

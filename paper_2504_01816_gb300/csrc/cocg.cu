@@ -3415,6 +3415,7 @@ bool fused_kernel_applies(const Ctx &c, bool warp_specialised, bool cluster) {
 int sternheimer_batch(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,
                       std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {
     check_orbitals(c, orb, nsys);
+    if (c.opt.block_cocg > 0) return sternheimer_block(c, omega, orb, nsys, b, nullptr, x, iters, status, s);
     SolveSpec sp;
     sp.rhs = b;
     sp.xout = (double2 *)x;
@@ -3429,6 +3430,11 @@ int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, 
                                 std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {
     check_orbitals(c, orb, nsys);
     double *T = (double *)c.pc_coef.ensure(sizeof(double) * (size_t)nsys * c.ns);
+    if (c.opt.block_cocg > 0) {
+        // FP64 coefficients: the block iteration does not project its residuals again
+        gram(b, nsys, c.psi64, c.ns, c.nd, T, s, c.dense_scratch);
+        return sternheimer_block(c, omega, orb, nsys, b, T, x, iters, status, s);
+    }
     pc_coefficients(c, b, nsys, T, s);
     SolveSpec sp;
     sp.rhs = b;
@@ -3472,6 +3478,7 @@ int response_square(Ctx &c, double omega, const double *dv, const double *coef, 
 }
 
 int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    if (c.opt.block_cocg > 0) return chi0_apply_block(c, omega, dv, drho, ncols, s);
     RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
     const int nsys = c.ns * ncols;
     SolveSpec sp;

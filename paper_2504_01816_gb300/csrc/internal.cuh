@@ -15,6 +15,7 @@ namespace rpa {
 constexpr int kRadius = 6;              // 12th-order centred differences
 constexpr int kMaxOmega = 64;
 constexpr int kMaxSqOrder = 32;     // largest Gauss spectral quadrature order
+constexpr int kMaxBlock = 16;       // largest block of block COCG
 
 // ------------------------------------------------------------------------------------------
 // Errors: every internal failure throws rpa::Error; the C entry points catch it and turn it
@@ -205,6 +206,13 @@ void ritz_rotation(const double *Q, const double *w, int n, double weight, doubl
 // Whether the fused single-pass COCG kernel applies to this context's grid (a whole xy plane fits
 // its shared-memory ring); the mixed form then uses it by default.
 bool fused_kernel_applies(const Ctx &c, bool warp_specialised = false, bool cluster = false);
+
+// Block COCG (block_cocg.cu) for systems grouped by orbital: chi0 on ncols columns (as chi0_apply)
+// and the Sternheimer solves of rpa_sternheimer_solve (as sternheimer_batch; Tc: P_c coefficients
+// of the rows of b, or nullptr).
+int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s);
+int sternheimer_block(Ctx &c, double omega, const int *orb, int nsys, const double *b, const double *Tc,
+                      double *x, std::vector<int> *iters, std::vector<int> *status, cudaStream_t s);
 
 // Same as sternheimer_batch, with b replaced by P_c b first.
 int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

@@ -44,7 +44,8 @@ class rpa_options(ctypes.Structure):
                 ("z_chunks", ctypes.c_int), ("stencil_shape", ctypes.c_int),
                 ("independent_frequencies", ctypes.c_int), ("sq_order", ctypes.c_int),
                 ("contractions", ctypes.c_int), ("omega_first", ctypes.c_int), ("omega_count", ctypes.c_int),
-                ("periodic", ctypes.c_int), ("precondition", ctypes.c_int)]
+                ("periodic", ctypes.c_int), ("precondition", ctypes.c_int),
+                ("block_cocg", ctypes.c_int)]
 
 
 PROF_SLOTS = 8
@@ -180,6 +181,7 @@ class Options:
     omega_count: int = 0
     periodic: int = 0
     precondition: int = 0
+    block_cocg: int = 0
 
     def to_c(self) -> rpa_options:
         o = rpa_options()

@@ -50,11 +50,11 @@ def test_struct_layouts_match_header(rpa, tmp_path):
 #include <stddef.h>
 #include "rpa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rpa_options), sizeof(rpa_stats),
          offsetof(rpa_options, independent_frequencies), offsetof(rpa_stats, ms_coulomb),
          offsetof(rpa_stats, worst_status), offsetof(rpa_stats, prof_bytes), offsetof(rpa_stats, launches),
          offsetof(rpa_stats, near_breakdowns), offsetof(rpa_options, sq_order), offsetof(rpa_options, contractions),
-         offsetof(rpa_options, periodic), offsetof(rpa_options, precondition));
+         offsetof(rpa_options, periodic), offsetof(rpa_options, precondition), offsetof(rpa_options, block_cocg));
   return 0;
 }
 """)
@@ -65,7 +65,7 @@ int main(void) {
     assert got == [ctypes.sizeof(O), ctypes.sizeof(S), O.independent_frequencies.offset, S.ms_coulomb.offset,
                    S.worst_status.offset, S.prof_bytes.offset, S.launches.offset,
                    S.near_breakdowns.offset, O.sq_order.offset, O.contractions.offset, O.periodic.offset,
-                   O.precondition.offset]
+                   O.precondition.offset, O.block_cocg.offset]
 
 
 def test_setup_rejects_bad_arguments_without_a_gpu(rpa):
@@ -87,11 +87,24 @@ def test_setup_rejects_bad_arguments_without_a_gpu(rpa):
     st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)
     assert st == rpa.RPA_ERR_INVALID and b"n_omega" in lib.rpa_last_error()
     for field, value in (("sq_order", 33), ("stencil_shape", 7), ("z_chunks", -1), ("contractions", 4),
-                         ("periodic", 2), ("precondition", 3)):
+                         ("periodic", 2), ("precondition", 3), ("block_cocg", 17)):
         lib.rpa_default_options(ctypes.byref(bad))
         setattr(bad, field, value)
         st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)
         assert st == rpa.RPA_ERR_INVALID and field.encode() in lib.rpa_last_error()
+
+
+def test_block_cocg_excludes_precondition_and_projection(rpa):
+    lib = rpa.library()
+    hd = ctypes.c_void_p()
+    eps = (ctypes.c_double * 1)(-1.0)
+    bad = rpa.rpa.rpa_options()
+    for field in ("precondition", "project_solution"):
+        lib.rpa_default_options(ctypes.byref(bad))
+        bad.block_cocg = 4
+        setattr(bad, field, 1)
+        st = lib.rpa_setup(ctypes.byref(hd), 4, 4, 4, 0.5, 12, 1, 1, eps, 1, ctypes.byref(bad), None)
+        assert st == rpa.RPA_ERR_INVALID and b"block_cocg" in lib.rpa_last_error()
 
 
 def test_calls_on_null_context_are_rejected(rpa):
