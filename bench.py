@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--workload", default="mixed40")
     ap.add_argument("--slots", type=int, default=0,
                     help="rpa_options.batch_systems: systems in flight (0: as many as fit the slot budget)")
+    ap.add_argument("--block-cocg", type=int, default=0,
+                    help="rpa_options.block_cocg: s > 0 solves the systems of an orbital s at a time by block COCG")
     ap.add_argument("--precondition", type=int, default=0,
                     help="rpa_options.precondition: 1 = Laplacian-preconditioned COCG")
     ap.add_argument("--stencil-shape", type=int, default=-1,
@@ -308,6 +310,7 @@ def run_ours(args):
     opts.profile = 0                           # the timed steps run without per-launch events
     opts.periodic = int(getattr(s, "periodic", False))   # the system's boundary conditions
     opts.precondition = args.precondition
+    opts.block_cocg = args.block_cocg
     opts.batch_systems = args.slots
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -335,7 +338,7 @@ def run_ours(args):
     if args.stencil_shape >= 0:                # a fixed kernel configuration (profiler captures)
         opts.stencil_shape = args.stencil_shape
         ctx.set_options(opts)
-    elif args.prec == "mixed" and not args.no_autotune:
+    elif args.prec == "mixed" and not args.no_autotune and not args.block_cocg:
         om_mid = ctx_omegas(w.n_omega)[w.n_omega // 2]
         chosen, names, times = ctx.autotune(om_mid, V0)
         opts.stencil_shape, opts.z_chunks = ctx.options.stencil_shape, ctx.options.z_chunks
@@ -398,7 +401,8 @@ def run_ours(args):
                            "l2": "flushed (512 MB write) between timed steps",
                            "contractions": "tensor cores (tcgen05, exact integer pieces)"
                            if args.prec == "mixed" else "FP64 CUDA cores",
-                           "cocg": "Laplacian-preconditioned" if args.precondition else "plain",
+                           "cocg": ("Laplacian-preconditioned" if args.precondition else
+                                    f"block COCG, groups of {args.block_cocg}" if args.block_cocg else "plain"),
                            "mean_cocg_iterations_per_solve": mean_iters,
                            "near_breakdowns_per_step": sum(st.get("near_breakdowns", 0) for st in kstats) / args.steps,
                            "autotune": tune,
@@ -412,7 +416,7 @@ def run_ours(args):
                 "e_c_per_atom_last_step": res.e_c_per_atom}
     if not args.no_fp64 and rank == 0:
         o64 = rpa.default_options()
-        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "periodic", "precondition"):
+        for k in ("tol", "n_omega", "fixed_subspace_iters", "n_atoms", "periodic", "precondition", "block_cocg"):
             setattr(o64, k, getattr(opts, k))
         o64.prec = rpa.RPA_FP64
         r64, ms64 = timed_ec(o64)
@@ -428,7 +432,8 @@ def run_ours(args):
         tts = {}
         for name, prec in (("mixed", rpa.RPA_MIXED), ("fp64", rpa.RPA_FP64)):
             ot = rpa.default_options()
-            for k in ("tol", "n_omega", "n_atoms", "stencil_shape", "z_chunks", "periodic", "precondition"):
+            for k in ("tol", "n_omega", "n_atoms", "stencil_shape", "z_chunks", "periodic", "precondition",
+                      "block_cocg"):
                 setattr(ot, k, getattr(opts, k))
             ot.prec = prec
             ot.eps_c = 1e-5

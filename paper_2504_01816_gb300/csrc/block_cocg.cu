@@ -37,10 +37,12 @@ namespace {
 
 constexpr int kBT = 256;               // threads of the streaming kernels
 constexpr int kBChunk = 2048;          // grid points per norm work item (8 per thread)
-constexpr int kBCheckEvery = 8;        // inner iterations between the host's looks at the active count
+constexpr int kBCheckEvery = 8;        // inner iterations between maintenance passes
 constexpr double kBBudget = 8.0e9;     // bytes of vectors of the groups in flight
 
-enum BPhase : int { kBDone = 0, kBInner = 1, kBInnerDone = 2, kBCheck = 3 };
+// A group's phase: its inner solve starting (kBStart) or running (kBInner), ended and awaiting the
+// FP64 residual (kBInnerDone), loaded and awaiting the first check (kBCheck), or done.
+enum BPhase : int { kBDone = 0, kBInner = 1, kBInnerDone = 2, kBCheck = 3, kBStart = 4 };
 
 template <typename T> struct BCx;
 template <> struct BCx<float> { using t = float2; };
@@ -254,12 +256,11 @@ __global__ void k_bcheck(BArgs A) {
             G.phase = kBDone;
             G.status = (mb || G.nonfinite) ? RPA_ERR_BREAKDOWN : RPA_ERR_NOT_CONVERGED;
         } else {
-            G.phase = kBInner;
+            G.phase = kBStart;
             G.nin = nin;
             G.refines += 1;
             G.inner_iters = 0;
             G.discard = 0;
-            atomicAdd(A.count, 1);
         }
     }
 }
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(kBT) k_bstart(BArgs A, const double2 *__restri
     const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (G.phase != kBInner || ci >= G.nin || idx >= A.nd) return;
+    if (G.phase != kBStart || ci >= G.nin || idx >= A.nd) return;
     const double inv = 1.0 / G.scl[ci];
     const double2 v = r64[((long long)gi * A.sb + G.cmap[ci]) * A.nd + idx];
     const long long o = ((long long)gi * A.sb + ci) * A.nd + idx;
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kBT) k_bstencil(BArgs A, const typename BCx<T>
 // entry e = (i, j); the nsub sums of an entry are added in order.  Grid: (ntile, groups).
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t *__restrict__ X,
-                                               const typename BCx<T>::t *__restrict__ Y, int norms) {
+                                               const typename BCx<T>::t *__restrict__ Y, int norms, int ph) {
     using C = typename BCx<T>::t;
     constexpr int TP = BTile<T>::v;
     extern __shared__ __align__(16) unsigned char bsm[];
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t
     __shared__ double redn[kBT];
     const int gi = blockIdx.y;
     const BGroup &G = A.g[gi];
-    if (G.phase != kBInner) return;
+    if (G.phase != ph) return;
     const int n = G.nin, E = n * n, tid = threadIdx.x;
     const long long p0 = (long long)blockIdx.x * TP;
     const int len = (int)min((long long)TP, A.nd - p0);
@@ -376,7 +377,7 @@ __device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
 }
 
 // Per group (one block): add the Gram partial sums in tile order, then
-//   mode 0 (inner start): rho = R^T R; stopping test;
+//   mode 0 (inner start): rho = R^T R; stopping test; the inner solve runs from here on;
 //   mode 1: alpha = (P^T Q)^-1 rho;
 //   mode 2: stopping test on the column norms, iteration limit; beta = rho^-1 rho', rho = rho'.
 // The s x s solves run in FP64 by Gaussian elimination with partial pivoting on the system
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(256) k_bsmall(BArgs A, int mode) {
     __shared__ int flag, piv;     // flag: 1 converged, 2 singular, 3 non-finite, 4 iteration limit
     const int gi = blockIdx.x, tid = threadIdx.x;
     BGroup &G = A.g[gi];
-    if (G.phase != kBInner) return;
+    if (G.phase != (mode == 0 ? kBStart : kBInner)) return;
     const int n = G.nin, E = n * n, ld = A.sb * A.sb + A.sb;
     for (int e = tid; e < E + n; e += blockDim.x) {
         const int off = e < E ? (e / n) * A.sb + e % n : A.sb * A.sb + (e - E);
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(256) k_bsmall(BArgs A, int mode) {
     }
     if (mode == 0) {
         for (int e = tid; e < E; e += blockDim.x) rho[e] = S[e];
+        if (tid == 0) G.phase = kBInner;
         return;
     }
     for (int e = tid; e < E; e += blockDim.x) {
@@ -643,13 +645,13 @@ __global__ void __launch_bounds__(kBT) k_bresid(BArgs A, const double *__restric
     r64[o + idx] = make_double2(b[o + idx] - ax.x, -ax.y);
 }
 
-// Number of groups with an inner solve running.
+// Number of groups not done.
 __global__ void k_bcount(BArgs A) {
     __shared__ int tot;
     if (threadIdx.x == 0) tot = 0;
     __syncthreads();
     int m = 0;
-    for (int g = threadIdx.x; g < A.ngroups; g += blockDim.x) m += A.g[g].phase == kBInner;
+    for (int g = threadIdx.x; g < A.ngroups; g += blockDim.x) m += A.g[g].phase != kBDone;
     atomicAdd(&tot, m);
     __syncthreads();
     if (threadIdx.x == 0) *A.count = tot;
@@ -809,47 +811,44 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
         k_bload<<<gcols, kBT, 0, st>>>(A, c.psi64, c.ns, sp.vt, sp.rhs, sp.Tc, sp.sign, b, x64, r64);
         RPA_LAUNCH("block COCG load");
         count_launches(1);
+        // Maintenance, then kBCheckEvery inner iterations, until every group is done: a group whose
+        // inner solve ended takes its FP64 residual, stopping test and next inner start at the next
+        // maintenance pass while the others keep iterating.
         for (;;) {
-            RPA_CUDA(cudaMemsetAsync(A.count, 0, sizeof(int), st));
+            k_bacc<T><<<gcols, kBT, 0, st>>>(A, xv, x64);
+            RPA_LAUNCH("block COCG accumulate");
+            k_bresid<<<gcols, kBT, 0, st>>>(A, c.vloc64, b, x64, r64);
+            RPA_LAUNCH("block COCG residual");
             k_bnorm<<<dim3(A.nchunk, nw * sb), kBT, 0, st>>>(A, b, r64);
             RPA_LAUNCH("block COCG norms");
             k_bcheck<<<nw, 32, 0, st>>>(A);
             RPA_LAUNCH("block COCG check");
-            count_launches(2);
-            if (read_count() == 0) break;
             k_bstart<T><<<gcols, kBT, 0, st>>>(A, r64, xv, rv, pv);
             RPA_LAUNCH("block COCG start");
-            k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1);
+            k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1, kBStart);
             RPA_LAUNCH("block COCG gram");
             k_bsmall<T><<<nw, 256, 0, st>>>(A, 0);
             RPA_LAUNCH("block COCG small");
-            count_launches(3);
-            for (int it = 1;; ++it) {
+            count_launches(7);
+            for (int it = 0; it < kBCheckEvery; ++it) {
                 k_bstencil<T><<<gcols, kBT, 0, st>>>(A, pv, qv, Vt);
                 RPA_LAUNCH("block COCG stencil");
-                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, pv, qv, 0);
+                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, pv, qv, 0, kBInner);
                 RPA_LAUNCH("block COCG gram");
                 k_bsmall<T><<<nw, 256, 0, st>>>(A, 1);
                 RPA_LAUNCH("block COCG small");
                 mix<T>(A, xv, rv, pv, qv, true, ggrp, st);
-                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1);
+                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1, kBInner);
                 RPA_LAUNCH("block COCG gram");
                 k_bsmall<T><<<nw, 256, 0, st>>>(A, 2);
                 RPA_LAUNCH("block COCG small");
                 mix<T>(A, xv, rv, pv, qv, false, ggrp, st);
                 count_launches(7);
-                if (it % kBCheckEvery == 0) {
-                    k_bcount<<<1, 256, 0, st>>>(A);
-                    RPA_LAUNCH("block COCG count");
-                    count_launches(1);
-                    if (read_count() == 0) break;
-                }
             }
-            k_bacc<T><<<gcols, kBT, 0, st>>>(A, xv, x64);
-            RPA_LAUNCH("block COCG accumulate");
-            k_bresid<<<gcols, kBT, 0, st>>>(A, c.vloc64, b, x64, r64);
-            RPA_LAUNCH("block COCG residual");
-            count_launches(2);
+            k_bcount<<<1, 256, 0, st>>>(A);
+            RPA_LAUNCH("block COCG count");
+            count_launches(1);
+            if (read_count() == 0) break;
         }
         if (sp.drho) {
             k_bretire_drho<<<dim3(pblk, sp.ncols), kBT, 0, st>>>(A, x64, c.psi64, sp.drho, 4.0 / (c.h * c.h * c.h));
