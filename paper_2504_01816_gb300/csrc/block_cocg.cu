@@ -38,6 +38,7 @@ namespace {
 constexpr int kBT = 256;               // threads of the streaming kernels
 constexpr int kBChunk = 2048;          // grid points per norm work item (8 per thread)
 constexpr int kBCheckEvery = 8;        // inner iterations between maintenance passes
+constexpr int kBGramSlots = 32;        // blocks per group of a Gram launch (each sums every 32nd tile)
 constexpr double kBBudget = 8.0e9;     // bytes of vectors of the groups in flight
 
 // A group's phase: its inner solve starting (kBStart) or running (kBInner), ended and awaiting the
@@ -73,16 +74,20 @@ struct BArgs {
     long long nd;
     int nx, ny, nz, periodic;
     int ntile;                     // Gram tiles per group
+    int nslot;                     // Gram partial sums per group (blocks per group of a Gram launch)
     int nchunk;                    // norm work items per column
     int mixed, maxit, max_refine;
     double tol, inner_tol, piv_tol;
     double a[kRadius + 1];         // stencil coefficients
-    double2 *gpart;                // [group][ntile][sb*sb + sb] Gram partial sums; norms in .x of the tail
+    double2 *gpart;                // [group][nslot][sb*sb + sb] Gram partial sums; norms in .x of the tail
     double2 *rho;                  // [group][nin*nin]
     void *coef;                    // [group][nin*nin] alpha, then beta (complex T)
     double *npart;                 // [group*sb + c][nchunk][2] ||r64_c||^2, ||b_c||^2
-    int *count;
+    int *count;                    // [0] groups not done, [1] groups with an inner solve running
+    const int *alist;              // the inner iterations' launches: grid index -> group (else identity)
 };
+
+__device__ __forceinline__ int group_of(const BArgs &A, int y) { return A.alist ? A.alist[y] : y; }
 
 __device__ __forceinline__ int bwrap(int a, int n) {
     a %= n;
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(kBT) k_bstart(BArgs A, const double2 *__restri
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_bstencil(BArgs A, const typename BCx<T>::t *__restrict__ in,
                                                   typename BCx<T>::t *__restrict__ out, const T *__restrict__ V) {
-    const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
+    const int gi = group_of(A, blockIdx.y / A.sb), ci = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
     if (G.phase != kBInner || ci >= G.nin || idx >= A.nd) return;
@@ -303,68 +308,97 @@ __global__ void __launch_bounds__(kBT) k_bstencil(BArgs A, const typename BCx<T>
     out[o + idx] = bstencil_at<T>(in + o, V, (int)idx, A.nx, A.ny, A.nz, A.periodic, a, (T)G.sre, (T)G.sim);
 }
 
-// Gram partial sums of one tile: G_ij = sum_t X_i(t) Y_j(t) (unconjugated) over the tile's points,
-// and with norms != 0 also ||X_i||^2.  Thread (e, sub) of the block adds every nsub-th point for
-// entry e = (i, j); the nsub sums of an entry are added in order.  Grid: (ntile, groups).
-template <typename T>
+// Gram partial sums: G_ij = sum_t X_i(t) Y_j(t) (unconjugated), and with norms != 0 also ||X_i||^2,
+// over the tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the group's points.  A tile of TP
+// points of the n rows is staged in shared memory (once when X and Y are the same block), and the
+// next tile's values are loaded into registers while the current one is summed.  Thread (e, sub)
+// adds every nsub-th point of a tile for entry e = (i, j), in T within a tile and in FP64 across
+// tiles; the nsub sums of an entry are added in order.  Grid: (nslot, groups); the partial sums of
+// slot blockIdx.x go to gpart[group][blockIdx.x].
+template <typename T, int NB>
 __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t *__restrict__ X,
                                                const typename BCx<T>::t *__restrict__ Y, int norms, int ph) {
     using C = typename BCx<T>::t;
     constexpr int TP = BTile<T>::v;
+    constexpr int LPT = NB * TP / kBT;            // staged values per thread and row block, at most
     extern __shared__ __align__(16) unsigned char bsm[];
     C *sx = reinterpret_cast<C *>(bsm);
     C *sy = sx + (size_t)A.sb * (TP + 1);
     __shared__ double2 red[kBT];
     __shared__ double redn[kBT];
-    const int gi = blockIdx.y;
+    const int gi = group_of(A, blockIdx.y);
     const BGroup &G = A.g[gi];
     if (G.phase != ph) return;
+    const bool same = X == Y;
     const int n = G.nin, E = n * n, tid = threadIdx.x;
-    const long long p0 = (long long)blockIdx.x * TP;
-    const int len = (int)min((long long)TP, A.nd - p0);
-    const long long base = (long long)gi * A.sb * A.nd + p0;
-    for (int e = tid; e < n * TP; e += kBT) {
-        const int c = e / TP, t = e % TP;
-        C xv, yv;
-        xv.x = xv.y = yv.x = yv.y = (T)0;
-        if (t < len) {
-            xv = X[base + (long long)c * A.nd + t];
-            yv = Y[base + (long long)c * A.nd + t];
+    const long long gbase = (long long)gi * A.sb * A.nd;
+    C xr[LPT], yr[LPT];
+    auto fetch = [&](int tile) {
+        const long long p0 = (long long)tile * TP;
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+            const int e = tid + l * kBT;
+            xr[l].x = xr[l].y = (T)0;
+            yr[l] = xr[l];
+            if (e < n * TP) {
+                const int c = e / TP, t = e % TP;
+                if (p0 + t < A.nd) {
+                    const long long o = gbase + (long long)c * A.nd + p0 + t;
+                    xr[l] = X[o];
+                    if (!same) yr[l] = Y[o];
+                }
+            }
         }
-        sx[c * (TP + 1) + t] = xv;
-        sy[c * (TP + 1) + t] = yv;
-    }
-    __syncthreads();
+    };
     const int nsub = kBT / E;
-    double2 acc = make_double2(0.0, 0.0);
-    double accn = 0.0;
-    if (tid < E * nsub) {
-        const int e = tid % E, sub = tid / E, i = e / n, j = e % n;
-        T ar = 0, ai = 0, an = 0;
-        for (int t = sub; t < len; t += nsub) {
-            const C u = sx[i * (TP + 1) + t], w = sy[j * (TP + 1) + t];
-            ar += u.x * w.x - u.y * w.y;
-            ai += u.x * w.y + u.y * w.x;
-            an += u.x * u.x + u.y * u.y;
+    const bool active = tid < E * nsub;
+    const int e0 = tid % E, sub = tid / E, i = e0 / n, j = e0 % n;
+    const C *ys = same ? sx : sy;
+    double sr = 0.0, si = 0.0, sn = 0.0;
+    int tile = blockIdx.x;
+    if (tile < A.ntile) fetch(tile);
+    for (; tile < A.ntile; tile += gridDim.x) {
+        __syncthreads();                          // the previous tile has been summed
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) {
+            const int e = tid + l * kBT;
+            if (e < n * TP) {
+                const int c = e / TP, t = e % TP;
+                sx[c * (TP + 1) + t] = xr[l];
+                if (!same) sy[c * (TP + 1) + t] = yr[l];
+            }
         }
-        acc = make_double2((double)ar, (double)ai);
-        accn = (double)an;
+        __syncthreads();
+        const int len = (int)min((long long)TP, A.nd - (long long)tile * TP);
+        if (tile + (int)gridDim.x < A.ntile) fetch(tile + gridDim.x);
+        if (active) {
+            T ar = 0, ai = 0, an = 0;
+            for (int t = sub; t < len; t += nsub) {
+                const C u = sx[i * (TP + 1) + t], w = ys[j * (TP + 1) + t];
+                ar += u.x * w.x - u.y * w.y;
+                ai += u.x * w.y + u.y * w.x;
+                an += u.x * u.x + u.y * u.y;
+            }
+            sr += (double)ar;
+            si += (double)ai;
+            sn += (double)an;
+        }
     }
-    red[tid] = acc;
-    redn[tid] = accn;
+    red[tid] = make_double2(sr, si);
+    redn[tid] = sn;
     __syncthreads();
     if (tid < E) {
-        double sr = 0.0, si = 0.0, sn = 0.0;
-        for (int sub = 0; sub < nsub; ++sub) {
-            sr += red[sub * E + tid].x;
-            si += red[sub * E + tid].y;
-            sn += redn[sub * E + tid];
+        double tr = 0.0, ti = 0.0, tn = 0.0;
+        for (int q = 0; q < nsub; ++q) {
+            tr += red[q * E + tid].x;
+            ti += red[q * E + tid].y;
+            tn += redn[q * E + tid];
         }
-        const int i = tid / n, j = tid % n;
+        const int ii = tid / n, jj = tid % n;
         const int ld = A.sb * A.sb + A.sb;
-        double2 *o = A.gpart + ((long long)gi * A.ntile + blockIdx.x) * ld;
-        o[i * A.sb + j] = make_double2(sr, si);
-        if (norms && i == j) o[A.sb * A.sb + i] = make_double2(sn, 0.0);
+        double2 *o = A.gpart + ((long long)gi * A.nslot + blockIdx.x) * ld;
+        o[ii * A.sb + jj] = make_double2(tr, ti);
+        if (norms && ii == jj) o[A.sb * A.sb + ii] = make_double2(tn, 0.0);
     }
 }
 
@@ -392,15 +426,15 @@ __global__ void __launch_bounds__(256) k_bsmall(BArgs A, int mode) {
     __shared__ double nrm[kMaxBlock], sc[kMaxBlock];
     __shared__ double2 fct[kMaxBlock];
     __shared__ int flag, piv;     // flag: 1 converged, 2 singular, 3 non-finite, 4 iteration limit
-    const int gi = blockIdx.x, tid = threadIdx.x;
+    const int gi = group_of(A, blockIdx.x), tid = threadIdx.x;
     BGroup &G = A.g[gi];
     if (G.phase != (mode == 0 ? kBStart : kBInner)) return;
     const int n = G.nin, E = n * n, ld = A.sb * A.sb + A.sb;
     for (int e = tid; e < E + n; e += blockDim.x) {
         const int off = e < E ? (e / n) * A.sb + e % n : A.sb * A.sb + (e - E);
-        const double2 *q = A.gpart + (long long)gi * A.ntile * ld + off;
+        const double2 *q = A.gpart + (long long)gi * A.nslot * ld + off;
         double sr = 0.0, si = 0.0;
-        for (int t = 0; t < A.ntile; ++t) {
+        for (int t = 0; t < A.nslot; ++t) {
             const double2 v = q[(long long)t * ld];
             sr += v.x;
             si += v.y;
@@ -555,7 +589,7 @@ __global__ void __launch_bounds__(kBT) k_bmix(BArgs A, typename BCx<T>::t *__res
                                               const typename BCx<T>::t *__restrict__ q) {
     using C = typename BCx<T>::t;
     __shared__ C cf[NB * NB];
-    const int gi = blockIdx.y;
+    const int gi = group_of(A, blockIdx.y);
     const BGroup &G = A.g[gi];
     if (G.phase != kBInner) return;
     const int n = G.nin;
@@ -645,16 +679,38 @@ __global__ void __launch_bounds__(kBT) k_bresid(BArgs A, const double *__restric
     r64[o + idx] = make_double2(b[o + idx] - ax.x, -ax.y);
 }
 
-// Number of groups not done.
-__global__ void k_bcount(BArgs A) {
-    __shared__ int tot;
-    if (threadIdx.x == 0) tot = 0;
+// The groups with an inner solve running, in group order (each thread takes a contiguous range;
+// the ranges' counts are scanned in order), and the number of groups not done.  One block of 1024.
+__global__ void __launch_bounds__(1024) k_blist(BArgs A, int *__restrict__ list) {
+    __shared__ int cnt[1024];
+    __shared__ int notdone;
+    const int t = threadIdx.x;
+    const int per = (A.ngroups + 1023) / 1024;
+    const int g0 = min(A.ngroups, t * per), g1 = min(A.ngroups, g0 + per);
+    int m = 0, nd = 0;
+    for (int g = g0; g < g1; ++g) {
+        const int ph = A.g[g].phase;
+        m += ph == kBInner;
+        nd += ph != kBDone;
+    }
+    cnt[t] = m;
+    if (t == 0) notdone = 0;
     __syncthreads();
-    int m = 0;
-    for (int g = threadIdx.x; g < A.ngroups; g += blockDim.x) m += A.g[g].phase != kBDone;
-    atomicAdd(&tot, m);
+    atomicAdd(&notdone, nd);
+    if (t == 0) {
+        int sum = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int v = cnt[i];
+            cnt[i] = sum;
+            sum += v;
+        }
+        A.count[1] = sum;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) *A.count = tot;
+    int w = cnt[t];
+    for (int g = g0; g < g1; ++g)
+        if (A.g[g].phase == kBInner) list[w++] = g;
+    if (t == 0) A.count[0] = notdone;
 }
 
 // drho_j += (4/h^3) u_n (.) Re x64 for every column j, the groups of orbitals added in wave order.
@@ -722,6 +778,67 @@ void mix(const BArgs &A, void *x, void *r, void *p, const void *q, bool update, 
     else launch_mix<T, 16>(A, x, r, p, q, update, grid, s);
 }
 
+// With rpa_options.profile: CUDA events around every launch of the block path by kind, added up at
+// each synchronisation and reported in rpa_stats.prof_* (times and launches; no point counts).
+struct BTimer {
+    enum { kStencil, kGram, kSmall, kMix, kMaint, kLoadRetire, kKinds };
+    Ctx &c;
+    cudaStream_t st;
+    bool on;
+    std::vector<std::pair<int, size_t>> rec;
+    double ms[kKinds] = {};
+    long long n[kKinds] = {};
+    cudaEvent_t ev(size_t i) {
+        while (c.ev_pool.size() <= i) {
+            cudaEvent_t e;
+            RPA_CUDA(cudaEventCreate(&e));
+            c.ev_pool.push_back(e);
+        }
+        return c.ev_pool[i];
+    }
+    void begin(int kind) {
+        if (!on) return;
+        const size_t i = 2 * rec.size();
+        RPA_CUDA(cudaEventRecord(ev(i), st));
+        rec.push_back({kind, i});
+    }
+    void end() {
+        if (on) RPA_CUDA(cudaEventRecord(ev(rec.back().second + 1), st));
+    }
+    void collect() {   // after a synchronisation of st
+        for (const auto &r : rec) {
+            float t = 0.f;
+            RPA_CUDA(cudaEventElapsedTime(&t, c.ev_pool[r.second], c.ev_pool[r.second + 1]));
+            ms[r.first] += t;
+            n[r.first] += 1;
+        }
+        rec.clear();
+    }
+    void report() {
+        if (!on) return;
+        static const char *names[kKinds] = {"block_stencil", "block_gram", "block_small", "block_mix",
+                                            "block_maintenance", "block_load_retire"};
+        for (int k = 0; k < kKinds; ++k) {
+            if (!n[k]) continue;
+            const int sl = prof_slot(c, names[k]);
+            c.stats.prof_ms[sl] += ms[k];
+            c.stats.prof_launches[sl] += n[k];
+        }
+    }
+};
+
+// Gram launch for groups of up to NB >= sb columns.
+template <typename T>
+void gram_launch(const BArgs &A, const void *X, const void *Y, int norms, int ph, unsigned groups, size_t smem,
+                 cudaStream_t s) {
+    using C = typename BCx<T>::t;
+    const dim3 grid(A.nslot, groups);
+    if (A.sb <= 4) k_bgram<T, 4><<<grid, kBT, smem, s>>>(A, (const C *)X, (const C *)Y, norms, ph);
+    else if (A.sb <= 8) k_bgram<T, 8><<<grid, kBT, smem, s>>>(A, (const C *)X, (const C *)Y, norms, ph);
+    else k_bgram<T, 16><<<grid, kBT, smem, s>>>(A, (const C *)X, (const C *)Y, norms, ph);
+    RPA_LAUNCH("block COCG gram");
+}
+
 template <typename T>
 int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
     using C = typename BCx<T>::t;
@@ -745,6 +862,7 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
     A.nz = c.nz;
     A.periodic = c.opt.periodic;
     A.ntile = (int)((nd + TP - 1) / TP);
+    A.nslot = std::min(A.ntile, kBGramSlots);
     A.nchunk = (int)((nd + kBChunk - 1) / kBChunk);
     A.mixed = mixed;
     A.maxit = c.opt.maxit;
@@ -757,7 +875,7 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
     // storage: b, x64, r64 (FP64), then X, R, P, Q (inner precision), then the small arrays
     const size_t ld = (size_t)sb * sb + sb;
     const size_t bytes = n * (8 + 16 + 16 + 4 * sizeof(C)) + sizeof(BGroup) * W +
-                         sizeof(double2) * ((size_t)W * A.ntile * ld + 2 * (size_t)W * sb * sb) +
+                         sizeof(double2) * ((size_t)W * A.nslot * ld + 2 * (size_t)W * sb * sb) +
                          sizeof(double) * (size_t)W * sb * A.nchunk * 2 + 16 * 256;
     char *base = (char *)c.cocg_state.ensure(bytes);
     size_t off = 0;
@@ -775,24 +893,28 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
     C *pv = (C *)take(sizeof(C) * n);
     C *qv = (C *)take(sizeof(C) * n);
     A.g = (BGroup *)take(sizeof(BGroup) * W);
-    A.gpart = (double2 *)take(sizeof(double2) * (size_t)W * A.ntile * ld);
+    A.gpart = (double2 *)take(sizeof(double2) * (size_t)W * A.nslot * ld);
     A.rho = (double2 *)take(sizeof(double2) * (size_t)W * sb * sb);
     A.coef = take(sizeof(double2) * (size_t)W * sb * sb);
     A.npart = (double *)take(sizeof(double) * (size_t)W * sb * A.nchunk * 2);
     A.count = (int *)take(sizeof(int) * 4);
+    int *alist = (int *)take(sizeof(int) * W);
 
     const size_t gram_smem = 2 * (size_t)sb * (TP + 1) * sizeof(C);
-    allow_dynamic_smem((const void *)k_bgram<T>, gram_smem);
+    allow_dynamic_smem((const void *)k_bgram<T, 4>, gram_smem);
+    allow_dynamic_smem((const void *)k_bgram<T, 8>, gram_smem);
+    allow_dynamic_smem((const void *)k_bgram<T, 16>, gram_smem);
     const T *Vt = mixed ? (const T *)(const void *)c.vloc32 : (const T *)(const void *)c.vloc64;
     const unsigned pblk = (unsigned)((nd + kBT - 1) / kBT);
 
     QueueStats qs{};
     int worst = RPA_OK;
     std::vector<BGroup> h(W);
-    auto read_count = [&]() {
-        RPA_CUDA(cudaMemcpyAsync(c.h_count, A.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BTimer tm{c, st, c.opt.profile != 0};
+    auto read_counts = [&]() {
+        RPA_CUDA(cudaMemcpyAsync(c.h_count, A.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         sync_stream(c, st);
-        return *c.h_count;
+        tm.collect();
     };
     for (int w0 = 0; w0 < total; w0 += W) {
         const int nw = std::min(W, total - w0);
@@ -807,14 +929,20 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             h[i] = g;
         }
         RPA_CUDA(cudaMemcpyAsync(A.g, h.data(), sizeof(BGroup) * nw, cudaMemcpyHostToDevice, st));
-        const dim3 gcols(pblk, nw * sb), ggrp(pblk, nw);
+        const dim3 gcols(pblk, nw * sb);
+        tm.begin(BTimer::kLoadRetire);
         k_bload<<<gcols, kBT, 0, st>>>(A, c.psi64, c.ns, sp.vt, sp.rhs, sp.Tc, sp.sign, b, x64, r64);
         RPA_LAUNCH("block COCG load");
+        tm.end();
         count_launches(1);
-        // Maintenance, then kBCheckEvery inner iterations, until every group is done: a group whose
-        // inner solve ended takes its FP64 residual, stopping test and next inner start at the next
-        // maintenance pass while the others keep iterating.
+        // Maintenance, then kBCheckEvery inner iterations over the groups whose inner solve runs,
+        // until every group is done: a group whose inner solve ended takes its FP64 residual,
+        // stopping test and next inner start at the next maintenance pass while the others keep
+        // iterating.  The inner iterations launch over the list of running groups only.
+        BArgs Ai = A;
+        Ai.alist = alist;
         for (;;) {
+            tm.begin(BTimer::kMaint);
             k_bacc<T><<<gcols, kBT, 0, st>>>(A, xv, x64);
             RPA_LAUNCH("block COCG accumulate");
             k_bresid<<<gcols, kBT, 0, st>>>(A, c.vloc64, b, x64, r64);
@@ -825,31 +953,47 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             RPA_LAUNCH("block COCG check");
             k_bstart<T><<<gcols, kBT, 0, st>>>(A, r64, xv, rv, pv);
             RPA_LAUNCH("block COCG start");
-            k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1, kBStart);
-            RPA_LAUNCH("block COCG gram");
+            gram_launch<T>(A, rv, rv, 1, kBStart, nw, gram_smem, st);
             k_bsmall<T><<<nw, 256, 0, st>>>(A, 0);
             RPA_LAUNCH("block COCG small");
-            count_launches(7);
+            k_blist<<<1, 1024, 0, st>>>(A, alist);
+            RPA_LAUNCH("block COCG list");
+            tm.end();
+            count_launches(8);
+            read_counts();
+            const int notdone = c.h_count[0], running = c.h_count[1];
+            if (notdone == 0) break;
+            if (running == 0) continue;
+            const dim3 icols(pblk, running * sb), igrp(pblk, running);
             for (int it = 0; it < kBCheckEvery; ++it) {
-                k_bstencil<T><<<gcols, kBT, 0, st>>>(A, pv, qv, Vt);
+                tm.begin(BTimer::kStencil);
+                k_bstencil<T><<<icols, kBT, 0, st>>>(Ai, pv, qv, Vt);
                 RPA_LAUNCH("block COCG stencil");
-                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, pv, qv, 0, kBInner);
-                RPA_LAUNCH("block COCG gram");
-                k_bsmall<T><<<nw, 256, 0, st>>>(A, 1);
+                tm.end();
+                tm.begin(BTimer::kGram);
+                gram_launch<T>(Ai, pv, qv, 0, kBInner, running, gram_smem, st);
+                tm.end();
+                tm.begin(BTimer::kSmall);
+                k_bsmall<T><<<running, 256, 0, st>>>(Ai, 1);
                 RPA_LAUNCH("block COCG small");
-                mix<T>(A, xv, rv, pv, qv, true, ggrp, st);
-                k_bgram<T><<<dim3(A.ntile, nw), kBT, gram_smem, st>>>(A, rv, rv, 1, kBInner);
-                RPA_LAUNCH("block COCG gram");
-                k_bsmall<T><<<nw, 256, 0, st>>>(A, 2);
+                tm.end();
+                tm.begin(BTimer::kMix);
+                mix<T>(Ai, xv, rv, pv, qv, true, igrp, st);
+                tm.end();
+                tm.begin(BTimer::kGram);
+                gram_launch<T>(Ai, rv, rv, 1, kBInner, running, gram_smem, st);
+                tm.end();
+                tm.begin(BTimer::kSmall);
+                k_bsmall<T><<<running, 256, 0, st>>>(Ai, 2);
                 RPA_LAUNCH("block COCG small");
-                mix<T>(A, xv, rv, pv, qv, false, ggrp, st);
+                tm.end();
+                tm.begin(BTimer::kMix);
+                mix<T>(Ai, xv, rv, pv, qv, false, igrp, st);
+                tm.end();
                 count_launches(7);
             }
-            k_bcount<<<1, 256, 0, st>>>(A);
-            RPA_LAUNCH("block COCG count");
-            count_launches(1);
-            if (read_count() == 0) break;
         }
+        tm.begin(BTimer::kLoadRetire);
         if (sp.drho) {
             k_bretire_drho<<<dim3(pblk, sp.ncols), kBT, 0, st>>>(A, x64, c.psi64, sp.drho, 4.0 / (c.h * c.h * c.h));
             RPA_LAUNCH("block COCG retire");
@@ -857,9 +1001,11 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             k_bretire_copy<<<gcols, kBT, 0, st>>>(A, x64, sp.xout);
             RPA_LAUNCH("block COCG copy");
         }
+        tm.end();
         count_launches(1);
         RPA_CUDA(cudaMemcpyAsync(h.data(), A.g, sizeof(BGroup) * nw, cudaMemcpyDeviceToHost, st));
         sync_stream(c, st);
+        tm.collect();
         for (int i = 0; i < nw; ++i) {
             const BGroup &g = h[i];
             qs.solves += g.ncol;
@@ -874,6 +1020,7 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
         }
     }
     qs.worst = worst;
+    tm.report();
     return add_queue_stats(c, qs);
 }
 
