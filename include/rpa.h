@@ -279,8 +279,8 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
  * larger requests return RPA_ERR_INVALID with a message and do nothing.  The caller still
  * provides in_dev and out_dev (N_d x ncols, column-major; they may alias).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  The context's device
- * must be the current device.  Like rpa_coulomb_apply, the call synchronises `stream` before
+ * that device current, and later calls reuse it.  The context's device must be the current
+ * device.  Like rpa_coulomb_apply, the call synchronises `stream` before
  * it returns.
  * All calls share the one array and it keeps the last call's contents; every scratch word is
  * written before it is read, so nothing needs clearing.  Calls whose work overlaps on the GPU
