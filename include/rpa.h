@@ -263,6 +263,36 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
                            double *lambdas_host, double *ec_host, double *ec_per_omega_host, rpa_stats *stats,
                            void *stream);
 
+/* Uneven batch: several independent systems, one context each, in one set of launches.
+ *
+ * rpa_apply_nuchi0_batch does for every context k what rpa_apply_nuchi0 does for one: R_dev[k] =
+ * nu^1/2 chi0(i omega) nu^1/2 V_dev[k] (symmetric != 0) or nu chi0 V_dev[k], ncols[k] columns in
+ * [0, 1024] (N_d x ncols[k], column-major, no aliasing).  The Sternheimer systems (Eq. 9) of all the
+ * contexts run together in the block COCG kernels (block size max(1, block_cocg)): one launch per
+ * kernel and iteration for the whole batch, every system with its own grid, operator, orbitals and
+ * stopping rule.  The contexts must be distinct, on one device, with equal prec, tol, inner_tol,
+ * maxit, max_refine and block_cocg, and without precondition or project_solution (else
+ * RPA_ERR_INVALID); the first context's batch_systems and profile apply.  Synchronises `stream`.
+ * Returns the worst per-system status. */
+rpa_status rpa_apply_nuchi0_batch(rpa_ctx *const *ctxs, int n, double omega, const double *const *V_dev,
+                                  double *const *R_dev, const int *ncols, int symmetric, void *stream);
+
+/* rpa_ec for every context k of a batch: n_r[k] trial vectors V0_dev[k], each context with its own
+ * frequencies, subspace iteration and stopping rule (Algorithm 1), and the chi0 applications of
+ * the contexts still iterating run together as in rpa_apply_nuchi0_batch (one host thread per
+ * context drives its subspace iteration; the last to reach its chi0 application runs the batch,
+ * and a context that has finished drops out of later batches).  Outputs per context, each pointer
+ * may be NULL: lambdas_host[k] (n_omega x n_r[k] Ritz values), ec_host[2k] and ec_host[2k + 1]
+ * (E_c and E_c per atom), ec_per_omega_host[k] (n_omega values), stats[k] (the launches and
+ * synchronisations of a batch are counted in
+ * the context whose thread ran it).  Same conditions on the contexts as rpa_apply_nuchi0_batch.
+ * Work starts after what is already queued on `stream`; the call returns when every context is
+ * done.  Returns the worst per-system status; a failure of one context fails the call with that
+ * context's message. */
+rpa_status rpa_ec_batch(rpa_ctx *const *ctxs, int n, const int *n_r, const double *const *V0_dev,
+                        double *const *lambdas_host, double *ec_host, double *const *ec_per_omega_host,
+                        rpa_stats *stats, void *stream);
+
 /* Size of the fixed device scratch array used by rpa_coulomb_apply_noalloc (64 MiB).  Every
  * GPU on which the library is loaded keeps this much memory reserved until the process exits. */
 #define RPA_STATIC_SCRATCH_BYTES (64u << 20)

@@ -1,10 +1,15 @@
 // C entry points of librpa (declared in include/rpa.h) and the subspace-iteration driver of
 // Algorithm 1 (arXiv 2504.01816) with Rayleigh-Ritz energies.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -769,6 +774,219 @@ rpa_status rpa_ec_gradient(rpa_ctx *ctx, int n_r, const double *V0_dev, double *
     if (st != RPA_OK) return st;
     if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
     return (rpa_status)worst;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Several contexts at once (an uneven batch of independent systems)
+// ------------------------------------------------------------------------------------------
+namespace rpa {
+
+// Rendezvous of rpa_ec_batch's threads, one per context: a thread's chi0 application waits until
+// every thread still running has posted one, and the last to arrive runs them all as one batch
+// on its own stream; every thread's stream then waits for the batch before going on.  A thread
+// that finishes (or fails) leaves, and the others no longer wait for it.
+struct BatchCoord {
+    struct Pending {
+        Chi0Request r;
+        cudaEvent_t ready;   // the request's inputs are ready on its thread's stream
+        int *status;
+    };
+    std::mutex m;
+    std::condition_variable cv;
+    int active = 0;
+    long long round = 0;
+    std::vector<Pending> pending;
+    cudaEvent_t done = nullptr;    // recorded after each batch
+    bool failed = false;
+    rpa_status fail_status = RPA_OK;
+    std::string fail_msg;
+
+    void run(cudaStream_t s, const Ctx *runner) {   // m held
+        try {
+            // the runner's own request first: its context lends the workspaces and counts the syncs
+            std::stable_partition(pending.begin(), pending.end(), [&](const Pending &p) { return p.r.c == runner; });
+            std::vector<Chi0Request> reqs;
+            for (const Pending &p : pending) {
+                RPA_CUDA(cudaStreamWaitEvent(s, p.ready, 0));
+                reqs.push_back(p.r);
+            }
+            std::vector<int> st;
+            chi0_apply_batch(reqs, s, &st);
+            RPA_CUDA(cudaEventRecord(done, s));
+            for (size_t k = 0; k < pending.size(); ++k) *pending[k].status = st[k];
+            pending.clear();
+            ++round;
+        } catch (const Error &e) {
+            failed = true;
+            fail_status = e.status;
+            fail_msg = e.msg;
+        }
+        cv.notify_all();
+    }
+
+    int apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+        cudaEvent_t ready;
+        RPA_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        RPA_CUDA(cudaEventRecord(ready, s));
+        int st = RPA_OK;
+        std::unique_lock<std::mutex> lk(m);
+        if (!failed) {
+            pending.push_back({Chi0Request{&c, omega, dv, drho, ncols}, ready, &st});
+            const long long my = round;
+            if ((int)pending.size() == active) run(s, &c);
+            else cv.wait(lk, [&] { return round > my || failed; });
+        }
+        cudaEventDestroy(ready);
+        if (failed) fail(fail_status, "%s", fail_msg.c_str());
+        RPA_CUDA(cudaStreamWaitEvent(s, done, 0));
+        return st;
+    }
+
+    void leave(cudaStream_t s, const Ctx *c) {
+        std::unique_lock<std::mutex> lk(m);
+        --active;
+        if (active > 0 && !failed && !pending.empty() && (int)pending.size() == active) run(s, c);
+        cv.notify_all();
+    }
+};
+
+int batch_chi0(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    return c.coord->apply(c, omega, dv, drho, ncols, s);
+}
+
+namespace {
+
+// The contexts of a batch: distinct, on one device, with the same precision and COCG settings
+// (the batch runs them with the first one's), and without the options the batch does not run.
+void check_batch(rpa_ctx *const *ctxs, int n) {
+    if (!ctxs || n < 1) fail(RPA_ERR_INVALID, "a batch needs n >= 1 contexts");
+    for (int k = 0; k < n; ++k)
+        if (!ctxs[k]) fail(RPA_ERR_INVALID, "NULL context %d", k);
+    const Ctx &c0 = ctxs[0]->impl;
+    for (int k = 0; k < n; ++k) {
+        const Ctx &c = ctxs[k]->impl;
+        for (int q = 0; q < k; ++q)
+            if (ctxs[q] == ctxs[k]) fail(RPA_ERR_INVALID, "context %d appears twice in the batch", k);
+        if (c.device != c0.device) fail(RPA_ERR_INVALID, "the contexts of a batch must be on one device");
+        if (c.opt.prec != c0.opt.prec || c.opt.tol != c0.opt.tol || c.opt.inner_tol != c0.opt.inner_tol ||
+            c.opt.maxit != c0.opt.maxit || c.opt.max_refine != c0.opt.max_refine ||
+            c.opt.block_cocg != c0.opt.block_cocg)
+            fail(RPA_ERR_INVALID,
+                 "the contexts of a batch need equal prec, tol, inner_tol, maxit, max_refine and block_cocg");
+        if (c.opt.precondition || c.opt.project_solution)
+            fail(RPA_ERR_INVALID, "a batch runs without precondition and project_solution");
+        if (c.coord) fail(RPA_ERR_INVALID, "context %d is already in a running batch", k);
+    }
+}
+
+}  // namespace
+}  // namespace rpa
+
+extern "C" {
+
+rpa_status rpa_apply_nuchi0_batch(rpa_ctx *const *ctxs, int n, double omega, const double *const *V_dev,
+                                  double *const *R_dev, const int *ncols, int symmetric, void *stream) {
+    int worst = 0;
+    rpa_status st = guarded([&] {
+        check_batch(ctxs, n);
+        if (!V_dev || !R_dev || !ncols) fail(RPA_ERR_INVALID, "NULL argument");
+        if (!std::isfinite(omega)) fail(RPA_ERR_INVALID, "omega must be finite");
+        cudaStream_t s = as_stream(stream);
+        std::vector<Chi0Request> reqs;
+        std::vector<int> who;
+        for (int k = 0; k < n; ++k) {
+            Ctx &c = ctxs[k]->impl;
+            if (ncols[k] < 0 || ncols[k] > 1024) fail(RPA_ERR_INVALID, "ncols[%d] must be in [0, 1024]", k);
+            if (ncols[k] == 0) continue;
+            if (!V_dev[k] || !R_dev[k]) fail(RPA_ERR_INVALID, "NULL argument (context %d)", k);
+            if (V_dev[k] == R_dev[k]) fail(RPA_ERR_INVALID, "V and R must not alias (context %d)", k);
+            const size_t blk = sizeof(double) * (size_t)ncols[k] * c.nd;
+            double *t1 = (double *)c.blockA.ensure(blk);
+            double *t2 = (double *)c.blockB.ensure(blk);
+            const double *dv = V_dev[k];
+            if (symmetric) {
+                coulomb_apply(c, 0.5, V_dev[k], t1, ncols[k], s, use_tensor_cores_kronecker(c));
+                dv = t1;
+            }
+            reqs.push_back(Chi0Request{&c, omega, dv, t2, ncols[k]});
+            who.push_back(k);
+        }
+        worst = chi0_apply_batch(reqs, s);
+        for (size_t q = 0; q < reqs.size(); ++q) {
+            const int k = who[q];
+            Ctx &c = ctxs[k]->impl;
+            coulomb_apply(c, symmetric ? 0.5 : 1.0, reqs[q].drho, R_dev[k], ncols[k], s, use_tensor_cores_kronecker(c));
+        }
+        RPA_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st != RPA_OK) return st;
+    if (worst != RPA_OK) g_last_error = "a Sternheimer system did not converge";
+    return (rpa_status)worst;
+}
+
+rpa_status rpa_ec_batch(rpa_ctx *const *ctxs, int n, const int *n_r, const double *const *V0_dev,
+                        double *const *lambdas_host, double *ec_host, double *const *ec_per_omega_host,
+                        rpa_stats *stats, void *stream) {
+    std::vector<int> worst(n > 0 ? n : 0, 0);
+    rpa_status st = guarded([&] {
+        check_batch(ctxs, n);
+        if (!n_r || !V0_dev) fail(RPA_ERR_INVALID, "NULL argument");
+        for (int k = 0; k < n; ++k)
+            if (!V0_dev[k]) fail(RPA_ERR_INVALID, "NULL argument (context %d)", k);
+        BatchCoord coord;
+        coord.active = n;
+        cudaEvent_t start;
+        RPA_CUDA(cudaEventCreateWithFlags(&coord.done, cudaEventDisableTiming));
+        RPA_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+        RPA_CUDA(cudaEventRecord(start, as_stream(stream)));   // V0 is ready on the caller's stream
+        std::vector<rpa_status> sts(n, RPA_OK);
+        std::vector<std::string> msgs(n);
+        for (int k = 0; k < n; ++k) ctxs[k]->impl.coord = &coord;
+        const int dev = ctxs[0]->impl.device;
+        std::vector<std::thread> threads;
+        for (int k = 0; k < n; ++k)
+            threads.emplace_back([&, k] {
+                Ctx &c = ctxs[k]->impl;
+                cudaStream_t s = nullptr;
+                try {
+                    RPA_CUDA(cudaSetDevice(dev));
+                    RPA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+                    RPA_CUDA(cudaStreamWaitEvent(s, start, 0));
+                    double e2[2] = {0.0, 0.0};
+                    worst[k] = ec_impl(c, n_r[k], V0_dev[k], lambdas_host ? lambdas_host[k] : nullptr, e2,
+                                       ec_per_omega_host ? ec_per_omega_host[k] : nullptr,
+                                       stats ? stats + k : nullptr, s, nullptr, nullptr);
+                    if (ec_host) {
+                        ec_host[2 * k] = e2[0];
+                        ec_host[2 * k + 1] = e2[1];
+                    }
+                } catch (const Error &e) {
+                    sts[k] = e.status;
+                    msgs[k] = e.msg;
+                } catch (...) {
+                    sts[k] = RPA_ERR_INVALID;
+                    msgs[k] = "unexpected internal error";
+                }
+                coord.leave(s, &c);
+                if (s) {
+                    cudaStreamSynchronize(s);
+                    cudaStreamDestroy(s);
+                }
+            });
+        for (std::thread &t : threads) t.join();
+        for (int k = 0; k < n; ++k) ctxs[k]->impl.coord = nullptr;
+        cudaEventDestroy(coord.done);
+        cudaEventDestroy(start);
+        for (int k = 0; k < n; ++k)
+            if (sts[k] != RPA_OK) fail(sts[k], "context %d: %s", k, msgs[k].c_str());
+    });
+    if (st != RPA_OK) return st;
+    int w = 0;
+    for (int v : worst) w = std::max(w, v);
+    if (w != RPA_OK) g_last_error = "a Sternheimer system did not converge";
+    return (rpa_status)w;
 }
 
 }  // extern "C"

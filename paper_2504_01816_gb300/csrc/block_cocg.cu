@@ -53,9 +53,29 @@ template <> struct BCx<double> { using t = double2; };
 template <typename T> struct BTile { static constexpr int v = 256; };
 template <> struct BTile<double> { static constexpr int v = 128; };
 
-// One group: the columns row0 .. row0 + ncol - 1 of orbital n (systems sys0 ..).
+// One system (context) of a call: its grid, operator, orbitals and where its right-hand sides come
+// from and its solutions go.  A call may hold several (the uneven batch), one table entry each.
+struct BSys {
+    long long nd;
+    int nx, ny, nz, periodic;
+    int ntile, nslot;              // Gram tiles, and Gram blocks per group (each sums every nslot-th tile)
+    int ns;
+    double a[kRadius + 1];         // stencil coefficients
+    const double *V64;
+    const float *V32;
+    const double *psi;             // ns x nd orbitals
+    const double *vt, *rhs, *Tc;   // right-hand sides: u_n (.) vt_row or rhs_row, P_c coefficients
+    double sign;
+    double *drho;                  // retire: drho_row += scale u_n (.) Re x (or nullptr) ...
+    double scale;
+    double2 *xout;                 // ... or x_out[sys] = x
+};
+
+// One group: the columns row0 .. row0 + ncol - 1 of orbital n (systems sys0 ..) of system ctx;
+// column c of its vectors starts at element off + c nd.
 struct BGroup {
-    int n, ncol, sys0, row0;
+    int n, ncol, sys0, row0, ctx;
+    long long off;
     int phase, status, iters, refines, nearb, discard, nin, inner_iters;
     int nonfinite;
     int cap;                       // most columns an inner solve takes (halved at a near-breakdown)
@@ -70,16 +90,12 @@ struct BGroup {
 
 struct BArgs {
     BGroup *g;
-    int ngroups, sb;               // groups in flight, columns per group in the vector storage
-    long long nd;
-    int nx, ny, nz, periodic;
-    int ntile;                     // Gram tiles per group
-    int nslot;                     // Gram partial sums per group (blocks per group of a Gram launch)
-    int nchunk;                    // norm work items per column
+    const BSys *sys;
+    int ngroups, sb;               // groups in flight, columns per group
+    int nchunk;                    // norm work items per column (of the largest system)
     int mixed, maxit, max_refine;
     double tol, inner_tol, piv_tol;
-    double a[kRadius + 1];         // stencil coefficients
-    double2 *gpart;                // [group][nslot][sb*sb + sb] Gram partial sums; norms in .x of the tail
+    double2 *gpart;                // [group][kBGramSlots][sb*sb + sb] Gram partial sums; norms in .x of the tail
     double2 *rho;                  // [group][nin*nin]
     void *coef;                    // [group][nin*nin] alpha, then beta (complex T)
     double *npart;                 // [group*sb + c][nchunk][2] ||r64_c||^2, ||b_c||^2
@@ -162,21 +178,20 @@ __device__ __forceinline__ void bblock_sum2(double &a, double &b) {
 
 // b = sign * (base - sum_k Tc[sys][k] u_k), base = u_n (.) vt_row (pairs) or rhs_row; x64 = 0,
 // r64 = b.  Grid: (points / 256, groups * sb).
-__global__ void __launch_bounds__(kBT) k_bload(BArgs A, const double *__restrict__ psi, int ns,
-                                               const double *__restrict__ vt, const double *__restrict__ rhs,
-                                               const double *__restrict__ Tc, double sign, double *__restrict__ b,
-                                               double2 *__restrict__ x64, double2 *__restrict__ r64) {
+__global__ void __launch_bounds__(kBT) k_bload(BArgs A, double *__restrict__ b, double2 *__restrict__ x64,
+                                               double2 *__restrict__ r64) {
     const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
+    const BSys &S = A.sys[G.ctx];
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (c >= G.ncol || idx >= A.nd) return;
+    if (c >= G.ncol || idx >= S.nd) return;
     const int row = G.row0 + c, sys = G.sys0 + c;
-    double base = vt ? psi[(long long)G.n * A.nd + idx] * vt[(long long)row * A.nd + idx]
-                     : rhs[(long long)row * A.nd + idx];
-    if (Tc)
-        for (int k = 0; k < ns; ++k) base -= Tc[(long long)sys * ns + k] * psi[(long long)k * A.nd + idx];
-    const double bv = sign * base;
-    const long long o = ((long long)gi * A.sb + c) * A.nd + idx;
+    double base = S.vt ? S.psi[(long long)G.n * S.nd + idx] * S.vt[(long long)row * S.nd + idx]
+                       : S.rhs[(long long)row * S.nd + idx];
+    if (S.Tc)
+        for (int k = 0; k < S.ns; ++k) base -= S.Tc[(long long)sys * S.ns + k] * S.psi[(long long)k * S.nd + idx];
+    const double bv = S.sign * base;
+    const long long o = G.off + (long long)c * S.nd + idx;
     b[o] = bv;
     x64[o] = make_double2(0.0, 0.0);
     r64[o] = make_double2(bv, 0.0);
@@ -189,11 +204,12 @@ __global__ void __launch_bounds__(kBT) k_bnorm(BArgs A, const double *__restrict
     const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
     if (c >= G.ncol || (G.phase != kBInnerDone && G.phase != kBCheck)) return;
-    const long long o = ((long long)gi * A.sb + c) * A.nd;
+    const long long nd = A.sys[G.ctx].nd;
+    const long long o = G.off + (long long)c * nd;
     double rr = 0.0, bb = 0.0;
     for (int t = 0; t < kBChunk / kBT; ++t) {
         const long long idx = (long long)blockIdx.x * kBChunk + t * kBT + threadIdx.x;
-        if (idx < A.nd) {
+        if (idx < nd) {
             const double2 r = r64[o + idx];
             const double bv = b[o + idx];
             rr += r.x * r.x + r.y * r.y;
@@ -278,11 +294,12 @@ __global__ void __launch_bounds__(kBT) k_bstart(BArgs A, const double2 *__restri
     using C = typename BCx<T>::t;
     const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
+    const long long nd = A.sys[G.ctx].nd;
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (G.phase != kBStart || ci >= G.nin || idx >= A.nd) return;
+    if (G.phase != kBStart || ci >= G.nin || idx >= nd) return;
     const double inv = 1.0 / G.scl[ci];
-    const double2 v = r64[((long long)gi * A.sb + G.cmap[ci]) * A.nd + idx];
-    const long long o = ((long long)gi * A.sb + ci) * A.nd + idx;
+    const double2 v = r64[G.off + (long long)G.cmap[ci] * nd + idx];
+    const long long o = G.off + (long long)ci * nd + idx;
     C rv, z;
     rv.x = (T)(v.x * inv);
     rv.y = (T)(v.y * inv);
@@ -293,28 +310,35 @@ __global__ void __launch_bounds__(kBT) k_bstart(BArgs A, const double2 *__restri
     p[o] = rv;
 }
 
+template <typename T> __device__ __forceinline__ const T *bsys_v(const BSys &S);
+template <> __device__ __forceinline__ const float *bsys_v<float>(const BSys &S) { return S.V32; }
+template <> __device__ __forceinline__ const double *bsys_v<double>(const BSys &S) { return S.V64; }
+
 // out = (H + sigma) in on the inner columns (T = the inner precision).
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_bstencil(BArgs A, const typename BCx<T>::t *__restrict__ in,
-                                                  typename BCx<T>::t *__restrict__ out, const T *__restrict__ V) {
+                                                  typename BCx<T>::t *__restrict__ out) {
     const int gi = group_of(A, blockIdx.y / A.sb), ci = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
+    const BSys &S = A.sys[G.ctx];
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (G.phase != kBInner || ci >= G.nin || idx >= A.nd) return;
+    if (G.phase != kBInner || ci >= G.nin || idx >= S.nd) return;
     T a[kRadius + 1];
 #pragma unroll
-    for (int k = 0; k <= kRadius; ++k) a[k] = (T)A.a[k];
-    const long long o = ((long long)gi * A.sb + ci) * A.nd;
-    out[o + idx] = bstencil_at<T>(in + o, V, (int)idx, A.nx, A.ny, A.nz, A.periodic, a, (T)G.sre, (T)G.sim);
+    for (int k = 0; k <= kRadius; ++k) a[k] = (T)S.a[k];
+    const long long o = G.off + (long long)ci * S.nd;
+    out[o + idx] = bstencil_at<T>(in + o, bsys_v<T>(S), (int)idx, S.nx, S.ny, S.nz, S.periodic, a, (T)G.sre,
+                                  (T)G.sim);
 }
 
 // Gram partial sums: G_ij = sum_t X_i(t) Y_j(t) (unconjugated), and with norms != 0 also ||X_i||^2,
-// over the tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the group's points.  A tile of TP
+// over the tiles blockIdx.x, blockIdx.x + nslot, ... of the group's points (blocks past the
+// system's nslot have nothing to do).  A tile of TP
 // points of the n rows is staged in shared memory (once when X and Y are the same block), and the
 // next tile's values are loaded into registers while the current one is summed.  Thread (e, sub)
 // adds every nsub-th point of a tile for entry e = (i, j), in T within a tile and in FP64 across
-// tiles; the nsub sums of an entry are added in order.  Grid: (nslot, groups); the partial sums of
-// slot blockIdx.x go to gpart[group][blockIdx.x].
+// tiles; the nsub sums of an entry are added in order.  Grid: (kBGramSlots or fewer, groups); the
+// partial sums of slot blockIdx.x go to gpart[group][blockIdx.x].
 template <typename T, int NB>
 __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t *__restrict__ X,
                                                const typename BCx<T>::t *__restrict__ Y, int norms, int ph) {
@@ -328,10 +352,11 @@ __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t
     __shared__ double redn[kBT];
     const int gi = group_of(A, blockIdx.y);
     const BGroup &G = A.g[gi];
-    if (G.phase != ph) return;
+    const BSys &S = A.sys[G.ctx];
+    if (G.phase != ph || (int)blockIdx.x >= S.nslot) return;
     const bool same = X == Y;
     const int n = G.nin, E = n * n, tid = threadIdx.x;
-    const long long gbase = (long long)gi * A.sb * A.nd;
+    const long long gbase = G.off, nd = S.nd;
     C xr[LPT], yr[LPT];
     auto fetch = [&](int tile) {
         const long long p0 = (long long)tile * TP;
@@ -342,8 +367,8 @@ __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t
             yr[l] = xr[l];
             if (e < n * TP) {
                 const int c = e / TP, t = e % TP;
-                if (p0 + t < A.nd) {
-                    const long long o = gbase + (long long)c * A.nd + p0 + t;
+                if (p0 + t < nd) {
+                    const long long o = gbase + (long long)c * nd + p0 + t;
                     xr[l] = X[o];
                     if (!same) yr[l] = Y[o];
                 }
@@ -356,8 +381,8 @@ __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t
     const C *ys = same ? sx : sy;
     double sr = 0.0, si = 0.0, sn = 0.0;
     int tile = blockIdx.x;
-    if (tile < A.ntile) fetch(tile);
-    for (; tile < A.ntile; tile += gridDim.x) {
+    if (tile < S.ntile) fetch(tile);
+    for (; tile < S.ntile; tile += S.nslot) {
         __syncthreads();                          // the previous tile has been summed
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
@@ -369,8 +394,8 @@ __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t
             }
         }
         __syncthreads();
-        const int len = (int)min((long long)TP, A.nd - (long long)tile * TP);
-        if (tile + (int)gridDim.x < A.ntile) fetch(tile + gridDim.x);
+        const int len = (int)min((long long)TP, nd - (long long)tile * TP);
+        if (tile + S.nslot < S.ntile) fetch(tile + S.nslot);
         if (active) {
             T ar = 0, ai = 0, an = 0;
             for (int t = sub; t < len; t += nsub) {
@@ -396,7 +421,7 @@ __global__ void __launch_bounds__(kBT) k_bgram(BArgs A, const typename BCx<T>::t
         }
         const int ii = tid / n, jj = tid % n;
         const int ld = A.sb * A.sb + A.sb;
-        double2 *o = A.gpart + ((long long)gi * A.nslot + blockIdx.x) * ld;
+        double2 *o = A.gpart + ((long long)gi * kBGramSlots + blockIdx.x) * ld;
         o[ii * A.sb + jj] = make_double2(tr, ti);
         if (norms && ii == jj) o[A.sb * A.sb + ii] = make_double2(tn, 0.0);
     }
@@ -429,12 +454,12 @@ __global__ void __launch_bounds__(256) k_bsmall(BArgs A, int mode) {
     const int gi = group_of(A, blockIdx.x), tid = threadIdx.x;
     BGroup &G = A.g[gi];
     if (G.phase != (mode == 0 ? kBStart : kBInner)) return;
-    const int n = G.nin, E = n * n, ld = A.sb * A.sb + A.sb;
+    const int n = G.nin, E = n * n, ld = A.sb * A.sb + A.sb, nslot = A.sys[G.ctx].nslot;
     for (int e = tid; e < E + n; e += blockDim.x) {
         const int off = e < E ? (e / n) * A.sb + e % n : A.sb * A.sb + (e - E);
-        const double2 *q = A.gpart + (long long)gi * A.nslot * ld + off;
+        const double2 *q = A.gpart + (long long)gi * kBGramSlots * ld + off;
         double sr = 0.0, si = 0.0;
-        for (int t = 0; t < A.nslot; ++t) {
+        for (int t = 0; t < nslot; ++t) {
             const double2 v = q[(long long)t * ld];
             sr += v.x;
             si += v.y;
@@ -602,17 +627,18 @@ __global__ void __launch_bounds__(kBT) k_bmix(BArgs A, typename BCx<T>::t *__res
         cf[e] = v;
     }
     __syncthreads();
+    const long long nd = A.sys[G.ctx].nd;
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (idx >= A.nd) return;
-    const long long base = (long long)gi * A.sb * A.nd + idx;
+    if (idx >= nd) return;
+    const long long base = G.off + idx;
     C pk[NB], qk[NB];
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         pk[k].x = pk[k].y = (T)0;
         qk[k] = pk[k];
         if (k < n) {
-            pk[k] = p[base + (long long)k * A.nd];
-            if (UPDATE) qk[k] = q[base + (long long)k * A.nd];
+            pk[k] = p[base + (long long)k * nd];
+            if (UPDATE) qk[k] = q[base + (long long)k * nd];
         }
     }
 #pragma unroll
@@ -629,7 +655,7 @@ __global__ void __launch_bounds__(kBT) k_bmix(BArgs A, typename BCx<T>::t *__res
                     vi += qk[k].x * a.y + qk[k].y * a.x;
                 }
             }
-            const long long o = base + (long long)j * A.nd;
+            const long long o = base + (long long)j * nd;
             C rv = r[o];
             if (UPDATE) {
                 C xv = x[o];
@@ -655,27 +681,29 @@ __global__ void __launch_bounds__(kBT) k_bacc(BArgs A, const typename BCx<T>::t 
                                               double2 *__restrict__ x64) {
     const int gi = blockIdx.y / A.sb, ci = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
+    const long long nd = A.sys[G.ctx].nd;
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (G.phase != kBInnerDone || G.discard || ci >= G.nin || idx >= A.nd) return;
+    if (G.phase != kBInnerDone || G.discard || ci >= G.nin || idx >= nd) return;
     const double s = G.scl[ci];
-    const typename BCx<T>::t d = x[((long long)gi * A.sb + ci) * A.nd + idx];
-    double2 &o = x64[((long long)gi * A.sb + G.cmap[ci]) * A.nd + idx];
+    const typename BCx<T>::t d = x[G.off + (long long)ci * nd + idx];
+    double2 &o = x64[G.off + (long long)G.cmap[ci] * nd + idx];
     o.x += s * (double)d.x;
     o.y += s * (double)d.y;
 }
 
 // r64 = b - (H + sigma) x64 in FP64 on every column of the groups whose inner solve ended.
-__global__ void __launch_bounds__(kBT) k_bresid(BArgs A, const double *__restrict__ V, const double *__restrict__ b,
+__global__ void __launch_bounds__(kBT) k_bresid(BArgs A, const double *__restrict__ b,
                                                 const double2 *__restrict__ x64, double2 *__restrict__ r64) {
     const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
+    const BSys &S = A.sys[G.ctx];
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (G.phase != kBInnerDone || c >= G.ncol || idx >= A.nd) return;
+    if (G.phase != kBInnerDone || c >= G.ncol || idx >= S.nd) return;
     double a[kRadius + 1];
 #pragma unroll
-    for (int k = 0; k <= kRadius; ++k) a[k] = A.a[k];
-    const long long o = ((long long)gi * A.sb + c) * A.nd;
-    const double2 ax = bstencil_at<double>(x64 + o, V, (int)idx, A.nx, A.ny, A.nz, A.periodic, a, G.sre, G.sim);
+    for (int k = 0; k <= kRadius; ++k) a[k] = S.a[k];
+    const long long o = G.off + (long long)c * S.nd;
+    const double2 ax = bstencil_at<double>(x64 + o, S.V64, (int)idx, S.nx, S.ny, S.nz, S.periodic, a, G.sre, G.sim);
     r64[o + idx] = make_double2(b[o + idx] - ax.x, -ax.y);
 }
 
@@ -713,32 +741,34 @@ __global__ void __launch_bounds__(1024) k_blist(BArgs A, int *__restrict__ list)
     if (t == 0) A.count[0] = notdone;
 }
 
-// drho_j += (4/h^3) u_n (.) Re x64 for every column j, the groups of orbitals added in wave order.
-// Grid: (points / 256, ncols).
-__global__ void __launch_bounds__(kBT) k_bretire_drho(BArgs A, const double2 *__restrict__ x64,
-                                                      const double *__restrict__ psi, double *__restrict__ drho,
-                                                      double scale) {
-    const int j = blockIdx.y;
+// drho_j += (4/h^3) u_n (.) Re x64 for every row (system ctx, column j) of rows, the groups of
+// that system's orbitals added in group order.  Grid: (points / 256, rows).
+__global__ void __launch_bounds__(kBT) k_bretire_drho(BArgs A, const int2 *__restrict__ rows,
+                                                      const double2 *__restrict__ x64) {
+    const int2 rj = rows[blockIdx.y];
+    const BSys &S = A.sys[rj.x];
+    const int j = rj.y;
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (idx >= A.nd) return;
-    double acc = drho[(long long)j * A.nd + idx];
+    if (idx >= S.nd) return;
+    double acc = S.drho[(long long)j * S.nd + idx];
     for (int gi = 0; gi < A.ngroups; ++gi) {
         const BGroup &G = A.g[gi];
         const int c = j - G.row0;
-        if (c < 0 || c >= G.ncol) continue;
-        acc += scale * psi[(long long)G.n * A.nd + idx] * x64[((long long)gi * A.sb + c) * A.nd + idx].x;
+        if (G.ctx != rj.x || c < 0 || c >= G.ncol) continue;
+        acc += S.scale * S.psi[(long long)G.n * S.nd + idx] * x64[G.off + (long long)c * S.nd + idx].x;
     }
-    drho[(long long)j * A.nd + idx] = acc;
+    S.drho[(long long)j * S.nd + idx] = acc;
 }
 
-// x_out[sys] = x64 for every column.  Grid: (points / 256, groups * sb).
-__global__ void __launch_bounds__(kBT) k_bretire_copy(BArgs A, const double2 *__restrict__ x64,
-                                                      double2 *__restrict__ xout) {
+// x_out[sys] = x64 for every column of the systems that copy their solutions out.
+// Grid: (points / 256, groups * sb).
+__global__ void __launch_bounds__(kBT) k_bretire_copy(BArgs A, const double2 *__restrict__ x64) {
     const int gi = blockIdx.y / A.sb, c = blockIdx.y % A.sb;
     const BGroup &G = A.g[gi];
+    const BSys &S = A.sys[G.ctx];
     const long long idx = (long long)blockIdx.x * kBT + threadIdx.x;
-    if (c >= G.ncol || idx >= A.nd) return;
-    xout[(long long)(G.sys0 + c) * A.nd + idx] = x64[((long long)gi * A.sb + c) * A.nd + idx];
+    if (!S.xout || c >= G.ncol || idx >= S.nd) return;
+    S.xout[(long long)(G.sys0 + c) * S.nd + idx] = x64[G.off + (long long)c * S.nd + idx];
 }
 
 // rows[j] = u_n (.) dv_j for j < ncols (right-hand sides of orbital n before the projection).
@@ -749,7 +779,10 @@ __global__ void k_bpair_rows(const double *__restrict__ psi, const double *__res
         rows[(long long)j * nd + i] = psi[(long long)n * nd + i] * dv[(long long)j * nd + i];
 }
 
+// One system's share of a call: its context, where its right-hand sides come from, where its
+// solutions go, and its groups.
 struct BSpec {
+    Ctx *c = nullptr;
     const double *vt = nullptr;     // pair right-hand sides u_n (.) vt_row ...
     const double *rhs = nullptr;    // ... or rows of rhs
     const double *Tc = nullptr;     // P_c coefficients per system (or nullptr)
@@ -827,57 +860,128 @@ struct BTimer {
     }
 };
 
-// Gram launch for groups of up to NB >= sb columns.
+// Gram launch for groups of up to NB >= sb columns; gx blocks per group (the largest nslot).
 template <typename T>
-void gram_launch(const BArgs &A, const void *X, const void *Y, int norms, int ph, unsigned groups, size_t smem,
-                 cudaStream_t s) {
+void gram_launch(const BArgs &A, const void *X, const void *Y, int norms, int ph, int gx, unsigned groups,
+                 size_t smem, cudaStream_t s) {
     using C = typename BCx<T>::t;
-    const dim3 grid(A.nslot, groups);
+    const dim3 grid(gx, groups);
     if (A.sb <= 4) k_bgram<T, 4><<<grid, kBT, smem, s>>>(A, (const C *)X, (const C *)Y, norms, ph);
     else if (A.sb <= 8) k_bgram<T, 8><<<grid, kBT, smem, s>>>(A, (const C *)X, (const C *)Y, norms, ph);
     else k_bgram<T, 16><<<grid, kBT, smem, s>>>(A, (const C *)X, (const C *)Y, norms, ph);
     RPA_LAUNCH("block COCG gram");
 }
 
+// The block solves of every group of every system in specs, with the iteration settings and the
+// workspaces of `lead` (all systems share its precision, tolerances and block size).  Groups are
+// taken in waves (in spec order, then group order) as far as the vector budget allows.
 template <typename T>
-int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out, std::vector<int> *status_out) {
+int run_block_t(Ctx &lead, std::vector<BSpec *> &specs, cudaStream_t st, std::vector<int> *iters_out,
+                std::vector<int> *status_out, std::vector<int> *spec_worst) {
     using C = typename BCx<T>::t;
     constexpr int TP = BTile<T>::v;
-    const bool mixed = c.opt.prec == RPA_MIXED;
-    const int sb = c.opt.block_cocg;
-    const long long nd = c.nd;
-    const int total = (int)sp.groups.size();
+    const bool mixed = lead.opt.prec == RPA_MIXED;
+    const int sb = lead.opt.block_cocg > 0 ? lead.opt.block_cocg : 1;
+    const int nspec = (int)specs.size();
+
+    // the system table (host copy)
+    std::vector<BSys> sys(nspec);
+    long long nd_max = 0;
+    for (int k = 0; k < nspec; ++k) {
+        const BSpec &sp = *specs[k];
+        const Ctx &c = *sp.c;
+        BSys &S = sys[k];
+        S = BSys{};
+        S.nd = c.nd;
+        S.nx = c.nx;
+        S.ny = c.ny;
+        S.nz = c.nz;
+        S.periodic = c.opt.periodic;
+        S.ntile = (int)((c.nd + TP - 1) / TP);
+        S.nslot = std::min(S.ntile, kBGramSlots);
+        S.ns = c.ns;
+        for (int q = 0; q <= kRadius; ++q) S.a[q] = c.coef.a[q];
+        S.V64 = c.vloc64;
+        S.V32 = c.vloc32;
+        S.psi = c.psi64;
+        S.vt = sp.vt;
+        S.rhs = sp.rhs;
+        S.Tc = sp.Tc;
+        S.sign = sp.sign;
+        S.drho = sp.drho;
+        S.scale = 4.0 / (c.h * c.h * c.h);
+        S.xout = sp.xout;
+        nd_max = std::max(nd_max, c.nd);
+    }
+    // all groups, and the waves: consecutive groups whose vectors fit the budget
+    std::vector<BGroup> all;
+    for (int k = 0; k < nspec; ++k)
+        for (BGroup g : specs[k]->groups) {
+            g.ctx = k;
+            g.cap = g.ncol;
+            g.phase = kBCheck;
+            g.status = RPA_OK;
+            g.sre = -specs[k]->c->eps[g.n];
+            g.sim = specs[k]->omega;
+            all.push_back(g);
+        }
+    const int total = (int)all.size();
     if (total == 0) return RPA_OK;
-    const double per_group = (double)sb * nd * (8.0 + 16.0 + 16.0 + 4.0 * sizeof(C));
-    int W = (int)std::max(1.0, std::min((double)total, std::floor(kBBudget / per_group)));
-    W = std::min(W, 65535 / sb);
-    if (c.opt.batch_systems > 0) W = std::min(W, std::max(1, c.opt.batch_systems / sb));
-    const size_t n = (size_t)W * sb * nd;
+    const double per_point = 8.0 + 16.0 + 16.0 + 4.0 * sizeof(C);
+    int wmax = 65535 / sb;
+    if (lead.opt.batch_systems > 0) wmax = std::min(wmax, std::max(1, lead.opt.batch_systems / sb));
+    std::vector<int> wave_start{0};
+    std::vector<long long> wave_elems;
+    {
+        long long elems = 0;
+        int count = 0;
+        for (int i = 0; i < total; ++i) {
+            const long long e = (long long)sb * sys[all[i].ctx].nd;
+            if (count > 0 && (count >= wmax || (elems + e) * per_point > kBBudget)) {
+                wave_start.push_back(i);
+                wave_elems.push_back(elems);
+                elems = 0;
+                count = 0;
+            }
+            all[i].off = elems;
+            elems += e;
+            ++count;
+        }
+        wave_start.push_back(total);
+        wave_elems.push_back(elems);
+    }
+    int W = 0;
+    long long n = 0;
+    for (size_t w = 0; w + 1 < wave_start.size(); ++w) {
+        W = std::max(W, wave_start[w + 1] - wave_start[w]);
+        n = std::max(n, wave_elems[w]);
+    }
+    // drho rows (system, column) of the systems that retire into drho
+    std::vector<int2> rows;
+    for (int k = 0; k < nspec; ++k)
+        if (specs[k]->drho)
+            for (int j = 0; j < specs[k]->ncols; ++j) rows.push_back(make_int2(k, j));
+    if (rows.size() > 65535) fail(RPA_ERR_INVALID, "block COCG: more than 65535 columns in one call");
 
     BArgs A{};
     A.sb = sb;
-    A.nd = nd;
-    A.nx = c.nx;
-    A.ny = c.ny;
-    A.nz = c.nz;
-    A.periodic = c.opt.periodic;
-    A.ntile = (int)((nd + TP - 1) / TP);
-    A.nslot = std::min(A.ntile, kBGramSlots);
-    A.nchunk = (int)((nd + kBChunk - 1) / kBChunk);
+    A.nchunk = (int)((nd_max + kBChunk - 1) / kBChunk);
     A.mixed = mixed;
-    A.maxit = c.opt.maxit;
-    A.max_refine = c.opt.max_refine;
-    A.tol = c.opt.tol;
-    A.inner_tol = c.opt.inner_tol;
+    A.maxit = lead.opt.maxit;
+    A.max_refine = lead.opt.max_refine;
+    A.tol = lead.opt.tol;
+    A.inner_tol = lead.opt.inner_tol;
     A.piv_tol = mixed ? 1e-5 : 1e-12;
-    for (int k = 0; k <= kRadius; ++k) A.a[k] = c.coef.a[k];
+    int gx = 1;
+    for (const BSys &S : sys) gx = std::max(gx, S.nslot);
 
     // storage: b, x64, r64 (FP64), then X, R, P, Q (inner precision), then the small arrays
     const size_t ld = (size_t)sb * sb + sb;
-    const size_t bytes = n * (8 + 16 + 16 + 4 * sizeof(C)) + sizeof(BGroup) * W +
-                         sizeof(double2) * ((size_t)W * A.nslot * ld + 2 * (size_t)W * sb * sb) +
-                         sizeof(double) * (size_t)W * sb * A.nchunk * 2 + 16 * 256;
-    char *base = (char *)c.cocg_state.ensure(bytes);
+    const size_t bytes = (size_t)n * (8 + 16 + 16 + 4 * sizeof(C)) + sizeof(BGroup) * W + sizeof(BSys) * nspec +
+                         sizeof(int2) * rows.size() +
+                         sizeof(double2) * ((size_t)W * kBGramSlots * ld + 2 * (size_t)W * sb * sb) +
+                         sizeof(double) * (size_t)W * sb * A.nchunk * 2 + sizeof(int) * (W + 4) + 16 * 256;
+    char *base = (char *)lead.cocg_state.ensure(bytes);
     size_t off = 0;
     auto take = [&](size_t nb) {
         off = (off + 255) / 256 * 256;
@@ -893,45 +997,42 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
     C *pv = (C *)take(sizeof(C) * n);
     C *qv = (C *)take(sizeof(C) * n);
     A.g = (BGroup *)take(sizeof(BGroup) * W);
-    A.gpart = (double2 *)take(sizeof(double2) * (size_t)W * A.nslot * ld);
+    BSys *sys_dev = (BSys *)take(sizeof(BSys) * nspec);
+    A.sys = sys_dev;
+    int2 *rows_dev = (int2 *)take(sizeof(int2) * std::max<size_t>(rows.size(), 1));
+    A.gpart = (double2 *)take(sizeof(double2) * (size_t)W * kBGramSlots * ld);
     A.rho = (double2 *)take(sizeof(double2) * (size_t)W * sb * sb);
     A.coef = take(sizeof(double2) * (size_t)W * sb * sb);
     A.npart = (double *)take(sizeof(double) * (size_t)W * sb * A.nchunk * 2);
     A.count = (int *)take(sizeof(int) * 4);
     int *alist = (int *)take(sizeof(int) * W);
+    RPA_CUDA(cudaMemcpyAsync(sys_dev, sys.data(), sizeof(BSys) * nspec, cudaMemcpyHostToDevice, st));
+    if (!rows.empty())
+        RPA_CUDA(cudaMemcpyAsync(rows_dev, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice, st));
 
     const size_t gram_smem = 2 * (size_t)sb * (TP + 1) * sizeof(C);
     allow_dynamic_smem((const void *)k_bgram<T, 4>, gram_smem);
     allow_dynamic_smem((const void *)k_bgram<T, 8>, gram_smem);
     allow_dynamic_smem((const void *)k_bgram<T, 16>, gram_smem);
-    const T *Vt = mixed ? (const T *)(const void *)c.vloc32 : (const T *)(const void *)c.vloc64;
-    const unsigned pblk = (unsigned)((nd + kBT - 1) / kBT);
+    const unsigned pblk = (unsigned)((nd_max + kBT - 1) / kBT);
 
-    QueueStats qs{};
-    int worst = RPA_OK;
+    std::vector<QueueStats> qs(nspec, QueueStats{});
+    std::vector<int> worst(nspec, RPA_OK);
     std::vector<BGroup> h(W);
-    BTimer tm{c, st, c.opt.profile != 0};
+    BTimer tm{lead, st, lead.opt.profile != 0};
     auto read_counts = [&]() {
-        RPA_CUDA(cudaMemcpyAsync(c.h_count, A.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        sync_stream(c, st);
+        RPA_CUDA(cudaMemcpyAsync(lead.h_count, A.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        sync_stream(lead, st);
         tm.collect();
     };
-    for (int w0 = 0; w0 < total; w0 += W) {
-        const int nw = std::min(W, total - w0);
+    for (size_t w = 0; w + 1 < wave_start.size(); ++w) {
+        const int w0 = wave_start[w], nw = wave_start[w + 1] - w0;
         A.ngroups = nw;
-        for (int i = 0; i < nw; ++i) {
-            BGroup g = sp.groups[w0 + i];
-            g.phase = kBCheck;
-            g.status = RPA_OK;
-            g.cap = g.ncol;
-            g.sre = -c.eps[g.n];
-            g.sim = sp.omega;
-            h[i] = g;
-        }
+        std::copy(all.begin() + w0, all.begin() + w0 + nw, h.begin());
         RPA_CUDA(cudaMemcpyAsync(A.g, h.data(), sizeof(BGroup) * nw, cudaMemcpyHostToDevice, st));
         const dim3 gcols(pblk, nw * sb);
         tm.begin(BTimer::kLoadRetire);
-        k_bload<<<gcols, kBT, 0, st>>>(A, c.psi64, c.ns, sp.vt, sp.rhs, sp.Tc, sp.sign, b, x64, r64);
+        k_bload<<<gcols, kBT, 0, st>>>(A, b, x64, r64);
         RPA_LAUNCH("block COCG load");
         tm.end();
         count_launches(1);
@@ -945,7 +1046,7 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             tm.begin(BTimer::kMaint);
             k_bacc<T><<<gcols, kBT, 0, st>>>(A, xv, x64);
             RPA_LAUNCH("block COCG accumulate");
-            k_bresid<<<gcols, kBT, 0, st>>>(A, c.vloc64, b, x64, r64);
+            k_bresid<<<gcols, kBT, 0, st>>>(A, b, x64, r64);
             RPA_LAUNCH("block COCG residual");
             k_bnorm<<<dim3(A.nchunk, nw * sb), kBT, 0, st>>>(A, b, r64);
             RPA_LAUNCH("block COCG norms");
@@ -953,7 +1054,7 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             RPA_LAUNCH("block COCG check");
             k_bstart<T><<<gcols, kBT, 0, st>>>(A, r64, xv, rv, pv);
             RPA_LAUNCH("block COCG start");
-            gram_launch<T>(A, rv, rv, 1, kBStart, nw, gram_smem, st);
+            gram_launch<T>(A, rv, rv, 1, kBStart, gx, nw, gram_smem, st);
             k_bsmall<T><<<nw, 256, 0, st>>>(A, 0);
             RPA_LAUNCH("block COCG small");
             k_blist<<<1, 1024, 0, st>>>(A, alist);
@@ -961,17 +1062,17 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             tm.end();
             count_launches(8);
             read_counts();
-            const int notdone = c.h_count[0], running = c.h_count[1];
+            const int notdone = lead.h_count[0], running = lead.h_count[1];
             if (notdone == 0) break;
             if (running == 0) continue;
             const dim3 icols(pblk, running * sb), igrp(pblk, running);
             for (int it = 0; it < kBCheckEvery; ++it) {
                 tm.begin(BTimer::kStencil);
-                k_bstencil<T><<<icols, kBT, 0, st>>>(Ai, pv, qv, Vt);
+                k_bstencil<T><<<icols, kBT, 0, st>>>(Ai, pv, qv);
                 RPA_LAUNCH("block COCG stencil");
                 tm.end();
                 tm.begin(BTimer::kGram);
-                gram_launch<T>(Ai, pv, qv, 0, kBInner, running, gram_smem, st);
+                gram_launch<T>(Ai, pv, qv, 0, kBInner, gx, running, gram_smem, st);
                 tm.end();
                 tm.begin(BTimer::kSmall);
                 k_bsmall<T><<<running, 256, 0, st>>>(Ai, 1);
@@ -981,7 +1082,7 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
                 mix<T>(Ai, xv, rv, pv, qv, true, igrp, st);
                 tm.end();
                 tm.begin(BTimer::kGram);
-                gram_launch<T>(Ai, rv, rv, 1, kBInner, running, gram_smem, st);
+                gram_launch<T>(Ai, rv, rv, 1, kBInner, gx, running, gram_smem, st);
                 tm.end();
                 tm.begin(BTimer::kSmall);
                 k_bsmall<T><<<running, 256, 0, st>>>(Ai, 2);
@@ -994,39 +1095,52 @@ int run_block_t(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters_out,
             }
         }
         tm.begin(BTimer::kLoadRetire);
-        if (sp.drho) {
-            k_bretire_drho<<<dim3(pblk, sp.ncols), kBT, 0, st>>>(A, x64, c.psi64, sp.drho, 4.0 / (c.h * c.h * c.h));
+        if (!rows.empty()) {
+            k_bretire_drho<<<dim3(pblk, (unsigned)rows.size()), kBT, 0, st>>>(A, rows_dev, x64);
             RPA_LAUNCH("block COCG retire");
-        } else {
-            k_bretire_copy<<<gcols, kBT, 0, st>>>(A, x64, sp.xout);
+            count_launches(1);
+        }
+        bool copies = false;
+        for (const BSpec *sp : specs) copies = copies || sp->xout;
+        if (copies) {
+            k_bretire_copy<<<gcols, kBT, 0, st>>>(A, x64);
             RPA_LAUNCH("block COCG copy");
+            count_launches(1);
         }
         tm.end();
-        count_launches(1);
         RPA_CUDA(cudaMemcpyAsync(h.data(), A.g, sizeof(BGroup) * nw, cudaMemcpyDeviceToHost, st));
-        sync_stream(c, st);
+        sync_stream(lead, st);
         tm.collect();
         for (int i = 0; i < nw; ++i) {
             const BGroup &g = h[i];
-            qs.solves += g.ncol;
-            qs.nearb += g.nearb;
-            worst = std::max(worst, g.status);
+            QueueStats &q = qs[g.ctx];
+            q.solves += g.ncol;
+            q.nearb += g.nearb;
+            worst[g.ctx] = std::max(worst[g.ctx], g.status);
             for (int k = 0; k < g.ncol; ++k) {
-                qs.iters += g.itc[k];
-                qs.refines += g.refc[k];
+                q.iters += g.itc[k];
+                q.refines += g.refc[k];
                 if (iters_out) (*iters_out)[g.sys0 + k] = g.itc[k];
                 if (status_out) (*status_out)[g.sys0 + k] = g.status;
             }
         }
     }
-    qs.worst = worst;
     tm.report();
-    return add_queue_stats(c, qs);
+    int w_all = RPA_OK;
+    if (spec_worst) spec_worst->assign(nspec, RPA_OK);
+    for (int k = 0; k < nspec; ++k) {
+        qs[k].worst = worst[k];
+        const int wk = add_queue_stats(*specs[k]->c, qs[k]);
+        if (spec_worst) (*spec_worst)[k] = wk;
+        w_all = std::max(w_all, wk);
+    }
+    return w_all;
 }
 
-int run_block(Ctx &c, BSpec &sp, cudaStream_t st, std::vector<int> *iters, std::vector<int> *status) {
-    return c.opt.prec == RPA_MIXED ? run_block_t<float>(c, sp, st, iters, status)
-                                   : run_block_t<double>(c, sp, st, iters, status);
+int run_block(Ctx &lead, std::vector<BSpec *> &specs, cudaStream_t st, std::vector<int> *iters,
+              std::vector<int> *status, std::vector<int> *spec_worst = nullptr) {
+    return lead.opt.prec == RPA_MIXED ? run_block_t<float>(lead, specs, st, iters, status, spec_worst)
+                                      : run_block_t<double>(lead, specs, st, iters, status, spec_worst);
 }
 
 BGroup make_group(int n, int ncol, int sys0, int row0) {
@@ -1038,16 +1152,14 @@ BGroup make_group(int n, int ncol, int sys0, int row0) {
     return g;
 }
 
-}  // namespace
-
-int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+// The pair right-hand sides of chi0 on ncols columns of dv for one context: P_c coefficients
+// T[(n, j)][k] = u_k . (u_n (.) dv_j) in FP64 (the block iteration does not project its residuals
+// again, so the right-hand sides keep whatever occupied components these coefficients leave), and
+// the groups of s consecutive columns per orbital.  T lives in `coef` (grown as needed).
+void chi0_spec(Ctx &c, double omega, const double *dv, double *drho, int ncols, int sb, DevBuf &coef, BSpec &sp,
+               cudaStream_t s) {
     RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
-    if (ncols == 0) return RPA_OK;
-    const int sb = c.opt.block_cocg;
-    // P_c coefficients T[(n, j)][k] = u_k . (u_n (.) dv_j), in FP64: the block iteration does not
-    // project its residuals again, so the right-hand sides keep whatever occupied components these
-    // coefficients leave
-    double *T = (double *)c.pc_coef.ensure(sizeof(double) * (size_t)c.ns * ncols * c.ns);
+    double *T = (double *)coef.ensure(sizeof(double) * (size_t)c.ns * ncols * c.ns);
     double *rows = (double *)c.rhs.ensure(sizeof(double) * (size_t)ncols * c.nd);
     for (int n = 0; n < c.ns; ++n) {
         k_bpair_rows<<<dim3((unsigned)std::min<long long>((c.nd + 255) / 256, 1024), ncols), 256, 0, s>>>(
@@ -1056,7 +1168,7 @@ int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int n
         count_launches(1);
         gram(rows, ncols, c.psi64, c.ns, c.nd, T + (size_t)n * ncols * c.ns, s, c.dense_scratch);
     }
-    BSpec sp;
+    sp.c = &c;
     sp.vt = dv;
     sp.Tc = T;
     sp.sign = -1.0;
@@ -1066,13 +1178,46 @@ int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int n
     for (int n = 0; n < c.ns; ++n)
         for (int j0 = 0; j0 < ncols; j0 += sb)
             sp.groups.push_back(make_group(n, std::min(sb, ncols - j0), n * ncols + j0, j0));
-    return run_block(c, sp, s, nullptr, nullptr);
+}
+
+}  // namespace
+
+int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    if (ncols == 0) return RPA_OK;
+    BSpec sp;
+    chi0_spec(c, omega, dv, drho, ncols, c.opt.block_cocg, c.pc_coef, sp, s);
+    std::vector<BSpec *> specs{&sp};
+    return run_block(c, specs, s, nullptr, nullptr);
+}
+
+int chi0_apply_batch(const std::vector<Chi0Request> &reqs, cudaStream_t s, std::vector<int> *status) {
+    if (status) status->assign(reqs.size(), RPA_OK);
+    if (reqs.empty()) return RPA_OK;
+    Ctx &lead = *reqs[0].c;
+    const int sb = std::max(1, lead.opt.block_cocg);
+    std::vector<BSpec> sp(reqs.size());
+    std::vector<BSpec *> specs;
+    std::vector<size_t> which;
+    for (size_t k = 0; k < reqs.size(); ++k) {
+        const Chi0Request &r = reqs[k];
+        if (r.ncols == 0) continue;
+        chi0_spec(*r.c, r.omega, r.dv, r.drho, r.ncols, sb, r.c->pc_coef, sp[k], s);
+        specs.push_back(&sp[k]);
+        which.push_back(k);
+    }
+    if (specs.empty()) return RPA_OK;
+    std::vector<int> sw;
+    const int w = run_block(lead, specs, s, nullptr, nullptr, &sw);
+    if (status)
+        for (size_t q = 0; q < which.size(); ++q) (*status)[which[q]] = sw[q];
+    return w;
 }
 
 int sternheimer_block(Ctx &c, double omega, const int *orb, int nsys, const double *b, const double *Tc, double *x,
                       std::vector<int> *iters, std::vector<int> *status, cudaStream_t s) {
     const int sb = c.opt.block_cocg;
     BSpec sp;
+    sp.c = &c;
     sp.rhs = b;
     sp.Tc = Tc;
     sp.sign = 1.0;
@@ -1084,7 +1229,8 @@ int sternheimer_block(Ctx &c, double omega, const int *orb, int nsys, const doub
         sp.groups.push_back(make_group(orb[i], e - i, i, i));
         i = e;
     }
-    return run_block(c, sp, s, iters, status);
+    std::vector<BSpec *> specs{&sp};
+    return run_block(c, specs, s, iters, status);
 }
 
 }  // namespace rpa

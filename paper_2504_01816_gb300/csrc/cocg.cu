@@ -3478,6 +3478,7 @@ int response_square(Ctx &c, double omega, const double *dv, const double *coef, 
 }
 
 int chi0_apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
+    if (c.coord) return batch_chi0(c, omega, dv, drho, ncols, s);
     if (c.opt.block_cocg > 0) return chi0_apply_block(c, omega, dv, drho, ncols, s);
     RPA_CUDA(cudaMemsetAsync(drho, 0, sizeof(double) * (size_t)ncols * c.nd, s));
     const int nsys = c.ns * ncols;

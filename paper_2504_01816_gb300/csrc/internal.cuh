@@ -83,6 +83,8 @@ struct QueueStats {
     int unfinished;     // a queue stopped at its epoch bound with systems left
 };
 
+struct BatchCoord;   // rendezvous of rpa_ec_batch's threads (api.cu)
+
 // ------------------------------------------------------------------------------------------
 // Context
 // ------------------------------------------------------------------------------------------
@@ -146,6 +148,8 @@ struct Ctx {
     // profiling (rpa_options.profile): event pool and per-kernel point counters on the device
     std::vector<cudaEvent_t> ev_pool;
     unsigned long long *d_prof_points = nullptr;   // RPA_PROF_SLOTS counters
+    // rpa_ec_batch: the rendezvous this context's chi0 applications go to (nullptr otherwise)
+    BatchCoord *coord = nullptr;
     // CUDA graphs: epochs of COCG iterations are captured on a private stream and replayed
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
@@ -213,6 +217,22 @@ bool fused_kernel_applies(const Ctx &c, bool warp_specialised = false, bool clus
 int chi0_apply_block(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s);
 int sternheimer_block(Ctx &c, double omega, const int *orb, int nsys, const double *b, const double *Tc,
                       double *x, std::vector<int> *iters, std::vector<int> *status, cudaStream_t s);
+// One context's chi0 application within a batch.
+struct Chi0Request {
+    Ctx *c;
+    double omega;
+    const double *dv;
+    double *drho;
+    int ncols;
+};
+// chi0 for several contexts (distinct, on one device, with equal precision and COCG settings) in
+// one set of launches: the block COCG kernels over all their groups at once, with block size
+// max(1, block_cocg) and the iteration settings and workspaces of the first context.  The
+// statistics of each context get its own systems.
+int chi0_apply_batch(const std::vector<Chi0Request> &reqs, cudaStream_t s, std::vector<int> *status = nullptr);
+// While a context is attached to a BatchCoord, its chi0 applications are posted there and run
+// together with the other contexts' (batch_chi0).
+int batch_chi0(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s);
 
 // Same as sternheimer_batch, with b replaced by P_c b first.
 int sternheimer_batch_projected(Ctx &c, double omega, const int *orb, int nsys, const double *b, double *x,

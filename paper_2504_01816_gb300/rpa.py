@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "RPA_OK", 1: "RPA_ERR_INVALID", 2: "RPA_ERR_CUDA", 3: "RPA_ER
 
 EXPORTED = ("rpa_default_options", "rpa_setup", "rpa_set_options", "rpa_coulomb_apply", "rpa_coulomb_apply_noalloc",
             "rpa_sternheimer_solve", "rpa_apply_nuchi0", "rpa_ec", "rpa_ec_gradient", "rpa_autotune", "rpa_destroy",
-            "rpa_last_error", "rpa_version")
+            "rpa_last_error", "rpa_version", "rpa_apply_nuchi0_batch", "rpa_ec_batch")
 
 
 class rpa_options(ctypes.Structure):
@@ -104,6 +104,13 @@ def _load():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(rpa_stats), vp]
     lib.rpa_ec_gradient.restype = i
+    lib.rpa_apply_nuchi0_batch.argtypes = [ctypes.POINTER(vp), i, d, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(ctypes.c_int), i, vp]
+    lib.rpa_apply_nuchi0_batch.restype = i
+    lib.rpa_ec_batch.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
+                                 ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp),
+                                 ctypes.POINTER(rpa_stats), vp]
+    lib.rpa_ec_batch.restype = i
     lib.rpa_autotune.argtypes = [vp, d, dp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
     lib.rpa_autotune.restype = i
     lib.rpa_destroy.argtypes = [vp]
@@ -413,6 +420,51 @@ def _autograd_function():
             return gout * grad, None, None, None, None, None, None, None, None
 
     return EcFunction
+
+
+def apply_nuchi0_batch(contexts: Sequence[Context], omega: float, Vs, symmetric: bool = True, stream=None):
+    """rpa_apply_nuchi0_batch: nu^1/2 chi0 nu^1/2 V (or nu chi0 V) for every context with its own
+    block of columns Vs[k] ((n_k, N_d_k) float64 CUDA tensors), all Sternheimer systems in one set
+    of launches.  Returns ([R_k], status)."""
+    import torch
+    n = len(contexts)
+    for c, V in zip(contexts, Vs):
+        _dev64(V, (V.shape[0], c.n_d))
+    Rs = [torch.empty_like(V) for V in Vs]
+    hs = (ctypes.c_void_p * n)(*[c._h for c in contexts])
+    vp = (ctypes.c_void_p * n)(*[V.data_ptr() for V in Vs])
+    rp = (ctypes.c_void_p * n)(*[R.data_ptr() for R in Rs])
+    nc = (ctypes.c_int * n)(*[V.shape[0] for V in Vs])
+    st = _lib.rpa_apply_nuchi0_batch(hs, n, float(omega), vp, rp, nc, int(bool(symmetric)), _stream(stream))
+    _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
+    return Rs, st
+
+
+def ec_batch(contexts: Sequence[Context], V0s, stream=None):
+    """rpa_ec_batch: E_c of every context from its own trial vectors V0s[k] ((n_r_k, N_d_k) float64
+    CUDA tensors), the contexts' chi0 applications batched into one set of launches.  Returns a
+    list of EcResult and the call's status."""
+    n = len(contexts)
+    for c, V in zip(contexts, V0s):
+        _dev64(V, (V.shape[0], c.n_d))
+    lams = [np.zeros((c.options.n_omega, V.shape[0])) for c, V in zip(contexts, V0s)]
+    ecms = [np.zeros(c.options.n_omega) for c in contexts]
+    ec = np.zeros(2 * n)
+    stats = (rpa_stats * n)()
+    hs = (ctypes.c_void_p * n)(*[c._h for c in contexts])
+    vp = (ctypes.c_void_p * n)(*[V.data_ptr() for V in V0s])
+    lp = (ctypes.c_void_p * n)(*[lam.ctypes.data for lam in lams])
+    ep = (ctypes.c_void_p * n)(*[e.ctypes.data for e in ecms])
+    nr = (ctypes.c_int * n)(*[V.shape[0] for V in V0s])
+    st = _lib.rpa_ec_batch(hs, n, nr, vp, lp, ec.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ep, stats,
+                           _stream(stream))
+    _check(st, allow=(RPA_OK, RPA_ERR_NOT_CONVERGED))
+    out = []
+    for k, c in enumerate(contexts):
+        nw = c.options.n_omega
+        sd = stats_dict(stats[k], nw)
+        out.append(EcResult(float(ec[2 * k]), float(ec[2 * k + 1]), ecms[k], lams[k], st, sd))
+    return out, st
 
 
 def ec_autograd(vloc, psi, eps, V0, nx, ny, nz, h, options: Optional[Options] = None):
