@@ -273,7 +273,7 @@ def roofline_of(agg, step_ms, peaks):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s",
             "share_of_step": a["ms"] / step_ms, "avg_launch_us": 1e6 * per_launch_s,
             "floor_bytes_per_point": 48 if "c64" in name else 96,
-            # the whole COCG iteration against the survey's floor (x, r, p read and written once): all
+            # the whole COCG iteration against the floor of x, r, p read and written once: all
             # COCG kernels' time over the points of one of them (each processes every point once)
             "iteration_frac_vs_floor": (48.0 if "c64" in name else 96.0) * a["points"]
             / (sum(v["ms"] for v in agg.values()) / 1e3) / 1e9 / hbm}

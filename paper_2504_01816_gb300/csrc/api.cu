@@ -796,7 +796,7 @@ struct BatchCoord {
     std::mutex m;
     std::condition_variable cv;
     int active = 0;
-    long long round = 0;
+    long long batches = 0;         // batches run so far
     std::vector<Pending> pending;
     cudaEvent_t done = nullptr;    // recorded after each batch
     bool failed = false;
@@ -817,7 +817,7 @@ struct BatchCoord {
             RPA_CUDA(cudaEventRecord(done, s));
             for (size_t k = 0; k < pending.size(); ++k) *pending[k].status = st[k];
             pending.clear();
-            ++round;
+            ++batches;
         } catch (const Error &e) {
             failed = true;
             fail_status = e.status;
@@ -834,9 +834,9 @@ struct BatchCoord {
         std::unique_lock<std::mutex> lk(m);
         if (!failed) {
             pending.push_back({Chi0Request{&c, omega, dv, drho, ncols}, ready, &st});
-            const long long my = round;
+            const long long my = batches;
             if ((int)pending.size() == active) run(s, &c);
-            else cv.wait(lk, [&] { return round > my || failed; });
+            else cv.wait(lk, [&] { return batches > my || failed; });
         }
         cudaEventDestroy(ready);
         if (failed) fail(fail_status, "%s", fail_msg.c_str());
