@@ -21,11 +21,18 @@
 // relative residuals; a group can so shrink to single-column COCG.  Converged columns are left out
 // of every inner solve, and max_refine bounds the inner solves each column takes part in.
 //
-// One inner iteration is seven launches over the groups in flight: the stencil, a Gram kernel
-// (P^T Q), a per-group kernel (alpha by Gaussian elimination with partial pivoting on the
-// equilibrated s x s system), the X/R update, a Gram kernel (R^T R and the column norms), a
-// per-group kernel (stopping test, beta) and the direction update.  The Gram partial sums are
-// written per tile and added in tile order, so results do not depend on scheduling.
+// One inner iteration is seven launches over the groups whose inner solve runs: the stencil, a
+// Gram kernel (P^T Q), a per-group kernel (alpha by Gaussian elimination with partial pivoting on
+// the equilibrated s x s system), the X/R update, a Gram kernel (R^T R and the column norms), a
+// per-group kernel (stopping test, beta) and the direction update.  Every 8 iterations a
+// maintenance pass refines, tests and restarts the groups whose inner solve ended.  The Gram
+// partial sums are written per block and added in block order, so results do not depend on
+// scheduling.
+//
+// The kernels read each group's grid, operator and orbitals from a table of systems, so one set of
+// launches can serve several contexts at once (an uneven batch of independent systems, with
+// single-column groups when block COCG is off); a group's arithmetic is the same whichever other
+// groups are in flight.
 #include <algorithm>
 #include <cmath>
 #include <vector>
