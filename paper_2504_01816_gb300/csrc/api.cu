@@ -822,8 +822,16 @@ struct BatchCoord {
             failed = true;
             fail_status = e.status;
             fail_msg = e.msg;
+        } catch (const std::bad_alloc &) {
+            failed = true;
+            fail_status = RPA_ERR_OOM;
+            fail_msg = "host allocation failed";
+        } catch (...) {
+            failed = true;
+            fail_status = RPA_ERR_INVALID;
+            fail_msg = "unexpected internal error";
         }
-        cv.notify_all();
+        cv.notify_all();   // the waiting threads wake either way
     }
 
     int apply(Ctx &c, double omega, const double *dv, double *drho, int ncols, cudaStream_t s) {
@@ -946,39 +954,50 @@ rpa_status rpa_ec_batch(rpa_ctx *const *ctxs, int n, const int *n_r, const doubl
         for (int k = 0; k < n; ++k) ctxs[k]->impl.coord = &coord;
         const int dev = ctxs[0]->impl.device;
         std::vector<std::thread> threads;
-        for (int k = 0; k < n; ++k)
-            threads.emplace_back([&, k] {
-                Ctx &c = ctxs[k]->impl;
-                cudaStream_t s = nullptr;
-                try {
-                    RPA_CUDA(cudaSetDevice(dev));
-                    RPA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-                    RPA_CUDA(cudaStreamWaitEvent(s, start, 0));
-                    double e2[2] = {0.0, 0.0};
-                    worst[k] = ec_impl(c, n_r[k], V0_dev[k], lambdas_host ? lambdas_host[k] : nullptr, e2,
-                                       ec_per_omega_host ? ec_per_omega_host[k] : nullptr,
-                                       stats ? stats + k : nullptr, s, nullptr, nullptr);
-                    if (ec_host) {
-                        ec_host[2 * k] = e2[0];
-                        ec_host[2 * k + 1] = e2[1];
+        auto finish = [&] {
+            for (std::thread &t : threads) t.join();
+            for (int k = 0; k < n; ++k) ctxs[k]->impl.coord = nullptr;
+            cudaEventDestroy(coord.done);
+            cudaEventDestroy(start);
+        };
+        int spawned = 0;
+        try {
+            for (int k = 0; k < n; ++k, ++spawned)
+                threads.emplace_back([&, k] {
+                    Ctx &c = ctxs[k]->impl;
+                    cudaStream_t s = nullptr;
+                    try {
+                        RPA_CUDA(cudaSetDevice(dev));
+                        RPA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+                        RPA_CUDA(cudaStreamWaitEvent(s, start, 0));
+                        double e2[2] = {0.0, 0.0};
+                        worst[k] = ec_impl(c, n_r[k], V0_dev[k], lambdas_host ? lambdas_host[k] : nullptr, e2,
+                                           ec_per_omega_host ? ec_per_omega_host[k] : nullptr,
+                                           stats ? stats + k : nullptr, s, nullptr, nullptr);
+                        if (ec_host) {
+                            ec_host[2 * k] = e2[0];
+                            ec_host[2 * k + 1] = e2[1];
+                        }
+                    } catch (const Error &e) {
+                        sts[k] = e.status;
+                        msgs[k] = e.msg;
+                    } catch (...) {
+                        sts[k] = RPA_ERR_INVALID;
+                        msgs[k] = "unexpected internal error";
                     }
-                } catch (const Error &e) {
-                    sts[k] = e.status;
-                    msgs[k] = e.msg;
-                } catch (...) {
-                    sts[k] = RPA_ERR_INVALID;
-                    msgs[k] = "unexpected internal error";
-                }
-                coord.leave(s, &c);
-                if (s) {
-                    cudaStreamSynchronize(s);
-                    cudaStreamDestroy(s);
-                }
-            });
-        for (std::thread &t : threads) t.join();
-        for (int k = 0; k < n; ++k) ctxs[k]->impl.coord = nullptr;
-        cudaEventDestroy(coord.done);
-        cudaEventDestroy(start);
+                    coord.leave(s, &c);
+                    if (s) {
+                        cudaStreamSynchronize(s);
+                        cudaStreamDestroy(s);
+                    }
+                });
+        } catch (...) {
+            // a thread could not be started: the ones that run must not wait for it
+            for (int k = spawned; k < n; ++k) coord.leave(nullptr, nullptr);
+            finish();
+            throw;
+        }
+        finish();
         for (int k = 0; k < n; ++k)
             if (sts[k] != RPA_OK) fail(sts[k], "context %d: %s", k, msgs[k].c_str());
     });
