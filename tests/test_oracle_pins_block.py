@@ -90,8 +90,10 @@ def test_block_orthogonality_and_conjugacy(small):
             assert np.max(np.abs(Pk.T @ Ql)) < 1e-9 * scale_p
 
 
-def test_chi0_by_blocks_matches_plain(small):
-    o = oracle.Oracle.from_system(small)
+@pytest.mark.parametrize("periodic", [False, True])
+def test_chi0_by_blocks_matches_plain(small, periodic):
+    s = small if not periodic else synth.small_system((8, 7, 6), h=0.5, n_s=2, n_wells=2, seed=6, periodic=True)
+    o = oracle.Oracle.from_system(s)
     rng = np.random.default_rng(12)
     dv = rng.standard_normal((5, o.grid.n_d))          # blocks of 2: two full and a ragged one
     st_b = oracle.SolveStats()
